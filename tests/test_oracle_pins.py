@@ -1,0 +1,389 @@
+"""Pins for the FP64 oracle: each test checks it against something other than
+itself (closed forms, invariants, an independent solver, brute force, values
+evaluated by hand from the paper's Table I)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import osar_oracle as orc
+from paper_2603_08582_gb300 import synth
+from tests.helpers import small_workload, build_problem, oracle_config, rel_err
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ---------------------------------------------------------------- phases ---
+
+def test_phase_entries_unit_modulus_and_exact_phase():
+    """F[m,n] = exp(-i 2 k_m R_n) (Eqs. 2-4): |F| = 1 and the phase equals the
+    40-digit value of -4 pi f_m R_n / c mod 2 pi, where R_n is evaluated in
+    40-digit arithmetic from the same FP64 coordinates."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    w = synth.workloads()["c2_128x128_split_bf16"]
+    x = orc.pixel_positions(w.nx, w.ny, w.pixel_m)
+    f = orc.frequencies(w.n_freq, w.f_lo_hz, w.f_hi_hz)
+    gamma = synth.workload_track(w)[77]
+    rng = np.random.default_rng(5)
+    ms = rng.integers(0, w.n_freq, 40)
+    ns = rng.integers(0, w.n_pixels, 40)
+    fm = orc.phase_matrix(gamma, x[ns], f[ms])
+    two_pi = 2 * mp.pi
+    worst = 0.0
+    for q in range(40):
+        val = fm[q, q]
+        assert abs(abs(val) - 1.0) < 1e-14
+        r = mp.sqrt(sum((mp.mpf(float(gamma[a])) - mp.mpf(float(x[ns[q], a]))) ** 2
+                        for a in range(3)))
+        theta = -4 * mp.pi * mp.mpf(float(f[ms[q]])) * r / mp.mpf(orc.C_LIGHT)
+        exact = float(mp.fmod(theta, two_pi))
+        got = float(np.angle(val))
+        diff = (got - exact + np.pi) % (2 * np.pi) - np.pi
+        worst = max(worst, abs(diff))
+    # FP64 rounding of a ~5e5 rad argument is ~1e-10 rad
+    assert worst < 2e-9, worst
+
+
+def test_pixel_grid_and_frequencies():
+    x = orc.pixel_positions(4, 3, 2.0)
+    assert x.shape == (12, 3)
+    np.testing.assert_array_equal(x[0], [-3.0, -2.0, 0.0])
+    np.testing.assert_array_equal(x[5], [-1.0, 0.0, 0.0])    # i=1, j=1
+    np.testing.assert_array_equal(x[11], [3.0, 2.0, 0.0])
+    f = orc.frequencies(5, 1.0, 2.0)
+    np.testing.assert_allclose(f, [1.0, 1.25, 1.5, 1.75, 2.0])
+
+
+# ------------------------------------------------------- Gram recursion ---
+
+@pytest.mark.parametrize("dictionary", ["identity", "gaussian"])
+def test_recursion_equals_batch_gram_and_data(dictionary):
+    """Eq. 13's recursion equals the stacked (batch) Gram and data vector, and
+    G c - b equals the matrix-free gradient of Eq. 10."""
+    w = small_workload(nx=6, ny=5, n_freq=12, n_pulses=9,
+                       dictionary=dictionary,
+                       n_atoms=45 if dictionary == "gaussian" else None)
+    track, dic, c_true, data = build_problem(w)
+    of = orc.OnlineFista(oracle_config(w, dic))
+    blocks = []
+    for s in range(w.n_pulses):
+        of.push_pulse(track[s], data[s])
+        blocks.append(of.block(track[s]))
+    gb = orc.batch_gram(blocks)
+    bb = orc.batch_data(blocks, list(data))
+    assert rel_err(of.s.gram, gb) < 1e-12
+    assert rel_err(of.s.b, bb) < 1e-12
+    y = synth.sparse_coefficients(of.m, 0.3, np.random.default_rng(3))
+    assert rel_err(of.s.gram @ y - of.s.b,
+                   orc.gradient_matrix_free(blocks, list(data), y)) < 1e-12
+
+
+def test_identity_gram_closed_form():
+    """Pixel basis: G_jj = n K exactly and the off-diagonal entries are the
+    Dirichlet-kernel sum over pulses of
+    exp(i(2k0 + (K-1)dk) dR) sin(K dk dR) / sin(dk dR), dR = R_i - R_j."""
+    w = small_workload(nx=7, ny=6, n_freq=24, n_pulses=11, span_deg=20.0)
+    track, dic, c_true, data = build_problem(w)
+    of = orc.OnlineFista(oracle_config(w, None))
+    for s in range(w.n_pulses):
+        of.push_pulse(track[s], data[s])
+    g = of.s.gram
+    nk = w.n_pulses * w.n_freq
+    np.testing.assert_allclose(np.real(np.diag(g)), nk, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(np.imag(np.diag(g)), 0.0, atol=1e-10)
+    x = orc.pixel_positions(w.nx, w.ny, w.pixel_m)
+    k0 = 2 * np.pi * w.f_lo_hz / orc.C_LIGHT
+    dk = 2 * np.pi * (w.f_hi_hz - w.f_lo_hz) / ((w.n_freq - 1) * orc.C_LIGHT)
+    kk = w.n_freq
+    closed = np.zeros_like(g)
+    for gamma in track:
+        r = orc.ranges(gamma, x)
+        dr = r[:, None] - r[None, :]
+        s = np.sin(dk * dr)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            ratio = np.where(np.abs(s) < 1e-300, kk, np.sin(kk * dk * dr) / s)
+        closed += np.exp(1j * (2 * k0 + (kk - 1) * dk) * dr) * ratio
+    assert np.max(np.abs(g - closed)) / nk < 1e-8
+
+
+def test_gram_hermitian_psd():
+    w = small_workload(nx=5, ny=5, n_freq=8, n_pulses=4,
+                       dictionary="gaussian", n_atoms=50)
+    track, dic, c_true, data = build_problem(w)
+    of = orc.OnlineFista(oracle_config(w, dic))
+    for s in range(w.n_pulses):
+        of.push_pulse(track[s], data[s])
+    g = of.s.gram
+    assert np.linalg.norm(g - g.conj().T) <= 1e-14 * np.linalg.norm(g)
+    ev = np.linalg.eigvalsh(0.5 * (g + g.conj().T))
+    # rank <= K P = 32 < M = 50: PSD with a null space
+    assert ev.min() >= -1e-12 * ev.max()
+    assert np.sum(ev > 1e-9 * ev.max()) <= w.n_freq * w.n_pulses
+
+
+# ------------------------------------------------------------ Lipschitz ---
+
+def test_power_iteration_bounds_and_convergence():
+    """mu <= lambda_max (Eq. 11), converges to it, and stays under the
+    incremental bound of Eq. 14."""
+    w = small_workload(nx=6, ny=6, n_freq=16, n_pulses=8)
+    track, dic, c_true, data = build_problem(w)
+    of = orc.OnlineFista(oracle_config(w, None, power_iters_first=40,
+                                       power_iters=40, margin=0.0))
+    bound = 0.0
+    for s in range(w.n_pulses):
+        a_s = of.block(track[s])
+        bound = orc.incremental_lipschitz_bound(bound, a_s)
+        of.push_pulse(track[s], data[s])
+        lmax = np.linalg.eigvalsh(of.s.gram).max()
+        assert of.s.lip <= lmax * (1 + 1e-12)
+        assert lmax <= bound * (1 + 1e-12)
+    mu, _ = orc.power_iteration(of.s.gram, of.s.v, 2000)
+    assert abs(mu - np.linalg.eigvalsh(of.s.gram).max()) <= 1e-10 * mu
+
+
+# ------------------------------------------------------------- shrinkage ---
+
+def test_soft_threshold_table():
+    u = np.array([3 + 4j, 3 + 4j, 3 + 4j, 0j, -2j, 1e-300 + 0j])
+    a = [1.0, 5.0, 5.0 - 1e-9, 0.5, 2.0, 0.0]
+    out = np.array([orc.soft_threshold(np.array([ui]), ai)[0]
+                    for ui, ai in zip(u, a)])
+    np.testing.assert_allclose(out[0], 2.4 + 3.2j, rtol=0, atol=1e-15)
+    assert out[1] == 0                      # |u| == alpha: exactly zero
+    np.testing.assert_allclose(abs(out[2]), 1e-9, rtol=1e-6)
+    assert out[3] == 0                      # u = 0
+    assert out[4] == 0                      # |u| == alpha
+    assert out[5] == u[5]                   # alpha = 0: identity
+
+
+def test_soft_threshold_is_the_prox_by_brute_force():
+    """S_a(u) minimises 1/2 |x - u|^2 + a |x| over a fine grid of x in C."""
+    rng = np.random.default_rng(7)
+    grid = np.linspace(-3, 3, 1201)
+    xr, xi = np.meshgrid(grid, grid, indexing="ij")
+    xc = xr + 1j * xi
+    for _ in range(6):
+        u = complex(rng.uniform(-2, 2), rng.uniform(-2, 2))
+        a = float(rng.uniform(0.1, 1.5))
+        obj = 0.5 * np.abs(xc - u) ** 2 + a * np.abs(xc)
+        best = xc.flat[np.argmin(obj)]
+        s = orc.soft_threshold(np.array([u]), a)[0]
+        assert abs(best - s) <= 2 * (grid[1] - grid[0])
+        # phase is kept, modulus shrinks by a
+        if s != 0:
+            assert abs(abs(s) - (abs(u) - a)) < 1e-14
+            assert abs(np.angle(s) - np.angle(u)) < 1e-12
+
+
+# ---------------------------------------------------------------- FISTA ---
+
+def _tiny_problem(seed=0):
+    w = small_workload(nx=8, ny=8, n_freq=16, n_pulses=16, seed=seed)
+    track, dic, c_true, data = build_problem(w)
+    of = orc.OnlineFista(oracle_config(w, None))
+    for s in range(w.n_pulses):
+        of.push_pulse(track[s], data[s])
+    return w, of, c_true
+
+
+def _coordinate_descent(g, b, lam, sweeps):
+    """Independent LASSO solver: cyclic complex coordinate descent,
+    c_i <- S_lambda(b_i - sum_{j != i} G_ij c_j) / G_ii."""
+    c = np.zeros_like(b)
+    gc = np.zeros_like(b)
+    for _ in range(sweeps):
+        for i in range(b.size):
+            r = b[i] - (gc[i] - g[i, i] * c[i])
+            new = orc.soft_threshold(np.array([r]), lam)[0] / g[i, i].real
+            delta = new - c[i]
+            if delta != 0:
+                gc += g[:, i] * delta
+                c[i] = new
+    return c
+
+
+def test_fista_reaches_kkt_solution_and_matches_coordinate_descent():
+    w, of, c_true = _tiny_problem()
+    g, b, lam = of.s.gram, of.s.b, of.s.lam
+    lmax = np.linalg.eigvalsh(g).max()
+    lmin = np.linalg.eigvalsh(g).min()
+    assert lmin > 0                              # unique minimiser
+    c, _, _ = orc.fista_fixed(g, b, lam, lmax, 20000)
+    assert orc.kkt_residual(g, b, c, lam) < 1e-9
+    c_cd = _coordinate_descent(g, b, lam, 400)
+    assert orc.kkt_residual(g, b, c_cd, lam) < 1e-9
+    assert rel_err(c, c_cd) < 1e-8
+
+
+def test_fista_minimum_by_random_perturbation():
+    """Brute force: no perturbation of the FISTA point lowers Eq. 8."""
+    w, of, c_true = _tiny_problem(seed=4)
+    g, b, lam = of.s.gram, of.s.b, of.s.lam
+    c, _, _ = orc.fista_fixed(g, b, lam, np.linalg.eigvalsh(g).max(), 20000)
+    j0 = orc.lasso_objective_gram(g, b, c, lam)
+    rng = np.random.default_rng(1)
+    for scale in (1e-1, 1e-3, 1e-5):
+        d = scale * (rng.standard_normal((400, c.size))
+                     + 1j * rng.standard_normal((400, c.size)))
+        for k in range(d.shape[0]):
+            assert orc.lasso_objective_gram(g, b, c + d[k], lam) >= j0 - 1e-9 * abs(j0)
+
+
+def test_gram_objective_equals_data_objective():
+    """Eq. 8 through (G, b) equals Eq. 8 through the stored pulses."""
+    w = small_workload(nx=5, ny=4, n_freq=10, n_pulses=5)
+    track, dic, c_true, data = build_problem(w)
+    of = orc.OnlineFista(oracle_config(w, None))
+    blocks = []
+    for s in range(w.n_pulses):
+        of.push_pulse(track[s], data[s])
+        blocks.append(of.block(track[s]))
+    c = c_true * 0.7 + 0.01
+    const = 0.5 * float(np.sum(np.abs(data) ** 2))
+    j_gram = orc.lasso_objective_gram(of.s.gram, of.s.b, c, 0.3, const)
+    j_data = orc.lasso_objective(blocks, list(data), c, 0.3)
+    assert abs(j_gram - j_data) <= 1e-10 * abs(j_data)
+
+
+def test_fista_beck_teboulle_rate():
+    """With t_1 = 1: F(c_k) - F* <= 2 L |c_0 - c*|^2 / (k+1)^2."""
+    w, of, c_true = _tiny_problem(seed=2)
+    g, b, lam = of.s.gram, of.s.b, of.s.lam
+    lip = np.linalg.eigvalsh(g).max()
+    c_star = _coordinate_descent(g, b, lam, 600)
+    f_star = orc.lasso_objective_gram(g, b, c_star, lam)
+    _, _, hist = orc.fista_fixed(g, b, lam, lip, 300)
+    r0 = np.linalg.norm(c_star) ** 2
+    for k, ck in enumerate(hist, start=1):
+        gap = orc.lasso_objective_gram(g, b, ck, lam) - f_star
+        assert gap <= 2 * lip * r0 / (k + 1) ** 2 + 1e-9 * abs(f_star)
+
+
+def test_momentum_sequence():
+    t = 1.0
+    for k in range(1, 200):
+        assert t >= (k + 1) / 2.0 - 1e-12
+        tn = orc.momentum_next(t)
+        assert abs(tn * tn - tn - t * t) < 1e-9 * tn * tn   # t'^2 - t' = t^2
+        t = tn
+
+
+# ---------------------------------------------------------- point target ---
+
+def test_point_target_closed_form():
+    """Noise-free single scatterer in the pixel basis: the LASSO minimiser is
+    c* = a (1 - lambda / (|a| G_jj)) e_j."""
+    w = small_workload(nx=7, ny=7, n_freq=16, n_pulses=12, snr_db=300.0)
+    j = 17
+    a = 0.8 * np.exp(0.7j)
+    c_true = np.zeros(w.n_pixels, dtype=np.complex128)
+    c_true[j] = a
+    track, dic, _, data = build_problem(w, noise=False, c_true=c_true)
+    lam = 10.0
+    of = orc.OnlineFista(oracle_config(w, None, lam=lam, lambda_relative=False))
+    for s in range(w.n_pulses):
+        of.push_pulse(track[s], data[s])
+    g, b = of.s.gram, of.s.b
+    gjj = g[j, j].real
+    expect = np.zeros_like(c_true)
+    expect[j] = a * (1.0 - lam / (abs(a) * gjj))
+    assert orc.kkt_residual(g, b, expect, lam) < 1e-10
+    c, _, _ = orc.fista_fixed(g, b, lam, np.linalg.eigvalsh(g).max(), 5000)
+    assert np.max(np.abs(c - expect)) < 1e-9
+
+
+def test_online_point_targets_land_on_their_pixels():
+    w = small_workload(nx=16, ny=16, n_freq=32, n_pulses=24, span_deg=40.0,
+                       snr_db=30.0, seed=9)
+    c_true = np.zeros(w.n_pixels, dtype=np.complex128)
+    pix = [3 * 16 + 3, 8 * 16 + 12, 13 * 16 + 5]
+    c_true[pix] = [0.9, 0.8j, -0.7]
+    track, dic, _, data = build_problem(w, c_true=c_true)
+    of, _ = orc.run_online(oracle_config(w, None, lam=0.1), track, data, 20)
+    top = set(np.argsort(-np.abs(of.s.c_hat))[:3].tolist())
+    assert top == set(pix)
+
+
+# ---------------------------------------------------------- online burst ---
+
+def test_iterate_split_equals_single_burst():
+    w = small_workload(nx=6, ny=6, n_freq=12, n_pulses=5)
+    track, dic, c_true, data = build_problem(w)
+    a = orc.OnlineFista(oracle_config(w, None))
+    b = orc.OnlineFista(oracle_config(w, None))
+    for s in range(w.n_pulses):
+        a.push_pulse(track[s], data[s])
+        b.push_pulse(track[s], data[s])
+        a.iterate(7)
+        b.iterate(3)
+        b.iterate(4)
+        assert np.array_equal(a.s.c_hat, b.s.c_hat)
+        assert a.s.t == b.s.t
+
+
+def test_momentum_carried_vs_restart():
+    w = small_workload(nx=6, ny=6, n_freq=12, n_pulses=4)
+    track, dic, c_true, data = build_problem(w)
+    carry, _ = orc.run_online(oracle_config(w, None), track, data, 5)
+    rest, _ = orc.run_online(oracle_config(w, None, restart_momentum=True),
+                             track, data, 5)
+    t = 1.0
+    for _ in range(20):
+        t = orc.momentum_next(t)
+    assert abs(carry.s.t - t) < 1e-12              # 4 bursts x 5 steps, carried
+    t = 1.0
+    for _ in range(5):
+        t = orc.momentum_next(t)
+    assert abs(rest.s.t - t) < 1e-12
+
+
+def test_tolerance_stop_rule():
+    w = small_workload(nx=6, ny=6, n_freq=12, n_pulses=6)
+    track, dic, c_true, data = build_problem(w)
+    of = orc.OnlineFista(oracle_config(w, None))
+    for s in range(w.n_pulses):
+        of.push_pulse(track[s], data[s])
+    n = of.iterate(5000, tol=1e-5)
+    assert 0 < n < 5000
+    z_gap = np.linalg.norm(of.s.c_hat - of.s.c_prev)
+    assert z_gap == 0
+    assert of.iterate(10, tol=1e-5) == 0           # converged burst stays put
+
+
+# ------------------------------------------------------------- Table I ---
+
+def test_memory_table_golden():
+    g = json.load(open(os.path.join(HERE, "golden", "table1_memory.json")))
+    for case in g["cases"]:
+        fista, online = orc.memory_values(case["M"], case["N"], case["N_r"],
+                                          case["n"])
+        assert fista == case["fista"]
+        assert online == case["online"]
+
+
+# ------------------------------------------------------- input generator ---
+
+def test_philox_known_answers():
+    """Published Philox4x32-10 known-answer vectors (Random123)."""
+    z = synth.philox4x32_10(np.zeros((1, 4), np.uint32), (0, 0))[0]
+    assert [int(v) for v in z] == [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]
+    o = synth.philox4x32_10(np.full((1, 4), 0xFFFFFFFF, np.uint32),
+                            (0xFFFFFFFF, 0xFFFFFFFF))[0]
+    assert [int(v) for v in o] == [0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd]
+    p = synth.philox4x32_10(
+        np.array([[0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344]], np.uint32),
+        (0xa4093822, 0x299f31d0))[0]
+    assert [int(v) for v in p] == [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]
+
+
+def test_gaussian_dictionary_statistics():
+    d = synth.gaussian_dictionary(256, 300, seed=3)
+    np.testing.assert_allclose(np.linalg.norm(d, axis=0), 1.0, rtol=1e-14)
+    raw = d * np.sqrt(256)
+    assert abs(np.mean(raw.real)) < 0.02 and abs(np.mean(raw.imag)) < 0.02
+    assert abs(np.var(raw.real) - 0.5) < 0.02
+    cols = synth.gaussian_dictionary_columns(256, np.array([7, 299]), seed=3)
+    assert np.array_equal(cols, d[:, [7, 299]])
