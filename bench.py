@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark: pulses/s of online sparse-SAR reconstruction (per pulse: phase
+synthesis, dictionary apply, Gram + data-vector update, lambda and power
+iteration for L, then a FISTA burst of up to m = 20 steps to tol = 1e-4) on
+the 128 x 128 workload (N = 16384 pixels, M = 32768 Gaussian atoms,
+K = 512 frequencies, 256 pulses over 45 deg) in the split-BF16 precision
+form, against the plain FP64 GPU path and the FP64 CPU oracle.
+
+One JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle on
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("pulses/s online (Gram update + FISTA burst to tol) at 128×128 "
+          "vs FP64 path")
+WORKLOAD = "c2_128x128_split_bf16"
+INNER_STEPS = 20
+TOL = 1e-4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-pulses", type=int, default=2)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers --
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+                "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_source_hash() -> str:
+    path = os.path.join(ROOT, "paper_2603_08582_gb300", "csrc", "k_fista.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(kind: str):
+    """DRAM bytes per launch from the committed ncu summary, when it was taken
+    on the kernel source now in the tree (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kind}_ncu.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for ln in text.splitlines():
+        if ":" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("k_fista.cu sha256[:16]") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram bytes per full-size launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# -------------------------------------------------------------- workload ---
+
+def workload():
+    from paper_2603_08582_gb300 import synth
+    return synth.workloads()[WORKLOAD]
+
+
+def make_ctx(w, precision, stream):
+    from paper_2603_08582_gb300 import osar
+    cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
+                           pixel_m=w.pixel_m, precision=precision,
+                           dictionary="gaussian", n_atoms=w.m_atoms,
+                           dict_seed=w.dict_seed, lam=w.lambda_rel,
+                           stream=stream)
+    return osar.Osar(cfg)
+
+
+def pulse_data(ctx, w, n_pulses):
+    """Noisy pulses d_s = G_s c_true + noise (SNR per pulse), simulated by the
+    library on the device; the noise draws come from the input generator."""
+    from paper_2603_08582_gb300 import synth
+    track = synth.workload_track(w)
+    c_true = synth.workload_scene(w)
+    noise = synth.unit_noise(w.n_pulses, w.n_freq, w.seed)
+    clean = np.stack([ctx.simulate_pulse(track[s], c_true) for s in range(n_pulses)])
+    return track[:n_pulses], clean + synth.scale_noise(clean, noise[:n_pulses], w.snr_db)
+
+
+# ------------------------------------------------------------------ ours ---
+
+def run_ours(args):
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2603_08582_gb300 import osar
+
+    w = workload()
+    W, K = args.warmup, args.steps
+    stream = torch.cuda.Stream()
+    ctx = make_ctx(w, "split_bf16", stream.cuda_stream)
+    total = W + 2 * K
+    if total > w.n_pulses:
+        raise SystemExit(f"warmup + 2*steps must be <= {w.n_pulses} pulses")
+    track, data = pulse_data(ctx, w, total)
+    d_dev = torch.from_numpy(data).to(f"cuda:{local_rank}")
+    torch.cuda.synchronize()
+    d_ptr = d_dev.data_ptr()
+    row = w.n_freq * 16
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        for s in range(W):
+            ctx.push_pulse_dev(track[s], d_ptr + s * row)
+            ctx.iterate(INNER_STEPS, TOL, want_count=False)
+        ctx.synchronize()
+        ctx.profile_reset()
+        ctx.profile_enable(True)
+        launches0 = ctx.launch_count()
+        sampler = ClockSampler(local_rank)
+        sampler.start()
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for s in range(W, W + K):
+            ctx.push_pulse_dev(track[s], d_ptr + s * row)
+            ctx.iterate(INNER_STEPS, TOL, want_count=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+        launches = ctx.launch_count() - launches0
+        prof = {k: ctx.profile_read(k) for k in osar.KERNEL_CLASSES}
+        ctx.profile_enable(False)
+
+        # end to end: host pulses in, coefficients back, every step
+        pinned = torch.from_numpy(data[W + K:W + 2 * K].copy()).pin_memory().numpy()
+        iters = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q, s in enumerate(range(W + K, W + 2 * K)):
+            ctx.push_pulse(track[s], pinned[q])
+            iters.append(ctx.iterate(INNER_STEPS, TOL))
+            c_hat = ctx.coeffs()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+
+    ms_t = torch.tensor([ms], device=f"cuda:{local_rank}")
+    e2e_t = torch.tensor([e2e_s], device=f"cuda:{local_rank}")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    e2e_s = float(e2e_t.item())
+    value = world * K / (ms / 1e3)
+    e2e_value = world * K / e2e_s
+
+    peaks, peak_src = measured_peaks()
+    nblk = ctx_blocks(w.m_atoms)
+    gram_bytes = nblk * 128 * 128 * 8
+    mv_n, mv_ms = prof["matvec"]
+    mv_avg = mv_ms / max(mv_n, 1)
+    achieved = gram_bytes / (mv_avg / 1e3) / 1e9
+    traffic = profiled_traffic("matvec_c2")
+    roofline = {"bound": "hbm", "kernel": "k_matvec<float> (packed upper Gram)",
+                "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs",
+                "algorithmic_bytes_per_launch": gram_bytes,
+                "avg_launch_ms": round(mv_avg, 4), "launches": mv_n}
+    kp = ((w.n_freq + 127) // 128) * 128
+    npx = ((w.n_pixels + 127) // 128) * 128
+    gram_flops = nblk * 3 * 2 * 128 * 256 * 2 * kp
+    dict_flops = (w.m_atoms // 128) * (kp // 128) * 3 * 2 * 128 * 256 * 2 * npx
+    g_n, g_ms = prof["gram_gemm"]
+    d_n, d_ms = prof["dict_gemm"]
+    tens = {
+        "gram": {"bound": "tensor", "executed_flops_per_launch": gram_flops,
+                 "avg_launch_ms": round(g_ms / max(g_n, 1), 4),
+                 "achieved": round(gram_flops / (g_ms / max(g_n, 1) / 1e3) / 1e12, 1),
+                 "peak": peaks.get("bf16_tflops_sustained", 1724.5),
+                 "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16_tflops_sustained"},
+        "dict": {"bound": "tensor", "executed_flops_per_launch": dict_flops,
+                 "avg_ms_per_pulse": round(d_ms / max(g_n, 1), 4),
+                 "achieved": round(dict_flops / (d_ms / max(g_n, 1) / 1e3) / 1e12, 1),
+                 "peak": peaks.get("bf16_tflops_sustained", 1724.5),
+                 "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16_tflops_sustained"},
+    }
+    for v in tens.values():
+        v["frac"] = round(v["achieved"] / v["peak"], 4)
+    per_kernel = {k: {"launches": n, "total_ms": round(t, 3)} for k, (n, t) in prof.items()}
+
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        fp64 = run_fp64_path(w, track, data, stream, args.fp64_pulses)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(w, pulses=1)
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "pulses/s",
+        "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(ms / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3 (split-BF16) / fp32",
+        "data": "synthetic (seeded scene, Philox Gaussian dictionary, device-simulated pulses + 25 dB noise)",
+        "config": {"workload": WORKLOAD, "nx": w.nx, "ny": w.ny,
+                   "n_pixels": w.n_pixels, "n_atoms": w.m_atoms,
+                   "n_freq": w.n_freq, "pulses_total": w.n_pulses,
+                   "inner_steps_max": INNER_STEPS, "tol": TOL,
+                   "precision": "split_bf16 (compensated)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (packed Gram 4.3 GB streamed per step)"},
+        "clocks": clocks,
+        "e2e": {"value": round(e2e_value, 3), "unit": "pulses/s",
+                "h2d_bytes_per_step": w.n_freq * 16 + 24,
+                "d2h_bytes_per_step": w.m_atoms * 16 + 4,
+                "mean_iters_per_pulse": round(float(np.mean(iters)), 2)},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "tensor_rooflines": tens,
+        "per_kernel": per_kernel,
+    }
+    if fp64 is not None:
+        line["fp64_path"] = fp64
+        line["speedup_vs_fp64_path"] = round(value / fp64["value"], 2)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def ctx_blocks(m):
+    nb = (m + 127) // 128
+    return nb * (nb + 1) // 2
+
+
+def run_fp64_path(w, track, data, stream, pulses):
+    """The plain FP64 GPU path on the same workload (a few pulses: its Gram
+    update runs on the FP64 pipes)."""
+    import torch
+    ctx = make_ctx(w, "fp64", stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        ctx.push_pulse(track[0], data[0])
+        ctx.iterate(INNER_STEPS, TOL)
+        ctx.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for s in range(1, 1 + pulses):
+            ctx.push_pulse(track[s], data[s])
+            ctx.iterate(INNER_STEPS, TOL, want_count=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ctx.close()
+    return {"value": round(pulses / (ms / 1e3), 4), "unit": "pulses/s",
+            "pulses_timed": pulses, "ms_per_pulse": round(ms / pulses, 2),
+            "dtype": "f64"}
+
+
+# ------------------------------------------------------------ CPU oracle ---
+
+def _dict_chunk(args):
+    n, j0, j1, seed = args
+    from paper_2603_08582_gb300 import synth
+    return j0, synth.gaussian_dictionary_columns(n, np.arange(j0, j1), seed)
+
+
+def host_dictionary(w, procs):
+    """The same Philox dictionary on the host, generated by a spawn pool."""
+    import multiprocessing as mp
+    d = np.empty((w.n_pixels, w.m_atoms), dtype=np.complex128, order="F")
+    chunk = 512
+    jobs = [(w.n_pixels, j, min(w.m_atoms, j + chunk), w.dict_seed)
+            for j in range(0, w.m_atoms, chunk)]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for j0, cols in pool.imap_unordered(_dict_chunk, jobs):
+            d[:, j0:j0 + cols.shape[1]] = cols
+    return d
+
+
+def cpu_baseline(w, pulses=1):
+    """FP64 oracle on the host cores: one untimed pulse, then `pulses` timed
+    pulses of the full 128 x 128 / M = 32768 workload.  Its inputs are made on
+    the host: the dictionary by the input generator, the pulse data by the
+    oracle's own forward model (d_s = F_s (H c_true) + noise)."""
+    from oracle import osar_oracle as orc
+    from paper_2603_08582_gb300 import synth
+    cores = os.cpu_count() or 1
+    t_setup = time.perf_counter()
+    d = host_dictionary(w, cores)
+    track = synth.workload_track(w)
+    c_true = synth.workload_scene(w)
+    noise = synth.unit_noise(w.n_pulses, w.n_freq, w.seed)
+    rho = d @ c_true
+    x = orc.pixel_positions(w.nx, w.ny, w.pixel_m)
+    f = orc.frequencies(w.n_freq, w.f_lo_hz, w.f_hi_hz)
+    clean = np.stack([orc.phase_matrix(track[s], x, f) @ rho
+                      for s in range(1 + pulses)])
+    data = clean + synth.scale_noise(clean, noise[:1 + pulses], w.snr_db)
+    of = orc.OnlineFista(orc.OracleConfig(
+        nx=w.nx, ny=w.ny, pixel_m=w.pixel_m, n_freq=w.n_freq,
+        f_lo_hz=w.f_lo_hz, f_hi_hz=w.f_hi_hz, dictionary=d, lam=w.lambda_rel))
+    of.push_pulse(track[0], data[0])
+    of.iterate(INNER_STEPS, TOL)
+    setup = time.perf_counter() - t_setup
+    t0 = time.perf_counter()
+    for s in range(1, 1 + pulses):
+        of.push_pulse(track[s], data[s])
+        of.iterate(INNER_STEPS, TOL)
+    dt = time.perf_counter() - t0
+    return {"value": round(pulses / dt, 5), "unit": "pulses/s", "cores": cores,
+            "kind": "oracle",
+            "sample": (f"{pulses} full pulse(s) (pulse index 1..{pulses}) of the "
+                       "128x128 / M=32768 workload after one untimed pulse; "
+                       f"setup {setup:.1f} s untimed; numpy FP64, BLAS on all host cores")}
+
+
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    w = workload()
+    steps = max(1, min(args.steps, 2))
+    res = cpu_baseline(w, pulses=steps)
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"],
+            "unit": "pulses/s", "n_gpus": world, "steps": steps,
+            "warmup": 1, "ms_per_step": round(1e3 / res["value"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": "pulses/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": ("each step is one full oracle pulse (tens of seconds); steps "
+                     "are capped at 2 so the run ends within a few minutes")}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

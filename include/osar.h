@@ -1,0 +1,232 @@
+/*
+ * osar.h -- C ABI of libosar: Online FISTA for sparse SAR on one GB300 (sm_103a).
+ *
+ * Method: Flynn, Ivanov, Yazici, "Online Sparse Synthetic Aperture Radar
+ * Imaging" (arXiv 2603.08582).  Per slow-time pulse n the library
+ *   1. synthesises the pulse's forward block G_n = F_n H on the device, with
+ *      F_n[m, p] = exp(-i 2 k_m |gamma(s_n) - x_p|), k_m = 2 pi f_m / c
+ *      (Eqs. 2-4 and 6; the dictionary H is the identity, a host matrix or a
+ *      seeded complex Gaussian);
+ *   2. updates the sufficient statistics A_n = A_{n-1} + G_n^H G_n and
+ *      b_n = b_{n-1} + G_n^H d_n (Eqs. 12-13, white noise R_n = I);
+ *   3. refreshes lambda_n and the Lipschitz constant L_n (Eq. 11) by a
+ *      warm-started power iteration;
+ * and osar_iterate runs the inner loop of Algorithm 1 (gradient step,
+ * complex soft-thresholding, momentum update).
+ *
+ * Naming: the paper writes the accumulated Gram as A_n and the per-pulse
+ * operator as G_n; this header calls the accumulated Gram "gram" and the
+ * per-pulse operator "block", and the coefficients c (length M, complex).
+ *
+ * Conventions for every call:
+ *  - Complex numbers cross the boundary as interleaved (re, im) float64
+ *    pairs ("c128").  Host pointers are plain CPU memory; "_dev" variants
+ *    take device pointers of the stated type.
+ *  - Calls on one context are ordered on the context's CUDA stream and are
+ *    asynchronous unless they return data to host memory (those synchronise
+ *    the stream before returning).
+ *  - Every call returns an osar_status.  A CUDA error makes the context
+ *    sticky-failed: later calls return OSAR_E_CUDA until osar_destroy.
+ *    osar_last_error gives a one-line message for the last failure.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - The library owns every device buffer it allocates; inputs are copied
+ *    (or consumed on the stream) before the call's work completes, so the
+ *    caller may reuse host buffers once a call returns.
+ */
+#ifndef OSAR_H
+#define OSAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct osar_ctx osar_ctx;
+
+typedef enum {
+  OSAR_OK = 0,
+  OSAR_E_INVALID = 1,  /* bad argument or unsupported size */
+  OSAR_E_OOM = 2,      /* device or host allocation failed */
+  OSAR_E_CUDA = 3,     /* a CUDA call failed; the context is sticky-failed */
+  OSAR_E_STATE = 4,    /* call not valid in the context's current state */
+  OSAR_E_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+  OSAR_E_NUMERIC = 6,  /* non-finite value detected in a scalar */
+  OSAR_E_IO = 7        /* checkpoint file could not be read or written */
+} osar_status;
+
+/* Arithmetic of the Gram update and of the FISTA matvec. */
+typedef enum {
+  OSAR_FP64 = 0,        /* plain path: FP64 everywhere (FP64 FMA pipes) */
+  OSAR_FP32 = 1,        /* FP32 SIMT Gram and matvec */
+  OSAR_SPLIT_BF16 = 2   /* tcgen05 split-BF16 (hi*hi + hi*lo + lo*hi) Gram
+                           with FP32 accumulation; FP32 matvec; FP64 phases,
+                           lambda and L */
+} osar_precision;
+
+typedef enum {
+  OSAR_DICT_IDENTITY = 0,  /* H = I, M = N (pixel basis) */
+  OSAR_DICT_HOST = 1,      /* H given as an N x M complex matrix */
+  OSAR_DICT_GAUSSIAN = 2   /* H = unit-norm complex Gaussian columns drawn by
+                              Philox4x32-10 (see osar_config.dict_seed) */
+} osar_dict_kind;
+
+typedef struct {
+  /* Pixel grid (Sec. II): nx x ny pixels of pixel_m metres, centred at the
+     origin on flat ground; pixel p = i*nx + j sits at
+     ((j - (nx-1)/2) pixel_m, (i - (ny-1)/2) pixel_m, 0). */
+  int32_t nx, ny;
+  double pixel_m;
+  /* Frequencies f_m = linspace(f_lo_hz, f_hi_hz, n_freq), both ends kept. */
+  int32_t n_freq;
+  double f_lo_hz, f_hi_hz;
+  /* Dictionary H (Sec. III-A). */
+  int32_t dict_kind;          /* osar_dict_kind */
+  int32_t n_atoms;            /* M; ignored (M = N) for the identity */
+  const double* dict_c128;    /* OSAR_DICT_HOST: N x M column-major c128,
+                                 copied during osar_create */
+  uint64_t dict_seed;         /* OSAR_DICT_GAUSSIAN: entry (p, j) uses Philox
+                                 counter (p, j, 0x5A5D1C7, 0), key = seed;
+                                 z = sqrt(-2 ln u1) exp(2 pi i u2) with
+                                 u = (k + 1/2) 2^-53 from 64-bit word pairs;
+                                 columns scaled to unit 2-norm */
+  int32_t precision;          /* osar_precision */
+  /* lambda: lambda_relative != 0 => lambda_n = lambda * ||b_n||_inf, else
+     lambda_n = lambda. */
+  double lambda;
+  int32_t lambda_relative;
+  /* Power iteration for Eq. 11: power_iters_first steps at the first pulse
+     (from v = 1/sqrt(M)), power_iters warm-started steps afterwards;
+     L_n = max(L_{n-1}, (1 + lipschitz_margin) mu_n). */
+  int32_t power_iters_first, power_iters;
+  double lipschitz_margin;
+  /* 0: Algorithm 1 as printed (t carried across pulses); 1: t = 1 per pulse */
+  int32_t restart_momentum;
+  /* SPLIT_BF16 only: 1 keeps a second FP32 word per Gram entry and adds each
+     pulse with error-free (TwoSum) compensation; 0 plain FP32 accumulation */
+  int32_t compensated;
+  /* cudaStream_t for all work; NULL => a library-owned non-blocking stream */
+  void* cuda_stream;
+} osar_config;
+
+/* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
+   9.9-10.1 GHz, identity dictionary, FP64, lambda = 0.05 relative,
+   30 / 4 power steps, margin 0.01, carried momentum, compensated = 1. */
+void osar_config_default(osar_config* cfg);
+
+/* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128
+   blocks), data vector, coefficient state and per-pulse work buffers, builds
+   the dictionary on the device.  *out is NULL on failure.
+   Errors: OSAR_E_INVALID (sizes <= 0, unknown enums, M or N too large),
+   OSAR_E_OOM, OSAR_E_CUDA. */
+osar_status osar_create(const osar_config* cfg, osar_ctx** out);
+
+/* Release every device and host resource of ctx (NULL is accepted). */
+osar_status osar_destroy(osar_ctx* ctx);
+
+/* One pulse (Eqs. 12-13 and the lambda / L refresh).  gamma_xyz: platform
+   position gamma(s_n) in metres (3 doubles, host).  d_c128: the pulse's
+   n_freq complex samples (host).  Asynchronous; the inputs are staged before
+   return.  Errors: OSAR_E_INVALID for NULL pointers or non-finite gamma. */
+osar_status osar_push_pulse(osar_ctx* ctx, const double gamma_xyz[3],
+                            const double* d_c128);
+
+/* Same, with d already on the device (n_freq complex128, 16-byte aligned).
+   The buffer must stay valid until the stream reaches the call's work. */
+osar_status osar_push_pulse_dev(osar_ctx* ctx, const double gamma_xyz[3],
+                                const void* d_dev_c128);
+
+/* Run up to max_iters steps of Algorithm 1's inner loop.  The first call
+   after a pulse starts the burst (c^(0) = c_hat_{n-1}, z^(1) = c^(0),
+   t_1 = t_{n-1}, or 1 at the first pulse); later calls continue it, so
+   iterate(a) then iterate(b) equals iterate(a + b).  tol > 0 stops the burst
+   once ||c^(k) - z^(k)||_2 <= tol ||c^(k)||_2 (decided on the device; the
+   remaining launches return at once).  iters_done (nullable) receives the
+   number of steps taken in this call, which synchronises the stream.
+   Errors: OSAR_E_STATE before the first pulse, OSAR_E_INVALID for
+   max_iters < 0. */
+osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
+                         int32_t* iters_done);
+
+/* Copy c_hat (M complex) to host memory; synchronises. */
+osar_status osar_get_coeffs(osar_ctx* ctx, double* out_c128);
+
+/* Copy c_hat (M complex128) into device memory out_dev; asynchronous. */
+osar_status osar_get_coeffs_dev(osar_ctx* ctx, void* out_dev_c128);
+
+/* Pulse count n, L_n, lambda_n, momentum t; synchronises.  Any pointer may
+   be NULL. */
+osar_status osar_get_state(osar_ctx* ctx, int32_t* n, double* lipschitz,
+                           double* lambda, double* t);
+
+/* M and N of the context. */
+osar_status osar_get_dims(const osar_ctx* ctx, int32_t* m_atoms,
+                          int32_t* n_pixels, int32_t* n_freq);
+
+/* The accumulated Gram A_n as a dense M x M row-major c128 host matrix
+   (the stored upper half is mirrored; the compensation word is added when
+   present).  Synchronises. */
+osar_status osar_get_gram(osar_ctx* ctx, double* out_c128);
+
+/* Gram entries at (rows[q], cols[q]) for q < count, as c128; synchronises. */
+osar_status osar_get_gram_entries(osar_ctx* ctx, const int32_t* rows,
+                                  const int32_t* cols, int32_t count,
+                                  double* out_c128);
+
+/* The data vector b_n (M complex) as c128 host memory; synchronises. */
+osar_status osar_get_b(osar_ctx* ctx, double* out_c128);
+
+/* y = A_n x with the stored Gram, in the context's matvec arithmetic
+   (x, y: M complex, host c128); synchronises.  Does not touch the FISTA
+   state. */
+osar_status osar_gram_apply(osar_ctx* ctx, const double* x_c128,
+                            double* y_c128);
+
+/* Noise-free pulse data d = G_n c for a platform at gamma_xyz (Eqs. 5-6),
+   computed on the device in FP64: c (M complex, host) in, d (n_freq
+   complex, host) out.  Does not touch the statistics; synchronises. */
+osar_status osar_simulate_pulse(osar_ctx* ctx, const double gamma_xyz[3],
+                                const double* coeffs_c128, double* d_c128);
+
+/* Wait for all work queued on the context's stream. */
+osar_status osar_synchronize(osar_ctx* ctx);
+
+/* Per-kernel device timing.  When enabled, CUDA events bracket every
+   launch of the listed kernel classes on the context's stream; reading the
+   counters synchronises.  kernel: 0 phase, 1 dictionary GEMM, 2 Gram GEMM,
+   3 data-vector update, 4 matvec (FISTA and power steps), 5 FISTA finalize,
+   6 power finalize, 7 scalar steps.  launches / total_ms may be NULL. */
+osar_status osar_profile_enable(osar_ctx* ctx, int32_t on);
+osar_status osar_profile_read(osar_ctx* ctx, int32_t kernel,
+                              int64_t* launches, double* total_ms);
+osar_status osar_profile_reset(osar_ctx* ctx);
+
+/* Total library kernel launches issued on this context since creation
+   (or since the last reset); no synchronisation. */
+osar_status osar_launch_count(const osar_ctx* ctx, int64_t* launches);
+
+/* Bytes of device memory the context holds. */
+osar_status osar_device_bytes(const osar_ctx* ctx, int64_t* bytes);
+
+/* Checkpoint: the sufficient statistics (Gram, b), c_hat, t, L, lambda, the
+   power-iteration vector and the pulse count are exactly what Table I says
+   Online FISTA must keep; osar_save writes them with the config, osar_load
+   rebuilds a context (with cfg's stream, dictionary and precision, which
+   must match the file) that continues bit-for-bit.  Errors: OSAR_E_IO,
+   OSAR_E_INVALID on a mismatched config. */
+osar_status osar_save(osar_ctx* ctx, const char* path);
+osar_status osar_load(const char* path, const osar_config* cfg,
+                      osar_ctx** out);
+
+/* One-line description of the last error on ctx (or of the last failed
+   osar_create when ctx is NULL).  Never NULL. */
+const char* osar_last_error(const osar_ctx* ctx);
+
+/* Library version string. */
+const char* osar_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSAR_H */

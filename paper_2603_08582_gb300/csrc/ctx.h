@@ -1,0 +1,163 @@
+// Host-side context of libosar and the launchers each kernel file exports.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "osar.h"
+#include "common.cuh"
+
+namespace osar {
+
+constexpr double C_LIGHT = 299792458.0;
+
+// Scalars of the online state that live on the device so that no step of a
+// pulse or a FISTA burst needs a host round trip.
+struct DevScalars {
+  double t;         // momentum scalar t_k of Algorithm 1
+  double t_next;    // t_{k+1} of the step in flight
+  double lip;       // L_n
+  double tau;       // 1 / L_n
+  double lambda;    // lambda_n
+  double mu;        // last Rayleigh quotient of the power iteration
+  double inv_norm;  // 1 / |G v| of the last power step
+  double tol;       // stop tolerance of the current burst call
+  int32_t converged;
+  int32_t iters;    // steps taken in the current osar_iterate call
+  int32_t n;        // pulses pushed
+  int32_t error;    // device-side error code (bounded waits)
+  uint32_t done;    // blocks finished in the current grid (last-block steps)
+  uint32_t pad;
+};
+
+enum KernelClass {
+  KCL_PHASE = 0, KCL_DICT = 1, KCL_GRAM = 2, KCL_BUPD = 3, KCL_MATVEC = 4,
+  KCL_FIN = 5, KCL_POWFIN = 6, KCL_SCALAR = 7, KCL_COUNT = 8
+};
+
+struct ProfEvent {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+}  // namespace osar
+
+struct osar_ctx {
+  osar_config cfg;
+  int prec = OSAR_FP64;
+  bool dict = false;  // overcomplete / explicit dictionary present
+  int M = 0, N = 0, K = 0;
+  int Mp = 0, Np = 0, Kp = 0;
+  int nb = 0;          // Mp / BLK
+  int64_t nblk = 0;    // packed upper blocks
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+
+  osar_status sticky = OSAR_OK;
+  std::string last_error;
+
+  // device state
+  osar::DevScalars* scal = nullptr;
+  double2* b = nullptr;        // data vector b_n (Mp)
+  double2* c = nullptr;        // c^(k) == c_hat after a burst (Mp)
+  double2* z = nullptr;        // z^(k) (Mp)
+  double2* v = nullptr;        // power-iteration vector, unit norm (Mp)
+  double2* w = nullptr;        // G v scratch (Mp)
+  double2* xtmp = nullptr;     // scratch vector for osar_gram_apply (Mp)
+  void* zt = nullptr;          // z in the matvec's precision (Mp)
+  void* vt = nullptr;          // v in the matvec's precision (Mp)
+  void* xt = nullptr;          // osar_gram_apply input, matvec precision (Mp)
+  double2* part = nullptr;     // per-block partial sums (nb)
+  double2* d_dev = nullptr;    // staged pulse data (Kp)
+  ulonglong2* turns = nullptr; // per-pixel fixed-point phase terms (Np)
+  void* g_hi = nullptr;        // packed Gram, float2 or double2 per entry
+  float2* g_lo = nullptr;      // compensation word (split-BF16, compensated)
+  void* segpart = nullptr;     // matvec segment partials (nseg x BLK)
+  void* tilepart = nullptr;    // matvec per-block partials (nblk x BLK)
+  int4* segs = nullptr;        // matvec work items (J, I0, I1, slot)
+  int* seg_begin = nullptr;    // first segment of block column J (nb + 1)
+  double* bmax = nullptr;      // per-block max |b_j|^2 (data update)
+  float2* d32 = nullptr;       // staged pulse data in FP32 (Kp)
+  int nseg = 0;
+  int2* gram_tiles = nullptr;  // upper blocks in L2-friendly order
+  int2* dict_tiles = nullptr;  // (atom block, frequency block | slice << 16)
+  int n_dict_tiles = 0;
+  int dict_slices = 1;         // split-K slices of the dictionary product
+  float2* dict_part = nullptr; // split: FP32 slice partials (slices x Mp x Kp)
+  // per-pulse operands
+  void* A = nullptr;           // FP64/FP32: Mp x Kp complex, atom-major
+  void* F = nullptr;           // FP64/FP32 + dictionary: Kp x Np complex
+  void* D = nullptr;           // FP64/FP32 + dictionary: Mp x Np complex
+  __nv_bfloat16* Apl = nullptr;  // split: 6 planes x Mp x Kp
+  __nv_bfloat16* Fpl = nullptr;  // split + dictionary: 6 planes x Kp x Np
+  __nv_bfloat16* Dpl = nullptr;  // split + dictionary: 4 planes x Mp x Np
+  CUtensorMap map_a_rows1;     // Apl, box (KC, 128, 1)
+  CUtensorMap map_a_rows2;     // Apl, box (KC, 128, 2)
+  CUtensorMap map_d_rows1;     // Dpl, box (KC, 128, 1)
+  CUtensorMap map_f_rows2;     // Fpl, box (KC, 128, 2)
+  // pinned staging ring for pulse data (slots of Kp complex)
+  static constexpr int RING = 8;
+  double2* h_ring = nullptr;
+  cudaEvent_t ring_ev[RING] = {};
+  int ring_pos = 0;
+  // simulate scratch
+  double2* sim_rho = nullptr;  // Np
+  double2* sim_nz = nullptr;   // nonzero coefficient values (Mp)
+  int* sim_idx = nullptr;      // nonzero coefficient indices (Mp)
+  double2* sim_d = nullptr;    // simulated pulse (Kp)
+
+  // host mirror
+  int n = 0;
+  bool fresh = true;
+  int64_t launches = 0;
+  int64_t dev_bytes = 0;
+
+  // profiling
+  bool prof_on = false;
+  std::vector<osar::ProfEvent> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[osar::KCL_COUNT] = {0};
+  int64_t prof_launches[osar::KCL_COUNT] = {0};
+};
+
+namespace osar {
+
+// ---- launch bracketing for the per-kernel profile -------------------------
+void prof_begin(osar_ctx* ctx, int kind, ProfEvent* ev);
+void prof_end(osar_ctx* ctx, ProfEvent* ev);
+
+// ---- k_phase.cu -------------------------------------------------------------
+cudaError_t launch_pixel_turns(osar_ctx* ctx, const double gamma[3]);
+cudaError_t launch_phase(osar_ctx* ctx);
+cudaError_t launch_dictionary_build(osar_ctx* ctx, const double* host_dict);
+cudaError_t launch_simulate(osar_ctx* ctx, int nnz, double2* d_out);
+
+// ---- k_gemm_simt.cu --------------------------------------------------------
+cudaError_t launch_dict_simt(osar_ctx* ctx);
+cudaError_t launch_gram_simt(osar_ctx* ctx);
+
+// ---- k_gemm_tc.cu ----------------------------------------------------------
+bool make_tensor_maps(osar_ctx* ctx, std::string* err);
+cudaError_t launch_dict_tc(osar_ctx* ctx);
+int dict_slices(int np);
+cudaError_t launch_gram_tc(osar_ctx* ctx);
+
+// ---- k_fista.cu ------------------------------------------------------------
+cudaError_t launch_data_update(osar_ctx* ctx);
+cudaError_t launch_power_steps(osar_ctx* ctx, int steps);
+cudaError_t launch_set_working(osar_ctx* ctx);
+cudaError_t launch_burst_begin(osar_ctx* ctx);
+cudaError_t launch_iter_begin(osar_ctx* ctx, double tol);
+cudaError_t launch_fista_step(osar_ctx* ctx);
+cudaError_t launch_gram_apply(osar_ctx* ctx, const double2* x, double2* y);
+cudaError_t launch_gram_expand(osar_ctx* ctx, int r0, int rows, double2* dense);
+cudaError_t launch_gram_entries(osar_ctx* ctx, const int2* rc, int count,
+                                double2* out);
+
+}  // namespace osar

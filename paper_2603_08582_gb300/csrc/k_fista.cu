@@ -1,0 +1,745 @@
+// Bandwidth-bound part of Online FISTA: the Hermitian Gram matvec on the
+// packed upper triangle, the fused Algorithm-1 step (gradient, step,
+// complex shrinkage, momentum, stop rule), the power iteration for L
+// (Eq. 11), the data-vector update of Eqs. 12-13 and lambda_n.
+//
+// Gram storage: the upper 128 x 128 blocks T_IJ = A[I-rows, J-cols], I <= J,
+// each stored column-major: entry (r, c) of the block sits at c * 128 + r.
+// Column-major blocks make the tensor-core epilogue (one TMEM lane = one row
+// per thread) write 256 contiguous bytes per warp instruction.
+//
+// Matvec: y = A x needs, for every stored block,
+//     y_I += T_IJ x_J      and, when I < J,      y_J += T_IJ^H x_I.
+// Work items ("segments") are runs of blocks I0..I1-1 of one block column J.
+// A CTA streams each block once from HBM; each warp owns 16 stored columns c,
+// each lane 4 consecutive rows r (one 32-byte sector per column):
+//   * y_J[c] = sum_r conj(T[r][c]) x_I[r] accumulates over the whole segment
+//     in registers and is reduced across lanes once at the end (segment
+//     partial); on a diagonal block (T Hermitian, stored in full) this alone
+//     is the block's product;
+//   * y_I[r] = sum_c T[r][c] x_J[c] is reduced across the 8 warps through
+//     shared memory per off-diagonal block (block partial).
+// A second kernel sums, per output block K, the segment partials of column K
+// and the block partials of (K, J), J > K (contiguous in the packed order),
+// then applies the elementwise step.  The partial traffic is ~1/64 of the
+// Gram's.  The last CTA of that grid (an atomic ticket after a fence) does
+// the scalar bookkeeping, so an inner step is two launches.  No floating-point
+// atomics: results are deterministic and checkpoints resume bit-for-bit.
+//
+// GB300 has very little FP64 throughput, so on the split-BF16 and FP32 paths
+// the partial sums stay in FP32 and only the per-coefficient step (and the
+// scalars t, L, lambda) run in FP64.
+#include "ctx.h"
+
+namespace osar {
+namespace {
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using T2 = float2;
+};
+template <>
+struct Vec<double> {
+  using T2 = double2;
+};
+
+// Four consecutive complex entries of one stored column (streamed once).
+__device__ __forceinline__ void load4(const float2* p, float2 (&g)[4]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  float4 a = __ldcs(q), b = __ldcs(q + 1);
+  g[0] = make_float2(a.x, a.y);
+  g[1] = make_float2(a.z, a.w);
+  g[2] = make_float2(b.x, b.y);
+  g[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4(const double2* p, double2 (&g)[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) g[c] = __ldcs(p + c);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2)
+    k_matvec(const typename Vec<T>::T2* __restrict__ G,
+             const typename Vec<T>::T2* __restrict__ x,
+             typename Vec<T>::T2* __restrict__ segpart,
+             typename Vec<T>::T2* __restrict__ tilepart,
+             const int4* __restrict__ segs, int nseg, int nb,
+             const DevScalars* __restrict__ sc, int gated) {
+  using T2 = typename Vec<T>::T2;
+  constexpr int RB = sizeof(T) == 4 ? 8 : 4;  // stored columns per load batch
+  if (gated && sc->converged) return;
+  __shared__ T2 xs[BLK];
+  __shared__ T2 red[8][BLK];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int s = blockIdx.x; s < nseg; s += gridDim.x) {
+    const int4 sg = segs[s];
+    const int J = sg.x;
+    __syncthreads();
+    if (threadIdx.x < BLK) xs[threadIdx.x] = x[J * BLK + threadIdx.x];
+    __syncthreads();
+    T br[16], bi[16];  // y_J partials of this warp's 16 columns
+#pragma unroll
+    for (int c = 0; c < 16; ++c) br[c] = bi[c] = T(0);
+    for (int I = sg.y; I < sg.z; ++I) {
+      const T2* blk = G + packed_block(I, J, nb) * (int64_t)(BLK * BLK) +
+                      (int64_t)(warp * 16) * BLK + lane * 4;
+      T2 xi[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xi[q] = x[I * BLK + lane * 4 + q];
+      T ar[4], ai[4];  // y_I partials of this lane's 4 rows
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ar[q] = ai[q] = T(0);
+#pragma unroll
+      for (int c0 = 0; c0 < 16; c0 += RB) {
+        T2 g[RB][4];
+#pragma unroll
+        for (int c = 0; c < RB; ++c) load4(blk + (int64_t)(c0 + c) * BLK, g[c]);
+#pragma unroll
+        for (int c = 0; c < RB; ++c) {
+          const T2 xj = xs[warp * 16 + c0 + c];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const T2 e = g[c][q];
+            // y_J[c] += conj(e) x_I[r]
+            br[c0 + c] = fma(e.x, xi[q].x, br[c0 + c]);
+            br[c0 + c] = fma(e.y, xi[q].y, br[c0 + c]);
+            bi[c0 + c] = fma(e.x, xi[q].y, bi[c0 + c]);
+            bi[c0 + c] = fma(-e.y, xi[q].x, bi[c0 + c]);
+            // y_I[r] += e x_J[c]
+            ar[q] = fma(e.x, xj.x, ar[q]);
+            ar[q] = fma(-e.y, xj.y, ar[q]);
+            ai[q] = fma(e.x, xj.y, ai[q]);
+            ai[q] = fma(e.y, xj.x, ai[q]);
+          }
+        }
+      }
+      if (I != J) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          T2 v;
+          v.x = ar[q];
+          v.y = ai[q];
+          red[warp][lane * 4 + q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < BLK) {
+          T sr = 0, si = 0;
+#pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            sr += red[w][threadIdx.x].x;
+            si += red[w][threadIdx.x].y;
+          }
+          T2 v;
+          v.x = sr;
+          v.y = si;
+          tilepart[packed_block(I, J, nb) * BLK + threadIdx.x] = v;
+        }
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      T vr = br[c], vi = bi[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, o);
+        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      }
+      if (lane == c) {
+        T2 v;
+        v.x = vr;
+        v.y = vi;
+        segpart[(int64_t)sg.w * BLK + warp * 16 + c] = v;
+      }
+    }
+  }
+}
+
+constexpr int FIN_GROUPS = 8;                  // partial-list splits per block
+constexpr int FIN_THREADS = FIN_GROUPS * BLK;  // 1024
+
+// y_K = sum of the segment partials of block column K and the block partials
+// of (K, J), J > K, accumulated in Acc (FP32 on the FP32-Gram paths).  The
+// partial list is split over FIN_GROUPS thread groups and the group sums are
+// combined in a fixed order.  Called by every thread; threads < BLK get the
+// sum for coefficient threadIdx.x.
+template <typename T2, typename Acc>
+__device__ __forceinline__ double2 gather_row(const T2* __restrict__ segpart,
+                                              const T2* __restrict__ tilepart,
+                                              const int* __restrict__ seg_begin,
+                                              int nb, int K) {
+  __shared__ Acc red_r[FIN_GROUPS][BLK], red_i[FIN_GROUPS][BLK];
+  const int g = threadIdx.x / BLK, i = threadIdx.x % BLK;
+  const int s0 = seg_begin[K], nseg = seg_begin[K + 1] - s0;
+  const int total = nseg + (nb - 1 - K);
+  const int64_t t0 = packed_block(K, K, nb) + 1;  // block (K, K+1)
+  Acc yr = 0, yi = 0;
+#pragma unroll 4
+  for (int q = g; q < total; q += FIN_GROUPS) {
+    const T2 v = q < nseg ? segpart[(int64_t)(s0 + q) * BLK + i]
+                          : tilepart[(t0 + (q - nseg)) * BLK + i];
+    yr += (Acc)v.x;
+    yi += (Acc)v.y;
+  }
+  red_r[g][i] = yr;
+  red_i[g][i] = yi;
+  __syncthreads();
+  double2 y = make_double2(0.0, 0.0);
+  if (threadIdx.x < BLK) {
+    Acc sr = 0, si = 0;
+#pragma unroll
+    for (int k = 0; k < FIN_GROUPS; ++k) {
+      sr += red_r[k][i];
+      si += red_i[k][i];
+    }
+    y = make_double2((double)sr, (double)si);
+  }
+  return y;
+}
+
+// Sum (a, b) over all threads of the block; thread 0 gets the total.
+__device__ __forceinline__ double2 block_sum(double a, double b) {
+  __shared__ double2 red[32];
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(a, b);
+  __syncthreads();
+  double2 t = make_double2(0, 0);
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t.x += red[w].x;
+      t.y += red[w].y;
+    }
+  }
+  return t;
+}
+
+// Ticket for the last CTA of a grid: thread 0 fences this CTA's published
+// results and takes a ticket; returns true (block-uniform) in the CTA that
+// finishes last, which then sees every other CTA's published result.
+__device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblocks) {
+  __shared__ int is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(counter, 1u) == nblocks - 1;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last != 0;
+}
+
+// Sum of the per-block (x, y) partials in a fixed order, by one block.
+__device__ __forceinline__ double2 sum_parts(const double2* part, int n) {
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double2 v = __ldcg(part + k);
+    a += v.x;
+    b += v.y;
+  }
+  return block_sum(a, b);
+}
+
+// One step of Algorithm 1 for the 128 coefficients of block K:
+//   g = A z - b,  u = z - tau g,  c = S_{lambda tau}(u),
+//   t' = (1 + sqrt(1 + 4 t^2)) / 2,  z' = c + (t - 1)/t' (c - c_prev).
+// The last CTA then sets t <- t', counts the step and applies the stop rule
+// |c - z|_2 <= tol |c|_2 to the whole vector.
+template <typename T2, typename Acc>
+__global__ void __launch_bounds__(FIN_THREADS)
+    k_fista_finalize(const T2* __restrict__ segpart,
+                     const T2* __restrict__ tilepart,
+                     const int* __restrict__ seg_begin, int nb,
+                     const double2* __restrict__ b, double2* __restrict__ c,
+                     double2* __restrict__ z, T2* __restrict__ zt,
+                     double2* __restrict__ part, DevScalars* sc) {
+  if (sc->converged) return;
+  const int K = blockIdx.x, i = threadIdx.x, idx = K * BLK + i;
+  const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
+  double p0 = 0.0, p1 = 0.0;
+  if (i < BLK) {
+    const double tau = sc->tau, lam = sc->lambda, t = sc->t;
+    const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    const double beta = (t - 1.0) / t_next;
+    const double2 zk = z[idx], bk = b[idx], cprev = c[idx];
+    const double ur = zk.x - tau * (y.x - bk.x);
+    const double ui = zk.y - tau * (y.y - bk.y);
+    const double mag = hypot(ur, ui);
+    const double alpha = lam * tau;
+    const double keep = mag > alpha ? 1.0 - alpha / mag : 0.0;
+    const double cr = ur * keep, ci = ui * keep;
+    const double2 zn = make_double2(cr + beta * (cr - cprev.x),
+                                    ci + beta * (ci - cprev.y));
+    c[idx] = make_double2(cr, ci);
+    z[idx] = zn;
+    T2 znt;
+    znt.x = zn.x;
+    znt.y = zn.y;
+    zt[idx] = znt;
+    const double dr = cr - zk.x, di = ci - zk.y;
+    p0 = dr * dr + di * di;
+    p1 = cr * cr + ci * ci;
+  }
+  const double2 s = block_sum(p0, p1);
+  if (i == 0) part[K] = s;
+  if (!last_block(&sc->done, gridDim.x)) return;
+  const double2 tot = sum_parts(part, nb);
+  if (i == 0) {
+    const double t = sc->t;
+    sc->t = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    sc->iters += 1;
+    if (sc->tol > 0.0 && sqrt(tot.x) <= sc->tol * sqrt(tot.y)) sc->converged = 1;
+    sc->done = 0;
+  }
+}
+
+// Power step: w = A v; the last CTA forms mu = Re(v^H A v) (v has unit norm),
+// normalises v <- w / |w|, and on the last step of a pulse sets
+// L_n = max(L_{n-1}, (1 + margin) mu) and tau = 1/L_n.
+template <typename T2, typename Acc>
+__global__ void __launch_bounds__(FIN_THREADS)
+    k_power_finalize(const T2* __restrict__ segpart,
+                     const T2* __restrict__ tilepart,
+                     const int* __restrict__ seg_begin, int nb,
+                     double2* __restrict__ v, T2* __restrict__ vt,
+                     double2* __restrict__ w, double2* __restrict__ part,
+                     DevScalars* sc, int last_step, double margin) {
+  const int K = blockIdx.x, i = threadIdx.x, idx = K * BLK + i;
+  const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
+  double p0 = 0.0, p1 = 0.0;
+  if (i < BLK) {
+    w[idx] = y;
+    const double2 vk = v[idx];
+    p0 = vk.x * y.x + vk.y * y.y;
+    p1 = y.x * y.x + y.y * y.y;
+  }
+  const double2 s = block_sum(p0, p1);
+  if (i == 0) part[K] = s;
+  if (!last_block(&sc->done, gridDim.x)) return;
+  const double2 tot = sum_parts(part, nb);
+  __shared__ double inv_s;
+  if (i == 0) {
+    const double mu = tot.x;
+    sc->mu = mu;
+    inv_s = tot.y > 0.0 ? 1.0 / sqrt(tot.y) : 0.0;
+    sc->inv_norm = inv_s;
+    if (last_step) {
+      const double l = (1.0 + margin) * mu;
+      if (l > sc->lip) sc->lip = l;
+      sc->tau = sc->lip > 0.0 ? 1.0 / sc->lip : 0.0;
+    }
+    sc->done = 0;
+  }
+  __syncthreads();
+  const double inv = inv_s;
+  if (inv > 0.0) {
+    for (int k = i; k < nb * BLK; k += blockDim.x) {
+      const double2 yw = __ldcg(w + k);
+      const double2 nv = make_double2(yw.x * inv, yw.y * inv);
+      v[k] = nv;
+      T2 t;
+      t.x = nv.x;
+      t.y = nv.y;
+      vt[k] = t;
+    }
+  }
+}
+
+// y = A x for osar_gram_apply.
+template <typename T2, typename Acc>
+__global__ void __launch_bounds__(FIN_THREADS)
+    k_apply_finalize(const T2* __restrict__ segpart,
+                     const T2* __restrict__ tilepart,
+                     const int* __restrict__ seg_begin, int nb,
+                     double2* __restrict__ y) {
+  const int K = blockIdx.x, i = threadIdx.x;
+  const double2 v = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
+  if (i < BLK) y[K * BLK + i] = v;
+}
+
+// ------------------------------------------------------- data vector, lambda
+// The last CTA of a data-update grid sets lambda_n = rel * max_j |b_j| (or
+// the absolute value) and counts the pulse.
+__device__ __forceinline__ void lambda_tail(double local_max2, double* bmax,
+                                            DevScalars* sc, double lam,
+                                            int relative) {
+  __shared__ double red[32];
+  double m = local_max2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t = fmax(t, red[w2]);
+    bmax[blockIdx.x] = t;
+  }
+  if (!last_block(&sc->done, gridDim.x)) return;
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
+    mx = fmax(mx, __ldcg(bmax + k));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t = fmax(t, red[w2]);
+    sc->lambda = relative ? lam * sqrt(t) : lam;
+    sc->n += 1;
+    sc->done = 0;
+  }
+}
+
+// b_j += sum_m conj(A[j][m]) d_m (Eqs. 12-13), one warp per atom j.
+template <typename T2>
+__global__ void __launch_bounds__(256)
+    k_data_update_complex(const T2* __restrict__ A, int Mp, int Kp,
+                          const double2* __restrict__ d, double2* __restrict__ b,
+                          double* bmax, DevScalars* sc, double lam,
+                          int relative) {
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  double m2 = 0.0;
+  if (j < Mp) {
+    const T2* row = A + (int64_t)j * Kp;
+    double sr = 0.0, si = 0.0;
+    for (int m = lane; m < Kp; m += 32) {
+      const T2 a = row[m];
+      const double2 dm = d[m];
+      sr += (double)a.x * dm.x + (double)a.y * dm.y;
+      si += (double)a.x * dm.y - (double)a.y * dm.x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      const double2 bj = b[j];
+      const double2 nb2 = make_double2(bj.x + sr, bj.y + si);
+      b[j] = nb2;
+      m2 = nb2.x * nb2.x + nb2.y * nb2.y;
+    }
+  }
+  lambda_tail(m2, bmax, sc, lam, relative);
+}
+
+// Split-BF16 planes: A = (re_hi + re_lo) + i (im_hi + im_lo), FP32 products
+// and sums (8 entries per lane per load), one FP64 add into b_j per atom.
+__global__ void __launch_bounds__(256)
+    k_data_update_planes(const __nv_bfloat16* __restrict__ Ap, int Mp, int Kp,
+                         const float2* __restrict__ d, double2* __restrict__ b,
+                         double* bmax, DevScalars* sc, double lam,
+                         int relative) {
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  double m2 = 0.0;
+  if (j < Mp) {
+    const int64_t plane = (int64_t)Mp * Kp;
+    const __nv_bfloat16* rh = Ap + (int64_t)j * Kp;
+    float sr = 0.f, si = 0.f;
+    for (int m0 = lane * 8; m0 < Kp; m0 += 256) {
+      const uint4 vrh = *reinterpret_cast<const uint4*>(rh + m0);
+      const uint4 vih = *reinterpret_cast<const uint4*>(rh + plane + m0);
+      const uint4 vrl = *reinterpret_cast<const uint4*>(rh + 3 * plane + m0);
+      const uint4 vil = *reinterpret_cast<const uint4*>(rh + 4 * plane + m0);
+      const __nv_bfloat16* prh = reinterpret_cast<const __nv_bfloat16*>(&vrh);
+      const __nv_bfloat16* pih = reinterpret_cast<const __nv_bfloat16*>(&vih);
+      const __nv_bfloat16* prl = reinterpret_cast<const __nv_bfloat16*>(&vrl);
+      const __nv_bfloat16* pil = reinterpret_cast<const __nv_bfloat16*>(&vil);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float ar = __bfloat162float(prh[q]) + __bfloat162float(prl[q]);
+        const float ai = __bfloat162float(pih[q]) + __bfloat162float(pil[q]);
+        const float2 dm = d[m0 + q];
+        sr = fmaf(ar, dm.x, fmaf(ai, dm.y, sr));
+        si = fmaf(ar, dm.y, fmaf(-ai, dm.x, si));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      const double2 bj = b[j];
+      const double2 nb2 = make_double2(bj.x + (double)sr, bj.y + (double)si);
+      b[j] = nb2;
+      m2 = nb2.x * nb2.x + nb2.y * nb2.y;
+    }
+  }
+  lambda_tail(m2, bmax, sc, lam, relative);
+}
+
+__global__ void k_stage_data(const double2* __restrict__ d,
+                             float2* __restrict__ d32, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d32[i] = make_float2((float)d[i].x, (float)d[i].y);
+}
+
+// Start of a burst (Algorithm 1 initialisation): z^(1) = c^(0) = c_hat_{n-1},
+// t_1 = 1 at the first pulse (or always, with restart), else t_{n-1}.
+template <typename T2>
+__global__ void k_burst_begin(double2* __restrict__ z, T2* __restrict__ zt,
+                              const double2* __restrict__ c, int n,
+                              DevScalars* sc, int reset_t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 v = c[i];
+    z[i] = v;
+    T2 t;
+    t.x = v.x;
+    t.y = v.y;
+    zt[i] = t;
+  }
+  if (i == 0) {
+    if (reset_t) sc->t = 1.0;
+    sc->converged = 0;
+  }
+}
+
+__global__ void k_iter_begin(DevScalars* sc, double tol) {
+  sc->iters = 0;
+  sc->tol = tol;
+}
+
+template <typename T2>
+__global__ void k_to_working(const double2* __restrict__ x, T2* __restrict__ xt,
+                             int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    T2 t;
+    t.x = x[i].x;
+    t.y = x[i].y;
+    xt[i] = t;
+  }
+}
+
+// Offset of Gram entry (i, j) in the packed, column-major blocks; entries
+// below the diagonal are read from their mirror (upper = false: conjugate).
+__device__ __forceinline__ int64_t stored_index(int i, int j, int nb,
+                                                bool* upper) {
+  *upper = i <= j;
+  const int a = *upper ? i : j, c = *upper ? j : i;
+  return packed_block(a / BLK, c / BLK, nb) * (int64_t)(BLK * BLK) +
+         (int64_t)(c % BLK) * BLK + (a % BLK);
+}
+
+// Dense rows [r0, r0 + rows) of the Hermitian Gram (M columns), from the
+// packed upper blocks plus the optional compensation word.
+template <typename T2>
+__global__ void k_gram_expand(const T2* __restrict__ G,
+                              const float2* __restrict__ Glo, int nb, int M,
+                              int r0, int rows, double2* __restrict__ out) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)rows * M) return;
+  const int i = r0 + (int)(gid / M);
+  const int j = (int)(gid - (int64_t)(gid / M) * M);
+  bool upper;
+  const int64_t o = stored_index(i, j, nb, &upper);
+  double re = (double)G[o].x, im = (double)G[o].y;
+  if (Glo) {
+    re += (double)Glo[o].x;
+    im += (double)Glo[o].y;
+  }
+  out[gid] = make_double2(re, upper ? im : -im);
+}
+
+template <typename T2>
+__global__ void k_gram_entries(const T2* __restrict__ G,
+                               const float2* __restrict__ Glo, int nb,
+                               const int2* __restrict__ rc, int count,
+                               double2* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  bool upper;
+  const int64_t o = stored_index(rc[q].x, rc[q].y, nb, &upper);
+  double re = (double)G[o].x, im = (double)G[o].y;
+  if (Glo) {
+    re += (double)Glo[o].x;
+    im += (double)Glo[o].y;
+  }
+  out[q] = make_double2(re, upper ? im : -im);
+}
+
+unsigned grid_matvec(const osar_ctx* ctx) {
+  int g = 2 * ctx->sm_count;
+  return (unsigned)(ctx->nseg < g ? ctx->nseg : g);
+}
+
+// Launch the matvec on the working-precision copy of a vector.
+void matvec(osar_ctx* ctx, const void* xt, int gated) {
+  ProfEvent ev;
+  prof_begin(ctx, KCL_MATVEC, &ev);
+  if (ctx->prec == OSAR_FP64)
+    k_matvec<double><<<grid_matvec(ctx), 256, 0, ctx->stream>>>(
+        (const double2*)ctx->g_hi, (const double2*)xt, (double2*)ctx->segpart,
+        (double2*)ctx->tilepart, ctx->segs, ctx->nseg, ctx->nb, ctx->scal,
+        gated);
+  else
+    k_matvec<float><<<grid_matvec(ctx), 256, 0, ctx->stream>>>(
+        (const float2*)ctx->g_hi, (const float2*)xt, (float2*)ctx->segpart,
+        (float2*)ctx->tilepart, ctx->segs, ctx->nseg, ctx->nb, ctx->scal,
+        gated);
+  prof_end(ctx, &ev);
+  ctx->launches++;
+}
+
+}  // namespace
+
+cudaError_t launch_data_update(osar_ctx* ctx) {
+  ProfEvent ev;
+  prof_begin(ctx, KCL_BUPD, &ev);
+  const unsigned g = (unsigned)((ctx->Mp + 7) / 8);
+  const double lam = ctx->cfg.lambda;
+  const int rel = ctx->cfg.lambda_relative;
+  if (ctx->prec == OSAR_SPLIT_BF16) {
+    k_stage_data<<<(unsigned)((ctx->Kp + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->d_dev, ctx->d32, ctx->Kp);
+    k_data_update_planes<<<g, 256, 0, ctx->stream>>>(
+        ctx->Apl, ctx->Mp, ctx->Kp, ctx->d32, ctx->b, ctx->bmax, ctx->scal,
+        lam, rel);
+    ctx->launches++;
+  } else if (ctx->prec == OSAR_FP64) {
+    k_data_update_complex<double2><<<g, 256, 0, ctx->stream>>>(
+        (const double2*)ctx->A, ctx->Mp, ctx->Kp, ctx->d_dev, ctx->b, ctx->bmax,
+        ctx->scal, lam, rel);
+  } else {
+    k_data_update_complex<float2><<<g, 256, 0, ctx->stream>>>(
+        (const float2*)ctx->A, ctx->Mp, ctx->Kp, ctx->d_dev, ctx->b, ctx->bmax,
+        ctx->scal, lam, rel);
+  }
+  prof_end(ctx, &ev);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_power_steps(osar_ctx* ctx, int steps) {
+  const unsigned nb = (unsigned)ctx->nb;
+  for (int s = 0; s < steps; ++s) {
+    matvec(ctx, ctx->vt, 0);
+    ProfEvent ev;
+    prof_begin(ctx, KCL_POWFIN, &ev);
+    const int last = s == steps - 1 ? 1 : 0;
+    if (ctx->prec == OSAR_FP64)
+      k_power_finalize<double2, double><<<nb, FIN_THREADS, 0, ctx->stream>>>(
+          (const double2*)ctx->segpart, (const double2*)ctx->tilepart,
+          ctx->seg_begin, ctx->nb, ctx->v, (double2*)ctx->vt, ctx->w, ctx->part,
+          ctx->scal, last, ctx->cfg.lipschitz_margin);
+    else
+      k_power_finalize<float2, float><<<nb, FIN_THREADS, 0, ctx->stream>>>(
+          (const float2*)ctx->segpart, (const float2*)ctx->tilepart,
+          ctx->seg_begin, ctx->nb, ctx->v, (float2*)ctx->vt, ctx->w, ctx->part,
+          ctx->scal, last, ctx->cfg.lipschitz_margin);
+    prof_end(ctx, &ev);
+    ctx->launches++;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_burst_begin(osar_ctx* ctx) {
+  const bool reset = ctx->n == 1 || ctx->cfg.restart_momentum;
+  if (ctx->prec == OSAR_FP64)
+    k_burst_begin<double2><<<(unsigned)ctx->nb, 128, 0, ctx->stream>>>(
+        ctx->z, (double2*)ctx->zt, ctx->c, ctx->Mp, ctx->scal, reset ? 1 : 0);
+  else
+    k_burst_begin<float2><<<(unsigned)ctx->nb, 128, 0, ctx->stream>>>(
+        ctx->z, (float2*)ctx->zt, ctx->c, ctx->Mp, ctx->scal, reset ? 1 : 0);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iter_begin(osar_ctx* ctx, double tol) {
+  k_iter_begin<<<1, 1, 0, ctx->stream>>>(ctx->scal, tol);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fista_step(osar_ctx* ctx) {
+  matvec(ctx, ctx->zt, 1);
+  ProfEvent ev;
+  prof_begin(ctx, KCL_FIN, &ev);
+  if (ctx->prec == OSAR_FP64)
+    k_fista_finalize<double2, double><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
+        (const double2*)ctx->segpart, (const double2*)ctx->tilepart,
+        ctx->seg_begin, ctx->nb, ctx->b, ctx->c, ctx->z, (double2*)ctx->zt,
+        ctx->part, ctx->scal);
+  else
+    k_fista_finalize<float2, float><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
+        (const float2*)ctx->segpart, (const float2*)ctx->tilepart,
+        ctx->seg_begin, ctx->nb, ctx->b, ctx->c, ctx->z, (float2*)ctx->zt,
+        ctx->part, ctx->scal);
+  prof_end(ctx, &ev);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_apply(osar_ctx* ctx, const double2* x, double2* y) {
+  const unsigned g = (unsigned)((ctx->Mp + 255) / 256);
+  if (ctx->prec == OSAR_FP64)
+    k_to_working<double2><<<g, 256, 0, ctx->stream>>>(x, (double2*)ctx->xt, ctx->Mp);
+  else
+    k_to_working<float2><<<g, 256, 0, ctx->stream>>>(x, (float2*)ctx->xt, ctx->Mp);
+  matvec(ctx, ctx->xt, 0);
+  if (ctx->prec == OSAR_FP64)
+    k_apply_finalize<double2, double><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
+        (const double2*)ctx->segpart, (const double2*)ctx->tilepart,
+        ctx->seg_begin, ctx->nb, y);
+  else
+    k_apply_finalize<float2, float><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
+        (const float2*)ctx->segpart, (const float2*)ctx->tilepart,
+        ctx->seg_begin, ctx->nb, y);
+  ctx->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_working(osar_ctx* ctx) {
+  // working-precision copies of z and v (after a checkpoint load)
+  const unsigned g = (unsigned)((ctx->Mp + 255) / 256);
+  if (ctx->prec == OSAR_FP64) {
+    k_to_working<double2><<<g, 256, 0, ctx->stream>>>(ctx->z, (double2*)ctx->zt, ctx->Mp);
+    k_to_working<double2><<<g, 256, 0, ctx->stream>>>(ctx->v, (double2*)ctx->vt, ctx->Mp);
+  } else {
+    k_to_working<float2><<<g, 256, 0, ctx->stream>>>(ctx->z, (float2*)ctx->zt, ctx->Mp);
+    k_to_working<float2><<<g, 256, 0, ctx->stream>>>(ctx->v, (float2*)ctx->vt, ctx->Mp);
+  }
+  ctx->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_expand(osar_ctx* ctx, int r0, int rows, double2* dense) {
+  const int64_t n = (int64_t)rows * ctx->M;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  if (ctx->prec == OSAR_FP64)
+    k_gram_expand<double2><<<g, 256, 0, ctx->stream>>>(
+        (const double2*)ctx->g_hi, nullptr, ctx->nb, ctx->M, r0, rows, dense);
+  else
+    k_gram_expand<float2><<<g, 256, 0, ctx->stream>>>(
+        (const float2*)ctx->g_hi, ctx->g_lo, ctx->nb, ctx->M, r0, rows, dense);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_entries(osar_ctx* ctx, const int2* rc, int count,
+                                double2* out) {
+  const unsigned g = (unsigned)((count + 255) / 256);
+  if (ctx->prec == OSAR_FP64)
+    k_gram_entries<double2><<<g, 256, 0, ctx->stream>>>(
+        (const double2*)ctx->g_hi, nullptr, ctx->nb, rc, count, out);
+  else
+    k_gram_entries<float2><<<g, 256, 0, ctx->stream>>>(
+        (const float2*)ctx->g_hi, ctx->g_lo, ctx->nb, rc, count, out);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace osar

@@ -1,0 +1,490 @@
+// Split-BF16 complex GEMM on tcgen05 tensor cores (sm_103a), used for the
+// dictionary apply (Eq. 6) and the Gram update (Eqs. 12-13).
+//
+// Each complex operand is stored as bf16 planes [plane][row][k]:
+//   block / Gram operand (6 planes): re_hi, im_hi, -re_hi, re_lo, im_lo, -re_lo
+//   dictionary operand   (4 planes): re_hi, im_hi, re_lo, im_lo
+// with x = hi + lo, hi = rn_bf16(x), lo = rn_bf16(x - hi).  A 128 x 128
+// complex output tile C = sum_k op(P)[i][k] Q[j][k] is one real GEMM of
+// M = 128, N = 256, K = 2 Kc whose N axis stacks [real part | imaginary part]:
+//
+//   first half of K  (A = P_re):  B rows = [Q_re ; Q_im]
+//   second half of K (A = P_im):  B rows = [Q_im ; -Q_re]
+//
+// which accumulates  [Re | Im] = [P_re Q_re + P_im Q_im | P_re Q_im - P_im Q_re]
+// = conj(P) Q  (Gram), or, with the A operand negated in the second half,
+// [P_re Q_re - P_im Q_im | P_re Q_im + P_im Q_re] = P Q  (dictionary).  The
+// B operand of each half is one 3-D TMA box spanning two adjacent planes.
+// Three products per chunk (hi*hi, hi*lo, lo*hi) run on the tensor pipe with
+// FP32 accumulation in tensor memory.
+//
+// Kernel structure (persistent, one CTA per SM, 320 threads):
+//   warp 0  TMA producer: 4-stage ring of 48 KB stages (A hi/lo, B hi/lo).
+//   warp 1  TMEM allocation and the single-thread MMA issuer.
+//   warps 2-9  epilogue: two warps per TMEM lane quarter, each owning 64 of
+//           the 128 output columns, read the 128 x 256 fp32 accumulator in
+//           16-column pieces (tcgen05.ld) and either store an FP32 partial
+//           (dictionary) or apply a TwoSum read-modify-write to the packed
+//           Gram block (hi, lo), which is stored column-major so that a warp
+//           (32 consecutive rows) reads and writes 256 contiguous bytes per
+//           access.  The Gram words of the next piece are loaded before the
+//           current one is processed (~64 KB in flight per SM).
+// The accumulator is double-buffered (2 x 256 TMEM columns) so the epilogue
+// of tile t overlaps the MMAs of tile t+1.
+//
+// Accumulation in the tensor pipe rounds its FP32 partial sums toward zero,
+// which biases long reductions (|A| shrinks by ~(steps) 2^-24).  The
+// dictionary reduction runs over N = 16384 pixels, so it is split into
+// slices of at most 4096 pixels (split-K); each slice writes an FP32 partial
+// and a small kernel sums the slices with round-to-nearest before the bf16
+// split.  The Gram reduction (2K <= 2048 terms) stays in one accumulator.  Every mbarrier wait is bounded
+// (2 s); a timeout sets the device error word, stops the other roles, drains
+// in-flight TMA loads and MMAs, and frees TMEM before the kernel returns.
+#include <cudaTypedefs.h>
+
+#include "ctx.h"
+
+namespace osar {
+namespace {
+
+constexpr int TC_STAGES = 4;
+constexpr int TILE_A_BYTES = BLK * KC * 2;        // 128 rows x 64 B
+constexpr int TILE_B_BYTES = 2 * BLK * KC * 2;    // 256 rows x 64 B
+constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + 2 * TILE_B_BYTES;  // 48 KB
+constexpr int TC_THREADS = 320;
+constexpr int EPI_THREADS = 256;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int TC_SMEM = TC_STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+
+struct TcParams {
+  const int2* tiles;  // (row block, column block | slice << 16)
+  int n_tiles;
+  int k_chunks;    // KC chunks per half of the reduction (whole K)
+  int k_slice;     // KC chunks per half handled by one tile
+  int a_lo;        // plane offset of the lo part on the A side
+  int b_lo;        // plane offset of the lo part on the B side
+  int neg_second;  // negate A in the second half (plain product P Q)
+  int mode;        // 0: FP32 partial output, 1: packed Gram update
+  float2* part;    // mode 0: [slice][rows][part_ld] partial sums
+  int part_ld;
+  int64_t part_slice;
+  float2* g_hi;
+  float2* g_lo;
+  int nb;
+  int* err;
+};
+
+// One 16-column piece of the Gram read-modify-write for this thread's row:
+// (hi, lo) += delta with an error-free TwoSum.  Blocks are column-major, so
+// entry (row, c) is at c * 128 + row and the 32 lanes of a warp (32
+// consecutive rows) touch 256 contiguous bytes per access.
+__device__ __forceinline__ void gram_piece(float2* gh, float2* gl,
+                                           const float2 (&h)[16],
+                                           const float2 (&l)[16],
+                                           const float* re, const float* im,
+                                           bool comp) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    float2 hv = h[q];
+    if (comp) {
+      float2 lv = l[q];
+      float s, e;
+      two_sum(hv.x, __fadd_rn(re[q], lv.x), s, e);
+      hv.x = s;
+      lv.x = e;
+      two_sum(hv.y, __fadd_rn(im[q], lv.y), s, e);
+      hv.y = s;
+      lv.y = e;
+      gl[q * BLK] = lv;
+    } else {
+      hv.x += re[q];
+      hv.y += im[q];
+    }
+    gh[q * BLK] = hv;
+  }
+}
+
+__device__ __forceinline__ void load_piece(const float2* gh, const float2* gl,
+                                           float2 (&h)[16], float2 (&l)[16],
+                                           bool comp) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) h[q] = gh[q * BLK];
+  if (comp) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) l[q] = gl[q * BLK];
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_cgemm(const __grid_constant__ CUtensorMap mapA,
+               const __grid_constant__ CUtensorMap mapB, const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE_BYTES);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* tfull = empty + TC_STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EPI_THREADS);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    fence_proxy_async();
+    tma_prefetch_desc(&mapA);
+    tma_prefetch_desc(&mapB);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int total_k = 2 * p.k_slice;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------ TMA producer
+      uint32_t issued[TC_STAGES];
+      for (int s = 0; s < TC_STAGES; ++s) issued[s] = 0;
+      int stage = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x) {
+        const int2 tile = p.tiles[t];
+        const int ra = tile.x * BLK, rb = (tile.y & 0xFFFF) * BLK;
+        const int k0 = (tile.y >> 16) * p.k_slice;
+        for (int kc = 0; kc < total_k; ++kc) {
+          if (!mbar_wait_bounded(&empty[stage], ph ^ 1, abort_flag, p.err,
+                                 WAIT_LIMIT_NS)) {
+            ok = false;
+            break;
+          }
+          const int half = kc >= p.k_slice ? 1 : 0;
+          const int k = (k0 + kc - half * p.k_slice) * KC;
+          uint8_t* sb = smem + stage * STAGE_BYTES;
+          mbar_expect_tx(&full[stage], STAGE_BYTES);
+          tma_load_3d(sb, &mapA, &full[stage], k, ra, half);
+          tma_load_3d(sb + TILE_A_BYTES, &mapA, &full[stage], k, ra,
+                      half + p.a_lo);
+          tma_load_3d(sb + 2 * TILE_A_BYTES, &mapB, &full[stage], k, rb, half);
+          tma_load_3d(sb + 2 * TILE_A_BYTES + TILE_B_BYTES, &mapB, &full[stage],
+                      k, rb, half + p.b_lo);
+          issued[stage]++;
+          if (++stage == TC_STAGES) {
+            stage = 0;
+            ph ^= 1;
+          }
+        }
+      }
+      // Drain: every load this thread issued must land before the CTA exits.
+      volatile int no_abort = 0;
+      for (int s = 0; s < TC_STAGES; ++s)
+        if (issued[s])
+          mbar_wait_bounded(&full[s], (issued[s] - 1) & 1, &no_abort, p.err,
+                            WAIT_LIMIT_NS);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // -------------------------------------------------------- MMA issuer
+      const uint32_t id_pos = idesc_bf16_f32(128, 256, false);
+      const uint32_t id_neg = idesc_bf16_f32(128, 256, true);
+      int stage = 0, acc = 0;
+      uint32_t ph = 0, aph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x) {
+        if (!mbar_wait_bounded(&tempty[acc], aph ^ 1, abort_flag, p.err,
+                               WAIT_LIMIT_NS)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)acc * 256u;
+        for (int kc = 0; kc < total_k; ++kc) {
+          if (!mbar_wait_bounded(&full[stage], ph, abort_flag, p.err,
+                                 WAIT_LIMIT_NS)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int half = kc >= p.k_slice ? 1 : 0;
+          const uint32_t id = (half && p.neg_second) ? id_neg : id_pos;
+          const uint32_t a_hi = smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t a_lo = a_hi + TILE_A_BYTES;
+          const uint32_t b_hi = a_hi + 2 * TILE_A_BYTES;
+          const uint32_t b_lo = b_hi + TILE_B_BYTES;
+#pragma unroll
+          for (int k16 = 0; k16 < KC / 16; ++k16) {
+            const uint32_t o = (uint32_t)k16 * 32u;
+            const uint64_t dah = smem_desc_sw64(a_hi + o);
+            const uint64_t dal = smem_desc_sw64(a_lo + o);
+            const uint64_t dbh = smem_desc_sw64(b_hi + o);
+            const uint64_t dbl = smem_desc_sw64(b_lo + o);
+            tc_mma_f16(d, dah, dbh, id, (kc | k16) != 0 ? 1u : 0u);
+            tc_mma_f16(d, dah, dbl, id, 1u);
+            tc_mma_f16(d, dal, dbh, id, 1u);
+          }
+          tc_commit(&empty[stage]);
+          if (++stage == TC_STAGES) {
+            stage = 0;
+            ph ^= 1;
+          }
+        }
+        if (!ok) break;
+        tc_commit(&tfull[acc]);
+        acc ^= 1;
+        if (acc == 0) aph ^= 1;
+      }
+      // Drain: all MMAs issued by this thread complete before TMEM is freed.
+      tc_commit(drain);
+      volatile int no_abort = 0;
+      mbar_wait_bounded(drain, 0, &no_abort, p.err, WAIT_LIMIT_NS);
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;             // TMEM lane quarter this warp may access
+    const int colh = (warp - 2) >> 2;   // which 64-column half of the tile
+    const int row = q * 32 + lane;
+    const bool comp = p.g_lo != nullptr;
+    int acc = 0;
+    uint32_t aph = 0;
+    for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
+      const int2 tile = p.tiles[t];
+      const int tj = tile.y & 0xFFFF, slice = tile.y >> 16;
+      float2 h0[16], l0[16], h1[16], l1[16];
+      float2* gh = nullptr;
+      float2* gl = nullptr;
+      if (p.mode == 1) {
+        const int64_t off = packed_block(tile.x, tj, p.nb) * (int64_t)(BLK * BLK) +
+                            (int64_t)(colh * 64) * BLK + row;
+        gh = p.g_hi + off;
+        gl = comp ? p.g_lo + off : nullptr;
+        load_piece(gh, gl, h0, l0, comp);  // prefetch before the MMAs finish
+      }
+      if (!mbar_wait_bounded(&tfull[acc], aph, abort_flag, p.err,
+                             WAIT_LIMIT_NS))
+        break;
+      __syncwarp();
+      tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) +
+                            (uint32_t)acc * 256u + (uint32_t)colh * 64u;
+#pragma unroll
+      for (int pc = 0; pc < 4; ++pc) {
+        float re[16], im[16];
+        tmem_ld16(base + (uint32_t)(pc * 16), re);
+        tmem_ld16(base + 128u + (uint32_t)(pc * 16), im);
+        if (p.mode == 1 && pc < 3) {
+          const int64_t nxt = (int64_t)(16 * (pc + 1)) * BLK;
+          if (pc & 1)
+            load_piece(gh + nxt, comp ? gl + nxt : nullptr, h0, l0, comp);
+          else
+            load_piece(gh + nxt, comp ? gl + nxt : nullptr, h1, l1, comp);
+        }
+        tmem_wait_ld();
+        if (p.mode == 1) {
+          const int64_t cur = (int64_t)(16 * pc) * BLK;
+          if (pc & 1)
+            gram_piece(gh + cur, comp ? gl + cur : nullptr, h1, l1, re, im, comp);
+          else
+            gram_piece(gh + cur, comp ? gl + cur : nullptr, h0, l0, re, im, comp);
+        } else {
+          float4* dst = reinterpret_cast<float4*>(
+              p.part + slice * p.part_slice +
+              (int64_t)(tile.x * BLK + row) * p.part_ld + tj * BLK + colh * 64 +
+              pc * 16);
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            dst[c] = make_float4(re[2 * c], im[2 * c], re[2 * c + 1], im[2 * c + 1]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+      acc ^= 1;
+      if (acc == 0) aph ^= 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// Sum the split-K slices of the dictionary product (round-to-nearest FP32,
+// fixed order) and write the six bf16 planes of the forward block.
+__global__ void k_dict_reduce(const float2* __restrict__ part, int slices,
+                              int64_t slice_stride, int64_t groups,
+                              __nv_bfloat16* __restrict__ planes,
+                              int64_t plane) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= groups) return;
+  const int64_t off = g * 8;
+  float re[8], im[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) re[q] = im[q] = 0.f;
+  for (int s = 0; s < slices; ++s) {
+    const float4* src = reinterpret_cast<const float4*>(part + s * slice_stride + off);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float4 v = __ldcs(src + c);
+      re[2 * c] += v.x;
+      im[2 * c] += v.y;
+      re[2 * c + 1] += v.z;
+      im[2 * c + 1] += v.w;
+    }
+  }
+  __align__(16) __nv_bfloat16 v[6][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    split_bf16(re[q], v[0][q], v[3][q]);
+    split_bf16(im[q], v[1][q], v[4][q]);
+    split_bf16(-re[q], v[2][q], v[5][q]);
+  }
+#pragma unroll
+  for (int pl = 0; pl < 6; ++pl)
+    *reinterpret_cast<uint4*>(planes + pl * plane + off) =
+        *reinterpret_cast<const uint4*>(v[pl]);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                         cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+bool encode_planes(CUtensorMap* m, void* base, int cols, int rows, int planes,
+                   int box_planes, std::string* err) {
+  auto fn = encode_fn();
+  if (!fn) {
+    *err = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)cols * 2,
+                           (cuuint64_t)cols * (cuuint64_t)rows * 2};
+  cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)BLK, (cuuint32_t)box_planes};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+    return false;
+  }
+  return true;
+}
+
+cudaError_t launch_tc(osar_ctx* ctx, const CUtensorMap& ma,
+                      const CUtensorMap& mb, const TcParams& p, int kind) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(
+        k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int grid = p.n_tiles < ctx->sm_count ? p.n_tiles : ctx->sm_count;
+  if (grid <= 0) return cudaSuccess;
+  ProfEvent ev;
+  prof_begin(ctx, kind, &ev);
+  k_tc_cgemm<<<grid, TC_THREADS, TC_SMEM, ctx->stream>>>(ma, mb, p);
+  prof_end(ctx, &ev);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool make_tensor_maps(osar_ctx* ctx, std::string* err) {
+  if (!encode_planes(&ctx->map_a_rows1, ctx->Apl, ctx->Kp, ctx->Mp, 6, 1, err))
+    return false;
+  if (!encode_planes(&ctx->map_a_rows2, ctx->Apl, ctx->Kp, ctx->Mp, 6, 2, err))
+    return false;
+  if (ctx->dict) {
+    if (!encode_planes(&ctx->map_d_rows1, ctx->Dpl, ctx->Np, ctx->Mp, 4, 1, err))
+      return false;
+    if (!encode_planes(&ctx->map_f_rows2, ctx->Fpl, ctx->Np, ctx->Kp, 6, 2, err))
+      return false;
+  }
+  return true;
+}
+
+int dict_slices(int np) {
+  const int chunks = np / KC;
+  int s = 1;
+  while (chunks % (2 * s) == 0 && chunks / (2 * s) >= 4096 / KC) s *= 2;
+  return s;
+}
+
+cudaError_t launch_dict_tc(osar_ctx* ctx) {
+  TcParams p = {};
+  p.tiles = ctx->dict_tiles;
+  p.n_tiles = ctx->n_dict_tiles;
+  p.k_chunks = ctx->Np / KC;
+  p.k_slice = p.k_chunks / ctx->dict_slices;
+  p.a_lo = 2;
+  p.b_lo = 3;
+  p.neg_second = 1;
+  p.mode = 0;
+  p.part = ctx->dict_part;
+  p.part_ld = ctx->Kp;
+  p.part_slice = (int64_t)ctx->Mp * ctx->Kp;
+  p.nb = ctx->nb;
+  p.err = &ctx->scal->error;
+  cudaError_t e = launch_tc(ctx, ctx->map_d_rows1, ctx->map_f_rows2, p, KCL_DICT);
+  if (e != cudaSuccess) return e;
+  const int64_t groups = (int64_t)ctx->Mp * ctx->Kp / 8;
+  ProfEvent ev;
+  prof_begin(ctx, KCL_DICT, &ev);
+  k_dict_reduce<<<(unsigned)((groups + 255) / 256), 256, 0, ctx->stream>>>(
+      ctx->dict_part, ctx->dict_slices, p.part_slice, groups, ctx->Apl,
+      p.part_slice);
+  prof_end(ctx, &ev);
+  ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc(osar_ctx* ctx) {
+  TcParams p = {};
+  p.tiles = ctx->gram_tiles;
+  p.n_tiles = (int)ctx->nblk;
+  p.k_chunks = ctx->Kp / KC;
+  p.k_slice = p.k_chunks;
+  p.a_lo = 3;
+  p.b_lo = 3;
+  p.neg_second = 0;
+  p.mode = 1;
+  p.g_hi = (float2*)ctx->g_hi;
+  p.g_lo = ctx->g_lo;
+  p.nb = ctx->nb;
+  p.err = &ctx->scal->error;
+  return launch_tc(ctx, ctx->map_a_rows1, ctx->map_a_rows2, p, KCL_GRAM);
+}
+
+}  // namespace osar

@@ -1,0 +1,810 @@
+// libosar C ABI: context management and the per-pulse / per-burst call
+// sequences of Online FISTA (Eqs. 12-13 and Algorithm 1).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace osar;
+
+namespace {
+
+constexpr int RING = osar_ctx::RING;
+
+thread_local std::string g_create_error;
+
+osar_status fail(osar_ctx* ctx, osar_status st, const std::string& msg) {
+  if (ctx) {
+    ctx->last_error = msg;
+    if (st == OSAR_E_CUDA) ctx->sticky = OSAR_E_CUDA;
+  } else {
+    g_create_error = msg;
+  }
+  return st;
+}
+
+osar_status cuda_fail(osar_ctx* ctx, cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                    cudaGetErrorString(e) + ")";
+  return fail(ctx, e == cudaErrorMemoryAllocation ? OSAR_E_OOM : OSAR_E_CUDA,
+              msg);
+}
+
+#define CK(ctx, expr)                                    \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #expr); \
+  } while (0)
+
+int64_t roundup(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+template <typename T>
+osar_status dev_alloc(osar_ctx* ctx, T** p, size_t bytes) {
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(ctx, e, "cudaMalloc");
+  }
+  ctx->dev_bytes += (int64_t)bytes;
+  e = cudaMemsetAsync(*p, 0, bytes, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+  return OSAR_OK;
+}
+
+void free_all(osar_ctx* ctx) {
+  void* ptrs[] = {ctx->scal, ctx->b, ctx->c, ctx->z, ctx->v, ctx->w, ctx->xtmp,
+                  ctx->part, ctx->d_dev, ctx->turns, ctx->g_hi, ctx->g_lo,
+                  ctx->segpart, ctx->tilepart, ctx->segs, ctx->seg_begin,
+                  ctx->zt, ctx->vt, ctx->xt, ctx->bmax, ctx->d32,
+                  ctx->gram_tiles, ctx->dict_tiles, ctx->A, ctx->F, ctx->D,
+                  ctx->Apl, ctx->Fpl, ctx->Dpl, ctx->sim_rho, ctx->sim_nz,
+                  ctx->sim_idx, ctx->sim_d, ctx->dict_part};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+  for (int i = 0; i < RING; ++i)
+    if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);
+  for (auto& pe : ctx->prof_pending) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  for (auto ev : ctx->ev_pool) cudaEventDestroy(ev);
+}
+
+osar_status check_usable(osar_ctx* ctx) {
+  if (!ctx) return OSAR_E_INVALID;
+  if (ctx->sticky != OSAR_OK) return ctx->sticky;
+  return OSAR_OK;
+}
+
+osar_status validate(const osar_config* c, std::string* why) {
+  if (!c) return *why = "config is NULL", OSAR_E_INVALID;
+  if (c->nx < 1 || c->ny < 1) return *why = "nx, ny must be >= 1", OSAR_E_INVALID;
+  if ((int64_t)c->nx * c->ny > (1 << 20))
+    return *why = "nx * ny exceeds 2^20 pixels", OSAR_E_INVALID;
+  if (!is_finite(c->pixel_m) || c->pixel_m <= 0)
+    return *why = "pixel_m must be finite and > 0", OSAR_E_INVALID;
+  if (c->n_freq < 1 || c->n_freq > 16384)
+    return *why = "n_freq must be in [1, 16384]", OSAR_E_INVALID;
+  if (!is_finite(c->f_lo_hz) || !is_finite(c->f_hi_hz) || c->f_lo_hz <= 0 ||
+      c->f_hi_hz < c->f_lo_hz)
+    return *why = "need 0 < f_lo_hz <= f_hi_hz", OSAR_E_INVALID;
+  if (c->precision < OSAR_FP64 || c->precision > OSAR_SPLIT_BF16)
+    return *why = "unknown precision", OSAR_E_INVALID;
+  if (c->dict_kind < OSAR_DICT_IDENTITY || c->dict_kind > OSAR_DICT_GAUSSIAN)
+    return *why = "unknown dict_kind", OSAR_E_INVALID;
+  if (c->dict_kind != OSAR_DICT_IDENTITY) {
+    if (c->n_atoms < 1 || c->n_atoms > 131072)
+      return *why = "n_atoms must be in [1, 131072]", OSAR_E_INVALID;
+    if (c->dict_kind == OSAR_DICT_HOST && !c->dict_c128)
+      return *why = "dict_c128 is NULL", OSAR_E_INVALID;
+  } else if ((int64_t)c->nx * c->ny > 131072) {
+    return *why = "pixel-basis scenes are limited to 131072 pixels", OSAR_E_INVALID;
+  }
+  if (!is_finite(c->lambda) || c->lambda < 0)
+    return *why = "lambda must be finite and >= 0", OSAR_E_INVALID;
+  if (c->power_iters_first < 1 || c->power_iters < 0)
+    return *why = "need power_iters_first >= 1 and power_iters >= 0", OSAR_E_INVALID;
+  if (!is_finite(c->lipschitz_margin) || c->lipschitz_margin < 0)
+    return *why = "lipschitz_margin must be finite and >= 0", OSAR_E_INVALID;
+  return OSAR_OK;
+}
+
+void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
+                  std::vector<int>& seg_begin, std::vector<int2>& gram_tiles,
+                  std::vector<int2>& dict_tiles) {
+  const int nb = ctx->nb;
+  // matvec segments: runs of S blocks of one block column
+  int64_t target = (int64_t)ctx->sm_count * 2 * 12;
+  int S = (int)(ctx->nblk / (target > 0 ? target : 1));
+  if (S < 1) S = 1;
+  if (S > 16) S = 16;
+  seg_begin.assign(nb + 1, 0);
+  for (int J = 0; J < nb; ++J) {
+    seg_begin[J] = (int)segs.size();
+    for (int I0 = 0; I0 <= J; I0 += S) {
+      int I1 = I0 + S < J + 1 ? I0 + S : J + 1;
+      segs.push_back(make_int4(J, I0, I1, (int)segs.size()));
+    }
+  }
+  seg_begin[nb] = (int)segs.size();
+  // Gram tiles: upper blocks grouped in SB x SB super-blocks so that the
+  // CTAs running at the same time share operand rows in L2.
+  const int SB = 8;
+  for (int bi = 0; bi < nb; bi += SB)
+    for (int bj = bi; bj < nb; bj += SB)
+      for (int I = bi; I < bi + SB && I < nb; ++I)
+        for (int J = (bj > I ? bj : I); J < bj + SB && J < nb; ++J)
+          gram_tiles.push_back(make_int2(I, J));
+  if (ctx->dict) {
+    // split-K slices only on the tensor-core path; the (atom, frequency)
+    // tiles of one atom block are adjacent so its dictionary rows stay in L2
+    const int S = ctx->prec == OSAR_SPLIT_BF16 ? ctx->dict_slices : 1;
+    for (int I = 0; I < nb; ++I)
+      for (int sl = 0; sl < S; ++sl)
+        for (int J = 0; J < ctx->Kp / BLK; ++J)
+          dict_tiles.push_back(make_int2(I, J | (sl << 16)));
+  }
+}
+
+osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
+  std::string why;
+  osar_status st = validate(cfg, &why);
+  if (st != OSAR_OK) return fail(nullptr, st, why);
+  osar_ctx* ctx = new osar_ctx();
+  ctx->cfg = *cfg;
+  ctx->cfg.dict_c128 = nullptr;
+  ctx->prec = cfg->precision;
+  ctx->dict = cfg->dict_kind != OSAR_DICT_IDENTITY;
+  ctx->N = cfg->nx * cfg->ny;
+  ctx->M = ctx->dict ? cfg->n_atoms : ctx->N;
+  ctx->K = cfg->n_freq;
+  ctx->Mp = (int)roundup(ctx->M, BLK);
+  ctx->Np = (int)roundup(ctx->N, BLK);
+  ctx->Kp = (int)roundup(ctx->K, BLK);
+  ctx->nb = ctx->Mp / BLK;
+  ctx->nblk = packed_count(ctx->nb);
+  ctx->dict_slices = dict_slices(ctx->Np);
+
+  auto bail = [&](osar_status s) {
+    g_create_error = ctx->last_error;
+    free_all(ctx);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return s;
+  };
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaGetDevice"));
+  if (cfg->cuda_stream) {
+    ctx->stream = (cudaStream_t)cfg->cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaStreamCreate"));
+    ctx->own_stream = true;
+  }
+
+  std::vector<int4> segs;
+  std::vector<int> seg_begin;
+  std::vector<int2> gtiles, dtiles;
+  build_tables(ctx, segs, seg_begin, gtiles, dtiles);
+  ctx->nseg = (int)segs.size();
+  ctx->n_dict_tiles = (int)dtiles.size();
+
+  const size_t cplx = ctx->prec == OSAR_FP64 ? 16 : 8;
+  const int64_t Mp = ctx->Mp, Np = ctx->Np, Kp = ctx->Kp;
+  const int64_t bb = (int64_t)BLK * BLK;
+#define AL(p, bytes)                                 \
+  do {                                               \
+    osar_status _s = dev_alloc(ctx, &(p), (bytes));  \
+    if (_s != OSAR_OK) return bail(_s);              \
+  } while (0)
+  AL(ctx->scal, sizeof(DevScalars));
+  AL(ctx->b, 16 * Mp);
+  AL(ctx->c, 16 * Mp);
+  AL(ctx->z, 16 * Mp);
+  AL(ctx->v, 16 * Mp);
+  AL(ctx->w, 16 * Mp);
+  AL(ctx->xtmp, 16 * Mp);
+  AL(ctx->part, 16 * (int64_t)ctx->nb);
+  AL(ctx->d_dev, 16 * Kp);
+  AL(ctx->turns, 16 * Np);
+  AL(ctx->g_hi, cplx * bb * ctx->nblk);
+  if (ctx->prec == OSAR_SPLIT_BF16 && cfg->compensated)
+    AL(ctx->g_lo, 8 * bb * ctx->nblk);
+  AL(ctx->segpart, cplx * BLK * (int64_t)ctx->nseg);
+  AL(ctx->tilepart, cplx * BLK * ctx->nblk);
+  AL(ctx->zt, cplx * Mp);
+  AL(ctx->vt, cplx * Mp);
+  AL(ctx->xt, cplx * Mp);
+  AL(ctx->bmax, 8 * ((Mp + 7) / 8));
+  AL(ctx->d32, 8 * Kp);
+  AL(ctx->segs, sizeof(int4) * segs.size());
+  AL(ctx->seg_begin, sizeof(int) * seg_begin.size());
+  AL(ctx->gram_tiles, sizeof(int2) * gtiles.size());
+  if (ctx->dict) AL(ctx->dict_tiles, sizeof(int2) * (dtiles.size() ? dtiles.size() : 1));
+  if (ctx->prec == OSAR_SPLIT_BF16) {
+    AL(ctx->Apl, 2 * 6 * Mp * Kp);
+    if (ctx->dict) {
+      AL(ctx->Fpl, 2 * 6 * Kp * Np);
+      AL(ctx->Dpl, 2 * 4 * Mp * Np);
+      AL(ctx->dict_part, 8 * (int64_t)ctx->dict_slices * Mp * Kp);
+    }
+  } else {
+    AL(ctx->A, cplx * Mp * Kp);
+    if (ctx->dict) {
+      AL(ctx->F, cplx * Kp * Np);
+      AL(ctx->D, cplx * Mp * Np);
+    }
+  }
+  AL(ctx->sim_rho, 16 * Np);
+  AL(ctx->sim_nz, 16 * Mp);
+  AL(ctx->sim_idx, 4 * Mp);
+  AL(ctx->sim_d, 16 * Kp);
+#undef AL
+  e = cudaMallocHost((void**)&ctx->h_ring, sizeof(double2) * RING * Kp);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaMallocHost"));
+  for (int i = 0; i < RING; ++i) {
+    e = cudaEventCreateWithFlags(&ctx->ring_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaEventCreate"));
+  }
+
+  e = cudaMemcpyAsync(ctx->segs, segs.data(), sizeof(int4) * segs.size(),
+                      cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->seg_begin, seg_begin.data(),
+                        sizeof(int) * seg_begin.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->gram_tiles, gtiles.data(),
+                        sizeof(int2) * gtiles.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess && ctx->dict && !dtiles.empty())
+    e = cudaMemcpyAsync(ctx->dict_tiles, dtiles.data(),
+                        sizeof(int2) * dtiles.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  // initial scalars and power vector v = 1/sqrt(M) on the M real atoms
+  DevScalars s0 = {};
+  s0.t = 1.0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->scal, &s0, sizeof(s0), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  std::vector<double2> v0((size_t)Mp, make_double2(0.0, 0.0));
+  for (int i = 0; i < ctx->M; ++i) v0[i].x = 1.0 / std::sqrt((double)ctx->M);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->v, v0.data(), 16 * Mp, cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess) e = launch_set_working(ctx);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "upload tables"));
+
+  if (ctx->dict) {
+    e = launch_dictionary_build(
+        ctx, cfg->dict_kind == OSAR_DICT_HOST ? cfg->dict_c128 : nullptr);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "dictionary build"));
+  }
+  if (ctx->prec == OSAR_SPLIT_BF16) {
+    std::string err;
+    if (!make_tensor_maps(ctx, &err))
+      return bail(fail(ctx, OSAR_E_CUDA, err));
+  }
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "create synchronize"));
+  *out = ctx;
+  return OSAR_OK;
+}
+
+osar_status read_scalars(osar_ctx* ctx, DevScalars* s) {
+  CK(ctx, cudaMemcpyAsync(s, ctx->scal, sizeof(*s), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (s->error)
+    return fail(ctx, OSAR_E_TIMEOUT, "a bounded device wait gave up");
+  return OSAR_OK;
+}
+
+osar_status push_impl(osar_ctx* ctx, const double gamma[3]) {
+  cudaError_t e;
+  e = launch_pixel_turns(ctx, gamma);
+  if (e == cudaSuccess) e = launch_phase(ctx);
+  if (e == cudaSuccess && ctx->dict)
+    e = ctx->prec == OSAR_SPLIT_BF16 ? launch_dict_tc(ctx) : launch_dict_simt(ctx);
+  if (e == cudaSuccess) e = launch_data_update(ctx);
+  if (e == cudaSuccess)
+    e = ctx->prec == OSAR_SPLIT_BF16 ? launch_gram_tc(ctx) : launch_gram_simt(ctx);
+  ctx->n += 1;
+  if (e == cudaSuccess)
+    e = launch_power_steps(ctx, ctx->n == 1 ? ctx->cfg.power_iters_first
+                                            : ctx->cfg.power_iters);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_push_pulse");
+  ctx->fresh = true;
+  return OSAR_OK;
+}
+
+}  // namespace
+
+namespace osar {
+
+void prof_begin(osar_ctx* ctx, int kind, ProfEvent* ev) {
+  ev->kind = -1;
+  if (!ctx->prof_on) return;
+  for (int i = 0; i < 2; ++i) {
+    cudaEvent_t x;
+    if (!ctx->ev_pool.empty()) {
+      x = ctx->ev_pool.back();
+      ctx->ev_pool.pop_back();
+    } else if (cudaEventCreate(&x) != cudaSuccess) {
+      return;
+    }
+    (i == 0 ? ev->a : ev->b) = x;
+  }
+  ev->kind = kind;
+  cudaEventRecord(ev->a, ctx->stream);
+}
+
+void prof_end(osar_ctx* ctx, ProfEvent* ev) {
+  if (ev->kind < 0) return;
+  cudaEventRecord(ev->b, ctx->stream);
+  ctx->prof_pending.push_back(*ev);
+}
+
+}  // namespace osar
+
+extern "C" {
+
+void osar_config_default(osar_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->nx = 32;
+  c->ny = 32;
+  c->pixel_m = 1.0;
+  c->n_freq = 128;
+  c->f_lo_hz = 9.9e9;
+  c->f_hi_hz = 10.1e9;
+  c->dict_kind = OSAR_DICT_IDENTITY;
+  c->n_atoms = 0;
+  c->dict_c128 = nullptr;
+  c->dict_seed = 0;
+  c->precision = OSAR_FP64;
+  c->lambda = 0.05;
+  c->lambda_relative = 1;
+  c->power_iters_first = 30;
+  c->power_iters = 4;
+  c->lipschitz_margin = 0.01;
+  c->restart_momentum = 0;
+  c->compensated = 1;
+  c->cuda_stream = nullptr;
+}
+
+osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
+  if (!out) return fail(nullptr, OSAR_E_INVALID, "out is NULL");
+  *out = nullptr;
+  return create_impl(cfg, out);
+}
+
+osar_status osar_destroy(osar_ctx* ctx) {
+  if (!ctx) return OSAR_OK;
+  cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return OSAR_OK;
+}
+
+osar_status osar_push_pulse(osar_ctx* ctx, const double gamma_xyz[3],
+                            const double* d_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!gamma_xyz || !d_c128)
+    return fail(ctx, OSAR_E_INVALID, "osar_push_pulse: NULL argument");
+  for (int i = 0; i < 3; ++i)
+    if (!is_finite(gamma_xyz[i]))
+      return fail(ctx, OSAR_E_INVALID, "osar_push_pulse: non-finite gamma");
+  const int slot = ctx->ring_pos;
+  ctx->ring_pos = (ctx->ring_pos + 1) % RING;
+  CK(ctx, cudaEventSynchronize(ctx->ring_ev[slot]));
+  double2* h = ctx->h_ring + (size_t)slot * ctx->Kp;
+  std::memcpy(h, d_c128, sizeof(double2) * ctx->K);
+  CK(ctx, cudaMemcpyAsync(ctx->d_dev, h, sizeof(double2) * ctx->K,
+                          cudaMemcpyHostToDevice, ctx->stream));
+  CK(ctx, cudaEventRecord(ctx->ring_ev[slot], ctx->stream));
+  return push_impl(ctx, gamma_xyz);
+}
+
+osar_status osar_push_pulse_dev(osar_ctx* ctx, const double gamma_xyz[3],
+                                const void* d_dev_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!gamma_xyz || !d_dev_c128)
+    return fail(ctx, OSAR_E_INVALID, "osar_push_pulse_dev: NULL argument");
+  for (int i = 0; i < 3; ++i)
+    if (!is_finite(gamma_xyz[i]))
+      return fail(ctx, OSAR_E_INVALID, "osar_push_pulse_dev: non-finite gamma");
+  CK(ctx, cudaMemcpyAsync(ctx->d_dev, d_dev_c128, sizeof(double2) * ctx->K,
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+  return push_impl(ctx, gamma_xyz);
+}
+
+osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
+                         int32_t* iters_done) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (max_iters < 0 || !is_finite(tol) || tol < 0)
+    return fail(ctx, OSAR_E_INVALID, "osar_iterate: bad max_iters or tol");
+  if (ctx->n == 0)
+    return fail(ctx, OSAR_E_STATE, "osar_iterate before the first pulse");
+  cudaError_t e = cudaSuccess;
+  if (ctx->fresh) {
+    e = launch_burst_begin(ctx);
+    ctx->fresh = false;
+  }
+  if (e == cudaSuccess) e = launch_iter_begin(ctx, tol);
+  for (int k = 0; e == cudaSuccess && k < max_iters; ++k)
+    e = launch_fista_step(ctx);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_iterate");
+  if (iters_done) {
+    DevScalars s;
+    st = read_scalars(ctx, &s);
+    if (st != OSAR_OK) return st;
+    *iters_done = s.iters;
+  }
+  return OSAR_OK;
+}
+
+osar_status osar_get_coeffs(osar_ctx* ctx, double* out_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!out_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_coeffs: NULL");
+  CK(ctx, cudaMemcpyAsync(out_c128, ctx->c, sizeof(double2) * ctx->M,
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_get_coeffs_dev(osar_ctx* ctx, void* out_dev_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!out_dev_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_coeffs_dev: NULL");
+  CK(ctx, cudaMemcpyAsync(out_dev_c128, ctx->c, sizeof(double2) * ctx->M,
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_get_state(osar_ctx* ctx, int32_t* n, double* lipschitz,
+                           double* lambda, double* t) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  DevScalars s;
+  st = read_scalars(ctx, &s);
+  if (st != OSAR_OK) return st;
+  if (n) *n = ctx->n;
+  if (lipschitz) *lipschitz = s.lip;
+  if (lambda) *lambda = s.lambda;
+  if (t) *t = s.t;
+  return OSAR_OK;
+}
+
+osar_status osar_get_dims(const osar_ctx* ctx, int32_t* m_atoms,
+                          int32_t* n_pixels, int32_t* n_freq) {
+  if (!ctx) return OSAR_E_INVALID;
+  if (m_atoms) *m_atoms = ctx->M;
+  if (n_pixels) *n_pixels = ctx->N;
+  if (n_freq) *n_freq = ctx->K;
+  return OSAR_OK;
+}
+
+osar_status osar_get_gram(osar_ctx* ctx, double* out_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!out_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_gram: NULL");
+  const int64_t M = ctx->M;
+  int64_t rows = (int64_t)(256ll << 20) / (16 * M);
+  if (rows < 1) rows = 1;
+  if (rows > M) rows = M;
+  double2* tmp = nullptr;
+  CK(ctx, cudaMalloc(&tmp, sizeof(double2) * rows * M));
+  for (int64_t r0 = 0; r0 < M; r0 += rows) {
+    int64_t nr = r0 + rows <= M ? rows : M - r0;
+    cudaError_t e = launch_gram_expand(ctx, (int)r0, (int)nr, tmp);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out_c128 + 2 * r0 * M, tmp, sizeof(double2) * nr * M,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(ctx, e, "osar_get_gram");
+    }
+  }
+  cudaFree(tmp);
+  return OSAR_OK;
+}
+
+osar_status osar_get_gram_entries(osar_ctx* ctx, const int32_t* rows,
+                                  const int32_t* cols, int32_t count,
+                                  double* out_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (count < 0 || (count > 0 && (!rows || !cols || !out_c128)))
+    return fail(ctx, OSAR_E_INVALID, "osar_get_gram_entries: bad arguments");
+  if (count == 0) return OSAR_OK;
+  std::vector<int2> rc(count);
+  for (int q = 0; q < count; ++q) {
+    if (rows[q] < 0 || rows[q] >= ctx->M || cols[q] < 0 || cols[q] >= ctx->M)
+      return fail(ctx, OSAR_E_INVALID, "osar_get_gram_entries: index out of range");
+    rc[q] = make_int2(rows[q], cols[q]);
+  }
+  int2* drc = nullptr;
+  double2* dout = nullptr;
+  CK(ctx, cudaMalloc(&drc, sizeof(int2) * count));
+  cudaError_t e = cudaMalloc(&dout, sizeof(double2) * count);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(drc, rc.data(), sizeof(int2) * count,
+                        cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = launch_gram_entries(ctx, drc, count, dout);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_c128, dout, sizeof(double2) * count,
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(drc);
+  if (dout) cudaFree(dout);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_get_gram_entries");
+  return OSAR_OK;
+}
+
+osar_status osar_get_b(osar_ctx* ctx, double* out_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!out_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_b: NULL");
+  CK(ctx, cudaMemcpyAsync(out_c128, ctx->b, sizeof(double2) * ctx->M,
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_gram_apply(osar_ctx* ctx, const double* x_c128,
+                            double* y_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!x_c128 || !y_c128) return fail(ctx, OSAR_E_INVALID, "osar_gram_apply: NULL");
+  CK(ctx, cudaMemsetAsync(ctx->xtmp, 0, sizeof(double2) * ctx->Mp, ctx->stream));
+  CK(ctx, cudaMemcpyAsync(ctx->xtmp, x_c128, sizeof(double2) * ctx->M,
+                          cudaMemcpyHostToDevice, ctx->stream));
+  CK(ctx, launch_gram_apply(ctx, ctx->xtmp, ctx->w));
+  CK(ctx, cudaMemcpyAsync(y_c128, ctx->w, sizeof(double2) * ctx->M,
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_simulate_pulse(osar_ctx* ctx, const double gamma_xyz[3],
+                                const double* coeffs_c128, double* d_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!gamma_xyz || !coeffs_c128 || !d_c128)
+    return fail(ctx, OSAR_E_INVALID, "osar_simulate_pulse: NULL argument");
+  std::vector<int> idx;
+  std::vector<double2> val;
+  for (int j = 0; j < ctx->M; ++j) {
+    double re = coeffs_c128[2 * j], im = coeffs_c128[2 * j + 1];
+    if (re != 0.0 || im != 0.0) {
+      idx.push_back(j);
+      val.push_back(make_double2(re, im));
+    }
+  }
+  const int nnz = (int)idx.size();
+  if (nnz) {
+    CK(ctx, cudaMemcpyAsync(ctx->sim_idx, idx.data(), sizeof(int) * nnz,
+                            cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->sim_nz, val.data(), sizeof(double2) * nnz,
+                            cudaMemcpyHostToDevice, ctx->stream));
+  }
+  CK(ctx, launch_pixel_turns(ctx, gamma_xyz));
+  CK(ctx, launch_simulate(ctx, nnz, ctx->sim_d));
+  CK(ctx, cudaMemcpyAsync(d_c128, ctx->sim_d, sizeof(double2) * ctx->K,
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_synchronize(osar_ctx* ctx) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_profile_enable(osar_ctx* ctx, int32_t on) {
+  if (!ctx) return OSAR_E_INVALID;
+  ctx->prof_on = on != 0;
+  return OSAR_OK;
+}
+
+static osar_status profile_collect(osar_ctx* ctx) {
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  for (auto& pe : ctx->prof_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+      ctx->prof_ms[pe.kind] += ms;
+      ctx->prof_launches[pe.kind] += 1;
+    }
+    ctx->ev_pool.push_back(pe.a);
+    ctx->ev_pool.push_back(pe.b);
+  }
+  ctx->prof_pending.clear();
+  return OSAR_OK;
+}
+
+osar_status osar_profile_read(osar_ctx* ctx, int32_t kernel, int64_t* launches,
+                              double* total_ms) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (kernel < 0 || kernel >= KCL_COUNT)
+    return fail(ctx, OSAR_E_INVALID, "osar_profile_read: unknown kernel class");
+  st = profile_collect(ctx);
+  if (st != OSAR_OK) return st;
+  if (launches) *launches = ctx->prof_launches[kernel];
+  if (total_ms) *total_ms = ctx->prof_ms[kernel];
+  return OSAR_OK;
+}
+
+osar_status osar_profile_reset(osar_ctx* ctx) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  st = profile_collect(ctx);
+  if (st != OSAR_OK) return st;
+  for (int k = 0; k < KCL_COUNT; ++k) {
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_launches[k] = 0;
+  }
+  ctx->launches = 0;
+  return OSAR_OK;
+}
+
+osar_status osar_launch_count(const osar_ctx* ctx, int64_t* launches) {
+  if (!ctx || !launches) return OSAR_E_INVALID;
+  *launches = ctx->launches;
+  return OSAR_OK;
+}
+
+osar_status osar_device_bytes(const osar_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return OSAR_E_INVALID;
+  *bytes = ctx->dev_bytes;
+  return OSAR_OK;
+}
+
+// ------------------------------------------------------------ checkpoints --
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version;
+  int32_t M, N, K, prec, dict_kind, compensated, n, fresh;
+  int64_t nblk;
+  int32_t entry_bytes, has_lo;
+};
+
+osar_status write_dev(osar_ctx* ctx, FILE* f, const void* dev, size_t bytes) {
+  std::vector<char> buf(bytes);
+  CK(ctx, cudaMemcpyAsync(buf.data(), dev, bytes, cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (fwrite(buf.data(), 1, bytes, f) != bytes)
+    return fail(ctx, OSAR_E_IO, "checkpoint write failed");
+  return OSAR_OK;
+}
+
+osar_status read_dev(osar_ctx* ctx, FILE* f, void* dev, size_t bytes) {
+  std::vector<char> buf(bytes);
+  if (fread(buf.data(), 1, bytes, f) != bytes)
+    return fail(ctx, OSAR_E_IO, "checkpoint truncated");
+  CK(ctx, cudaMemcpyAsync(dev, buf.data(), bytes, cudaMemcpyHostToDevice,
+                          ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return OSAR_OK;
+}
+}  // namespace
+
+osar_status osar_save(osar_ctx* ctx, const char* path) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!path) return fail(ctx, OSAR_E_INVALID, "osar_save: NULL path");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(ctx, OSAR_E_IO, std::string("cannot open ") + path);
+  CkptHeader h = {};
+  std::memcpy(h.magic, "OSARCKP", 8);
+  h.version = 2;
+  h.M = ctx->M;
+  h.N = ctx->N;
+  h.K = ctx->K;
+  h.prec = ctx->prec;
+  h.dict_kind = ctx->cfg.dict_kind;
+  h.compensated = ctx->cfg.compensated;
+  h.n = ctx->n;
+  h.fresh = ctx->fresh ? 1 : 0;
+  h.nblk = ctx->nblk;
+  h.entry_bytes = ctx->prec == OSAR_FP64 ? 16 : 8;
+  h.has_lo = ctx->g_lo ? 1 : 0;
+  const size_t vec = sizeof(double2) * ctx->Mp;
+  const size_t gb = (size_t)h.entry_bytes * BLK * BLK * ctx->nblk;
+  bool ok = fwrite(&h, sizeof(h), 1, f) == 1;
+  if (!ok) {
+    fclose(f);
+    return fail(ctx, OSAR_E_IO, "checkpoint write failed");
+  }
+  st = write_dev(ctx, f, ctx->scal, sizeof(DevScalars));
+  if (st == OSAR_OK) st = write_dev(ctx, f, ctx->b, vec);
+  if (st == OSAR_OK) st = write_dev(ctx, f, ctx->c, vec);
+  if (st == OSAR_OK) st = write_dev(ctx, f, ctx->z, vec);
+  if (st == OSAR_OK) st = write_dev(ctx, f, ctx->v, vec);
+  if (st == OSAR_OK) st = write_dev(ctx, f, ctx->g_hi, gb);
+  if (st == OSAR_OK && ctx->g_lo) st = write_dev(ctx, f, ctx->g_lo, (size_t)8 * BLK * BLK * ctx->nblk);
+  if (fclose(f) != 0 && st == OSAR_OK) st = fail(ctx, OSAR_E_IO, "checkpoint close failed");
+  return st;
+}
+
+osar_status osar_load(const char* path, const osar_config* cfg, osar_ctx** out) {
+  if (!out) return fail(nullptr, OSAR_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!path || !cfg) return fail(nullptr, OSAR_E_INVALID, "osar_load: NULL argument");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(nullptr, OSAR_E_IO, std::string("cannot open ") + path);
+  CkptHeader h;
+  if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "OSARCKP", 8) != 0 ||
+      h.version != 2) {
+    fclose(f);
+    return fail(nullptr, OSAR_E_IO, "not an osar checkpoint");
+  }
+  osar_ctx* ctx = nullptr;
+  osar_status st = osar_create(cfg, &ctx);
+  if (st != OSAR_OK) {
+    fclose(f);
+    return st;
+  }
+  if (h.M != ctx->M || h.N != ctx->N || h.K != ctx->K || h.prec != ctx->prec ||
+      h.dict_kind != ctx->cfg.dict_kind || h.nblk != ctx->nblk ||
+      h.has_lo != (ctx->g_lo ? 1 : 0)) {
+    fclose(f);
+    osar_destroy(ctx);
+    return fail(nullptr, OSAR_E_INVALID, "checkpoint does not match the config");
+  }
+  const size_t vec = sizeof(double2) * ctx->Mp;
+  const size_t gb = (size_t)h.entry_bytes * BLK * BLK * ctx->nblk;
+  st = read_dev(ctx, f, ctx->scal, sizeof(DevScalars));
+  if (st == OSAR_OK) st = read_dev(ctx, f, ctx->b, vec);
+  if (st == OSAR_OK) st = read_dev(ctx, f, ctx->c, vec);
+  if (st == OSAR_OK) st = read_dev(ctx, f, ctx->z, vec);
+  if (st == OSAR_OK) st = read_dev(ctx, f, ctx->v, vec);
+  if (st == OSAR_OK) st = read_dev(ctx, f, ctx->g_hi, gb);
+  if (st == OSAR_OK && ctx->g_lo)
+    st = read_dev(ctx, f, ctx->g_lo, (size_t)8 * BLK * BLK * ctx->nblk);
+  fclose(f);
+  if (st == OSAR_OK) {
+    cudaError_t e = launch_set_working(ctx);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "osar_load");
+  }
+  if (st != OSAR_OK) {
+    g_create_error = ctx->last_error;
+    osar_destroy(ctx);
+    return st;
+  }
+  ctx->n = h.n;
+  ctx->fresh = h.fresh != 0;
+  *out = ctx;
+  return OSAR_OK;
+}
+
+const char* osar_last_error(const osar_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->last_error.c_str();
+}
+
+const char* osar_version(void) { return "libosar 0.1 (sm_103a)"; }
+
+}  // extern "C"

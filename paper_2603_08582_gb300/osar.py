@@ -1,0 +1,321 @@
+"""Python binding of libosar (ctypes, argument marshalling only).
+
+Every step of the online SAR hot path runs in the library's CUDA kernels;
+this module only converts NumPy arrays / torch tensors to pointers and status
+codes to exceptions.  If the compiled library is missing the import fails
+loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libosar.so")
+
+OSAR_OK, OSAR_E_INVALID, OSAR_E_OOM, OSAR_E_CUDA, OSAR_E_STATE, \
+    OSAR_E_TIMEOUT, OSAR_E_NUMERIC, OSAR_E_IO = range(8)
+OSAR_FP64, OSAR_FP32, OSAR_SPLIT_BF16 = 0, 1, 2
+OSAR_DICT_IDENTITY, OSAR_DICT_HOST, OSAR_DICT_GAUSSIAN = 0, 1, 2
+
+PRECISIONS = {"fp64": OSAR_FP64, "fp32": OSAR_FP32, "split_bf16": OSAR_SPLIT_BF16}
+
+KERNEL_CLASSES = {"phase": 0, "dict_gemm": 1, "gram_gemm": 2, "data_update": 3,
+                  "matvec": 4, "fista_finalize": 5, "power_finalize": 6,
+                  "scalar": 7}
+
+# Symbols declared in include/osar.h (checked by the CPU test suite).
+EXPORTS = [
+    "osar_config_default", "osar_create", "osar_destroy", "osar_push_pulse",
+    "osar_push_pulse_dev", "osar_iterate", "osar_get_coeffs",
+    "osar_get_coeffs_dev", "osar_get_state", "osar_get_dims", "osar_get_gram",
+    "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
+    "osar_simulate_pulse", "osar_synchronize", "osar_profile_enable",
+    "osar_profile_read", "osar_profile_reset", "osar_launch_count",
+    "osar_device_bytes", "osar_save", "osar_load", "osar_last_error",
+    "osar_version",
+]
+
+
+class OsarConfig(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("pixel_m", C.c_double),
+        ("n_freq", C.c_int32), ("f_lo_hz", C.c_double), ("f_hi_hz", C.c_double),
+        ("dict_kind", C.c_int32), ("n_atoms", C.c_int32),
+        ("dict_c128", C.c_void_p), ("dict_seed", C.c_uint64),
+        ("precision", C.c_int32),
+        ("lam", C.c_double), ("lambda_relative", C.c_int32),
+        ("power_iters_first", C.c_int32), ("power_iters", C.c_int32),
+        ("lipschitz_margin", C.c_double),
+        ("restart_momentum", C.c_int32), ("compensated", C.c_int32),
+        ("cuda_stream", C.c_void_p),
+    ]
+
+
+class OsarError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libosar status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libosar.so (built by paper_2603_08582_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"libosar.so not found at {path}; build it with "
+            "`python -m paper_2603_08582_gb300.build` (needs nvcc)")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    D = C.POINTER(C.c_double)
+    I32 = C.c_int32
+    sig = {
+        "osar_config_default": (None, [C.POINTER(OsarConfig)]),
+        "osar_create": (I32, [C.POINTER(OsarConfig), C.POINTER(P)]),
+        "osar_destroy": (I32, [P]),
+        "osar_push_pulse": (I32, [P, D, D]),
+        "osar_push_pulse_dev": (I32, [P, D, P]),
+        "osar_iterate": (I32, [P, I32, C.c_double, C.POINTER(I32)]),
+        "osar_get_coeffs": (I32, [P, D]),
+        "osar_get_coeffs_dev": (I32, [P, P]),
+        "osar_get_state": (I32, [P, C.POINTER(I32), D, D, D]),
+        "osar_get_dims": (I32, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
+        "osar_get_gram": (I32, [P, D]),
+        "osar_get_gram_entries": (I32, [P, C.POINTER(I32), C.POINTER(I32), I32, D]),
+        "osar_get_b": (I32, [P, D]),
+        "osar_gram_apply": (I32, [P, D, D]),
+        "osar_simulate_pulse": (I32, [P, D, D, D]),
+        "osar_synchronize": (I32, [P]),
+        "osar_profile_enable": (I32, [P, I32]),
+        "osar_profile_read": (I32, [P, I32, C.POINTER(C.c_int64), D]),
+        "osar_profile_reset": (I32, [P]),
+        "osar_launch_count": (I32, [P, C.POINTER(C.c_int64)]),
+        "osar_device_bytes": (I32, [P, C.POINTER(C.c_int64)]),
+        "osar_save": (I32, [P, C.c_char_p]),
+        "osar_load": (I32, [C.c_char_p, C.POINTER(OsarConfig), C.POINTER(P)]),
+        "osar_last_error": (C.c_char_p, [P]),
+        "osar_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def default_config() -> OsarConfig:
+    cfg = OsarConfig()
+    load_library().osar_config_default(C.byref(cfg))
+    return cfg
+
+
+def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
+                precision="fp64", dictionary=None, n_atoms=None, dict_seed=0,
+                lam=0.05, lambda_relative=True, power_iters_first=30,
+                power_iters=4, lipschitz_margin=0.01, restart_momentum=False,
+                compensated=True, stream=None):
+    """Build an osar_config.  dictionary: None (identity), "gaussian"
+    (seeded Philox atoms, needs n_atoms) or an N x M complex array."""
+    cfg = default_config()
+    cfg.nx, cfg.ny, cfg.pixel_m = int(nx), int(ny), float(pixel_m)
+    cfg.n_freq, cfg.f_lo_hz, cfg.f_hi_hz = int(n_freq), float(f_lo_hz), float(f_hi_hz)
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    keep = None
+    if dictionary is None:
+        cfg.dict_kind = OSAR_DICT_IDENTITY
+    elif isinstance(dictionary, str) and dictionary == "gaussian":
+        cfg.dict_kind = OSAR_DICT_GAUSSIAN
+        cfg.n_atoms = int(n_atoms)
+        cfg.dict_seed = int(dict_seed)
+    else:
+        d = np.asarray(dictionary, dtype=np.complex128)
+        keep = np.asfortranarray(d)
+        cfg.dict_kind = OSAR_DICT_HOST
+        cfg.n_atoms = d.shape[1]
+        cfg.dict_c128 = keep.ctypes.data
+    cfg.lam = float(lam)
+    cfg.lambda_relative = 1 if lambda_relative else 0
+    cfg.power_iters_first = int(power_iters_first)
+    cfg.power_iters = int(power_iters)
+    cfg.lipschitz_margin = float(lipschitz_margin)
+    cfg.restart_momentum = 1 if restart_momentum else 0
+    cfg.compensated = 1 if compensated else 0
+    cfg.cuda_stream = stream
+    cfg._keepalive = keep
+    return cfg
+
+
+class Osar:
+    """One online reconstruction context (owns its device memory)."""
+
+    def __init__(self, cfg: Optional[OsarConfig] = None, _handle=None, **kw):
+        self._lib = load_library()
+        self._h = None
+        if _handle is not None:
+            self._h = _handle
+            self.cfg = cfg
+        else:
+            self.cfg = cfg if cfg is not None else make_config(**kw)
+            h = C.c_void_p()
+            st = self._lib.osar_create(C.byref(self.cfg), C.byref(h))
+            if st != OSAR_OK:
+                raise OsarError(st, self._lib.osar_last_error(None).decode())
+            self._h = h
+        m, n, k = C.c_int32(), C.c_int32(), C.c_int32()
+        self._lib.osar_get_dims(self._h, C.byref(m), C.byref(n), C.byref(k))
+        self.m_atoms, self.n_pixels, self.n_freq = m.value, n.value, k.value
+
+    # -- helpers --------------------------------------------------------
+    def _check(self, st: int):
+        if st != OSAR_OK:
+            raise OsarError(st, self._lib.osar_last_error(self._h).decode())
+
+    def close(self):
+        if self._h is not None:
+            self._lib.osar_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- Eqs. 12-13 and Algorithm 1 ---------------------------------------
+    def push_pulse(self, gamma, d):
+        g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+        dv = _c128(d)
+        if dv.size != self.n_freq or g.size != 3:
+            raise ValueError("gamma must have 3 entries and d n_freq entries")
+        self._check(self._lib.osar_push_pulse(self._h, _dptr(g), _dptr(dv.view(np.float64))))
+
+    def push_pulse_dev(self, gamma, d_dev_ptr: int):
+        g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+        self._check(self._lib.osar_push_pulse_dev(self._h, _dptr(g), C.c_void_p(d_dev_ptr)))
+
+    def iterate(self, max_iters: int, tol: float = 0.0, want_count: bool = True):
+        cnt = C.c_int32(0)
+        self._check(self._lib.osar_iterate(
+            self._h, int(max_iters), float(tol), C.byref(cnt) if want_count else None))
+        return cnt.value if want_count else None
+
+    def coeffs(self) -> np.ndarray:
+        out = np.empty(self.m_atoms, dtype=np.complex128)
+        self._check(self._lib.osar_get_coeffs(self._h, _dptr(out.view(np.float64))))
+        return out
+
+    def coeffs_dev(self, out_ptr: int):
+        self._check(self._lib.osar_get_coeffs_dev(self._h, C.c_void_p(out_ptr)))
+
+    def state(self) -> dict:
+        n = C.c_int32()
+        lip, lam, t = C.c_double(), C.c_double(), C.c_double()
+        self._check(self._lib.osar_get_state(self._h, C.byref(n), C.byref(lip),
+                                             C.byref(lam), C.byref(t)))
+        return {"n": n.value, "lipschitz": lip.value, "lambda": lam.value, "t": t.value}
+
+    def gram(self) -> np.ndarray:
+        out = np.empty((self.m_atoms, self.m_atoms), dtype=np.complex128)
+        self._check(self._lib.osar_get_gram(self._h, _dptr(out.view(np.float64))))
+        return out
+
+    def gram_entries(self, rows, cols) -> np.ndarray:
+        r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32))
+        c = np.ascontiguousarray(np.asarray(cols, dtype=np.int32))
+        out = np.empty(r.size, dtype=np.complex128)
+        self._check(self._lib.osar_get_gram_entries(
+            self._h, r.ctypes.data_as(C.POINTER(C.c_int32)),
+            c.ctypes.data_as(C.POINTER(C.c_int32)), int(r.size),
+            _dptr(out.view(np.float64))))
+        return out
+
+    def b(self) -> np.ndarray:
+        out = np.empty(self.m_atoms, dtype=np.complex128)
+        self._check(self._lib.osar_get_b(self._h, _dptr(out.view(np.float64))))
+        return out
+
+    def gram_apply(self, x) -> np.ndarray:
+        xv = _c128(x)
+        out = np.empty(self.m_atoms, dtype=np.complex128)
+        self._check(self._lib.osar_gram_apply(self._h, _dptr(xv.view(np.float64)),
+                                              _dptr(out.view(np.float64))))
+        return out
+
+    def simulate_pulse(self, gamma, coeffs) -> np.ndarray:
+        g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
+        cv = _c128(coeffs)
+        out = np.empty(self.n_freq, dtype=np.complex128)
+        self._check(self._lib.osar_simulate_pulse(self._h, _dptr(g), _dptr(cv.view(np.float64)),
+                                                  _dptr(out.view(np.float64))))
+        return out
+
+    def synchronize(self):
+        self._check(self._lib.osar_synchronize(self._h))
+
+    # -- profiling ----------------------------------------------------------
+    def profile_enable(self, on: bool = True):
+        self._check(self._lib.osar_profile_enable(self._h, 1 if on else 0))
+
+    def profile_reset(self):
+        self._check(self._lib.osar_profile_reset(self._h))
+
+    def profile_read(self, kernel: str):
+        n = C.c_int64()
+        ms = C.c_double()
+        self._check(self._lib.osar_profile_read(self._h, KERNEL_CLASSES[kernel],
+                                                C.byref(n), C.byref(ms)))
+        return n.value, ms.value
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self._check(self._lib.osar_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    def device_bytes(self) -> int:
+        n = C.c_int64()
+        self._check(self._lib.osar_device_bytes(self._h, C.byref(n)))
+        return n.value
+
+    # -- checkpoints ----------------------------------------------------------
+    def save(self, path: str):
+        self._check(self._lib.osar_save(self._h, path.encode()))
+
+    @classmethod
+    def load(cls, path: str, cfg: OsarConfig) -> "Osar":
+        lib = load_library()
+        h = C.c_void_p()
+        st = lib.osar_load(path.encode(), C.byref(cfg), C.byref(h))
+        if st != OSAR_OK:
+            raise OsarError(st, lib.osar_last_error(None).decode())
+        return cls(cfg, _handle=h)
+
+
+def version() -> str:
+    return load_library().osar_version().decode()

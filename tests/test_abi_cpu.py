@@ -1,0 +1,88 @@
+"""CPU-side checks of the C ABI: libosar.so builds for sm_103a, loads, exports
+every function include/osar.h declares, and its host-only logic (defaults,
+argument validation) behaves as documented.  No kernel runs here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2603_08582_gb300 import build, osar
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "osar.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return osar.load_library()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(osar_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declarations_match_binding():
+    assert _declared() == sorted(osar.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_config_defaults_and_layout(lib):
+    cfg = osar.default_config()
+    assert (cfg.nx, cfg.ny, cfg.n_freq) == (32, 32, 128)
+    assert cfg.pixel_m == 1.0
+    assert cfg.f_lo_hz == 9.9e9 and cfg.f_hi_hz == 10.1e9
+    assert cfg.precision == osar.OSAR_FP64
+    assert cfg.dict_kind == osar.OSAR_DICT_IDENTITY
+    assert cfg.lam == 0.05 and cfg.lambda_relative == 1
+    assert (cfg.power_iters_first, cfg.power_iters) == (30, 4)
+    assert cfg.lipschitz_margin == 0.01
+    assert cfg.restart_momentum == 0 and cfg.compensated == 1
+    assert cfg.cuda_stream is None
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nx", 0), ("n_freq", 0), ("pixel_m", -1.0), ("f_lo_hz", 0.0),
+    ("precision", 7), ("dict_kind", 9), ("power_iters_first", 0),
+    ("lam", float("nan")), ("lipschitz_margin", -0.5),
+])
+def test_create_rejects_invalid_config_before_any_device_work(lib, field, value):
+    cfg = osar.default_config()
+    setattr(cfg, field, value)
+    h = C.c_void_p()
+    st = lib.osar_create(C.byref(cfg), C.byref(h))
+    assert st == osar.OSAR_E_INVALID
+    assert h.value is None
+    assert len(lib.osar_last_error(None)) > 0
+
+
+def test_create_rejects_missing_host_dictionary(lib):
+    cfg = osar.default_config()
+    cfg.dict_kind = osar.OSAR_DICT_HOST
+    cfg.n_atoms = 10
+    h = C.c_void_p()
+    assert lib.osar_create(C.byref(cfg), C.byref(h)) == osar.OSAR_E_INVALID
+
+
+def test_null_context_calls_are_rejected(lib):
+    assert lib.osar_destroy(None) == osar.OSAR_OK
+    assert lib.osar_iterate(None, 1, 0.0, None) == osar.OSAR_E_INVALID
+    assert lib.osar_synchronize(None) == osar.OSAR_E_INVALID
+    assert b"libosar" in lib.osar_version()
+
+
+def test_sources_have_no_cpu_fallback():
+    """The product package never reaches the oracle."""
+    pkg = os.path.join(ROOT, "paper_2603_08582_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", text, re.M), f
