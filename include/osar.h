@@ -182,6 +182,20 @@ osar_status osar_get_b(osar_ctx* ctx, double* out_c128);
 osar_status osar_gram_apply(osar_ctx* ctx, const double* x_c128,
                             double* y_c128);
 
+/* y = A_n x like osar_gram_apply, but without any allocation: x and y are
+   caller device buffers (M complex128 each, 16-byte aligned), the call is
+   asynchronous on the context's stream, and the matvec's scratch comes from
+   a 4 MiB static device array inside the library instead of cudaMalloc.
+   No counterpart in the paper: it exists for callers that may not allocate
+   device memory after start-up (fixed-budget embedded or flight pipelines,
+   hosts with their own memory pool).  Limit: contexts with M <= 4096 atoms
+   (larger ones return OSAR_E_INVALID).  The array is shared by all calls on
+   a device and keeps the last call's contents; calls that overlap on the GPU
+   race on it and must be ordered by the caller.  The first call on a device
+   looks up the array's address (make it before any stream capture). */
+osar_status osar_gram_apply_static(osar_ctx* ctx, const void* x_dev_c128,
+                                   void* y_dev_c128);
+
 /* Noise-free pulse data d = G_n c for a platform at gamma_xyz (Eqs. 5-6),
    computed on the device in FP64: c (M complex, host) in, d (n_freq
    complex, host) out.  Does not touch the statistics; synchronises. */

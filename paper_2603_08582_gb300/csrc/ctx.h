@@ -159,5 +159,8 @@ cudaError_t launch_gram_apply(osar_ctx* ctx, const double2* x, double2* y);
 cudaError_t launch_gram_expand(osar_ctx* ctx, int r0, int rows, double2* dense);
 cudaError_t launch_gram_entries(osar_ctx* ctx, const int2* rc, int count,
                                 double2* out);
+size_t gram_apply_scratch_bytes(const osar_ctx* ctx);
+cudaError_t launch_gram_apply_scratch(osar_ctx* ctx, const double2* x,
+                                      double2* y, void* scratch);
 
 }  // namespace osar

@@ -571,6 +571,32 @@ __global__ void k_gram_entries(const T2* __restrict__ G,
   out[q] = make_double2(re, upper ? im : -im);
 }
 
+// Working-precision copy of a caller vector that holds only n_valid entries
+// (zero beyond), and y = A x written only for the first m_valid entries:
+// used when x and y are caller buffers of length M rather than Mp.
+template <typename T2>
+__global__ void k_to_working_bounded(const double2* __restrict__ x,
+                                     T2* __restrict__ xt, int n_valid, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = i < n_valid ? x[i] : make_double2(0.0, 0.0);
+  T2 t;
+  t.x = v.x;
+  t.y = v.y;
+  xt[i] = t;
+}
+
+template <typename T2, typename Acc>
+__global__ void __launch_bounds__(FIN_THREADS)
+    k_apply_finalize_bounded(const T2* __restrict__ segpart,
+                             const T2* __restrict__ tilepart,
+                             const int* __restrict__ seg_begin, int nb,
+                             double2* __restrict__ y, int m_valid) {
+  const int K = blockIdx.x, i = threadIdx.x;
+  const double2 v = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
+  if (i < BLK && K * BLK + i < m_valid) y[K * BLK + i] = v;
+}
+
 unsigned grid_matvec(const osar_ctx* ctx) {
   int g = 2 * ctx->sm_count;
   return (unsigned)(ctx->nseg < g ? ctx->nseg : g);
@@ -739,6 +765,52 @@ cudaError_t launch_gram_entries(osar_ctx* ctx, const int2* rc, int count,
     k_gram_entries<float2><<<g, 256, 0, ctx->stream>>>(
         (const float2*)ctx->g_hi, ctx->g_lo, ctx->nb, rc, count, out);
   ctx->launches++;
+  return cudaGetLastError();
+}
+
+size_t gram_apply_scratch_bytes(const osar_ctx* ctx) {
+  const size_t cplx = ctx->prec == OSAR_FP64 ? 16 : 8;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  return al(cplx * ctx->Mp) + al(cplx * BLK * (size_t)ctx->nseg) +
+         al(cplx * BLK * (size_t)ctx->nblk);
+}
+
+// y = A x with caller-provided scratch (working copy of x, segment and block
+// partials carved from `scratch`, which must hold gram_apply_scratch_bytes);
+// x and y are device vectors of M entries.  Every scratch byte read is
+// written earlier in the same call, so the scratch needs no clearing.
+cudaError_t launch_gram_apply_scratch(osar_ctx* ctx, const double2* x,
+                                      double2* y, void* scratch) {
+  const size_t cplx = ctx->prec == OSAR_FP64 ? 16 : 8;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  char* base = static_cast<char*>(scratch);
+  void* xt = base;
+  void* segp = base + al(cplx * ctx->Mp);
+  void* tilep = base + al(cplx * ctx->Mp) + al(cplx * BLK * (size_t)ctx->nseg);
+  const unsigned g = (unsigned)((ctx->Mp + 255) / 256);
+  const unsigned gm = grid_matvec(ctx);
+  if (ctx->prec == OSAR_FP64) {
+    k_to_working_bounded<double2><<<g, 256, 0, ctx->stream>>>(
+        x, (double2*)xt, ctx->M, ctx->Mp);
+    k_matvec<double><<<gm, 256, 0, ctx->stream>>>(
+        (const double2*)ctx->g_hi, (const double2*)xt, (double2*)segp,
+        (double2*)tilep, ctx->segs, ctx->nseg, ctx->nb, ctx->scal, 0);
+    k_apply_finalize_bounded<double2, double>
+        <<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
+            (const double2*)segp, (const double2*)tilep, ctx->seg_begin,
+            ctx->nb, y, ctx->M);
+  } else {
+    k_to_working_bounded<float2><<<g, 256, 0, ctx->stream>>>(
+        x, (float2*)xt, ctx->M, ctx->Mp);
+    k_matvec<float><<<gm, 256, 0, ctx->stream>>>(
+        (const float2*)ctx->g_hi, (const float2*)xt, (float2*)segp,
+        (float2*)tilep, ctx->segs, ctx->nseg, ctx->nb, ctx->scal, 0);
+    k_apply_finalize_bounded<float2, float>
+        <<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
+            (const float2*)segp, (const float2*)tilep, ctx->seg_begin, ctx->nb,
+            y, ctx->M);
+  }
+  ctx->launches += 3;
   return cudaGetLastError();
 }
 

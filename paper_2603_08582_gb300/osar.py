@@ -33,6 +33,7 @@ EXPORTS = [
     "osar_push_pulse_dev", "osar_iterate", "osar_get_coeffs",
     "osar_get_coeffs_dev", "osar_get_state", "osar_get_dims", "osar_get_gram",
     "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
+    "osar_gram_apply_static",
     "osar_simulate_pulse", "osar_synchronize", "osar_profile_enable",
     "osar_profile_read", "osar_profile_reset", "osar_launch_count",
     "osar_device_bytes", "osar_save", "osar_load", "osar_last_error",
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "osar_get_gram_entries": (I32, [P, C.POINTER(I32), C.POINTER(I32), I32, D]),
         "osar_get_b": (I32, [P, D]),
         "osar_gram_apply": (I32, [P, D, D]),
+        "osar_gram_apply_static": (I32, [P, P, P]),
         "osar_simulate_pulse": (I32, [P, D, D, D]),
         "osar_synchronize": (I32, [P]),
         "osar_profile_enable": (I32, [P, I32]),
@@ -267,6 +269,12 @@ class Osar:
         self._check(self._lib.osar_gram_apply(self._h, _dptr(xv.view(np.float64)),
                                               _dptr(out.view(np.float64))))
         return out
+
+    def gram_apply_static(self, x_dev_ptr: int, y_dev_ptr: int):
+        """y = A x on caller device buffers with no allocation (asynchronous
+        on the context's stream; see osar_gram_apply_static)."""
+        self._check(self._lib.osar_gram_apply_static(
+            self._h, C.c_void_p(x_dev_ptr), C.c_void_p(y_dev_ptr)))
 
     def simulate_pulse(self, gamma, coeffs) -> np.ndarray:
         g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
