@@ -125,7 +125,7 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
-    path = os.path.join(ROOT, "paper_2603_08582_gb300", "csrc", "k_fista.cu")
+    path = os.path.join(ROOT, "paper_2603_08582_gb300", "csrc", "matvec.cuh")
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
@@ -142,7 +142,7 @@ def profiled_traffic(kind: str):
         if ":" in ln and ln.strip().startswith("- "):
             k, v = ln.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("k_fista.cu sha256[:16]") != kernel_source_hash():
+    if vals.get("matvec.cuh sha256[:16]") != kernel_source_hash():
         return None
     try:
         return float(vals["dram bytes per full-size launch"])

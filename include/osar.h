@@ -202,6 +202,30 @@ osar_status osar_gram_apply_static(osar_ctx* ctx, const void* x_dev_c128,
 osar_status osar_simulate_pulse(osar_ctx* ctx, const double gamma_xyz[3],
                                 const double* coeffs_c128, double* d_c128);
 
+/* Differentiation form.  The paper leaves online parameter tuning to future
+   work (Sec. I, Sec. V); this call provides the gradients it would need.  It
+   runs `steps` (T) steps of Algorithm 1's inner loop on the context's current
+   Gram A_n and data vector b_n, from c^(0) = z^(1) = c0 with t_1 = t0, using
+   the given step tau and threshold lambda * tau (not the context's own), then
+   evaluates L = ||c_T - c_true||_2^2 and back-propagates through all T steps
+   with hand-written adjoint kernels.  Memory: (z_k, c_{k-1}) is stored every
+   ckpt_every steps (sqrt(T) is the usual choice) and each segment is
+   recomputed during the reverse sweep, so a step costs three Gram passes.
+   Outputs (host memory, each nullable): loss, dL/dlambda, dL/dtau, dL/db
+   (M complex, convention dL/dRe + i dL/dIm), c_T (M complex).  Since
+   b_n = sum_s G_s^H d_s, the gradient with respect to pulse s's data is
+   dL/dd_s = G_s dL/db, which osar_simulate_pulse computes when given dL/db
+   as its coefficients.  Arithmetic: FP64 on the FP64 path; on the FP32 and
+   split-BF16 paths the Gram passes run in FP32 and everything else in FP64.
+   The first call allocates the scratch (kept until destroy).  Synchronises.
+   Errors: OSAR_E_STATE before the first pulse; OSAR_E_INVALID for steps < 1,
+   ckpt_every < 1, tau <= 0, lambda < 0, t0 < 1 or NULL c0 / c_true. */
+osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
+                             double lambda, double tau, double t0,
+                             const double* c0_c128, const double* c_true_c128,
+                             double* loss, double* d_lambda, double* d_tau,
+                             double* d_b_c128, double* c_T_c128);
+
 /* Wait for all work queued on the context's stream. */
 osar_status osar_synchronize(osar_ctx* ctx);
 

@@ -112,6 +112,10 @@ struct osar_ctx {
   int* sim_idx = nullptr;      // nonzero coefficient indices (Mp)
   double2* sim_d = nullptr;    // simulated pulse (Kp)
 
+  // differentiation-form scratch (allocated by the first unrolled gradient)
+  void* adj_buf = nullptr;
+  size_t adj_bytes = 0;
+
   // host mirror
   int n = 0;
   bool fresh = true;
@@ -160,6 +164,13 @@ cudaError_t launch_gram_expand(osar_ctx* ctx, int r0, int rows, double2* dense);
 cudaError_t launch_gram_entries(osar_ctx* ctx, const int2* rc, int count,
                                 double2* out);
 size_t gram_apply_scratch_bytes(const osar_ctx* ctx);
+cudaError_t launch_matvec(osar_ctx* ctx, const void* xt);
+
+// ---- k_adjoint.cu ----------------------------------------------------------
+cudaError_t run_unroll_grad(osar_ctx* ctx, int T, int C, double lambda,
+                            double tau, double t0, const double* c0,
+                            const double* ctrue, double* loss, double* dlam,
+                            double* dtau, double* db, double* cT);
 cudaError_t launch_gram_apply_scratch(osar_ctx* ctx, const double2* x,
                                       double2* y, void* scratch);
 

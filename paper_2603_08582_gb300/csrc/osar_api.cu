@@ -68,6 +68,7 @@ void free_all(osar_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+  if (ctx->adj_buf) cudaFree(ctx->adj_buf);
   for (int i = 0; i < RING; ++i)
     if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);
   for (auto& pe : ctx->prof_pending) {
@@ -610,6 +611,26 @@ osar_status osar_simulate_pulse(osar_ctx* ctx, const double gamma_xyz[3],
   CK(ctx, cudaMemcpyAsync(d_c128, ctx->sim_d, sizeof(double2) * ctx->K,
                           cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
+                             double lambda, double tau, double t0,
+                             const double* c0_c128, const double* c_true_c128,
+                             double* loss, double* d_lambda, double* d_tau,
+                             double* d_b_c128, double* c_T_c128) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (ctx->n == 0)
+    return fail(ctx, OSAR_E_STATE, "osar_unroll_grad before the first pulse");
+  if (steps < 1 || ckpt_every < 1 || !is_finite(tau) || tau <= 0 ||
+      !is_finite(lambda) || lambda < 0 || !is_finite(t0) || t0 < 1 ||
+      !c0_c128 || !c_true_c128)
+    return fail(ctx, OSAR_E_INVALID, "osar_unroll_grad: bad arguments");
+  cudaError_t e = run_unroll_grad(ctx, steps, ckpt_every, lambda, tau, t0,
+                                  c0_c128, c_true_c128, loss, d_lambda, d_tau,
+                                  d_b_c128, c_T_c128);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_unroll_grad");
   return OSAR_OK;
 }
 

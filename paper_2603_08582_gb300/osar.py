@@ -34,7 +34,8 @@ EXPORTS = [
     "osar_get_coeffs_dev", "osar_get_state", "osar_get_dims", "osar_get_gram",
     "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
     "osar_gram_apply_static",
-    "osar_simulate_pulse", "osar_synchronize", "osar_profile_enable",
+    "osar_simulate_pulse", "osar_unroll_grad", "osar_synchronize",
+    "osar_profile_enable",
     "osar_profile_read", "osar_profile_reset", "osar_launch_count",
     "osar_device_bytes", "osar_save", "osar_load", "osar_last_error",
     "osar_version",
@@ -95,6 +96,8 @@ def load_library(path: str = LIB_PATH):
         "osar_gram_apply": (I32, [P, D, D]),
         "osar_gram_apply_static": (I32, [P, P, P]),
         "osar_simulate_pulse": (I32, [P, D, D, D]),
+        "osar_unroll_grad": (I32, [P, I32, I32, C.c_double, C.c_double,
+                                     C.c_double, D, D, D, D, D, D, D]),
         "osar_synchronize": (I32, [P]),
         "osar_profile_enable": (I32, [P, I32]),
         "osar_profile_read": (I32, [P, I32, C.POINTER(C.c_int64), D]),
@@ -283,6 +286,29 @@ class Osar:
         self._check(self._lib.osar_simulate_pulse(self._h, _dptr(g), _dptr(cv.view(np.float64)),
                                                   _dptr(out.view(np.float64))))
         return out
+
+    def unroll_grad(self, steps: int, ckpt_every: int, lam: float, tau: float,
+                    c0, c_true, t0: float = 1.0) -> dict:
+        """Loss ||c_T - c_true||^2 after `steps` unrolled inner steps on the
+        current Gram and data vector, and its gradients with respect to
+        lambda, tau and b (adjoint kernels, checkpoints every ckpt_every)."""
+        c0v = _c128(c0)
+        ctv = _c128(c_true)
+        loss, dl, dt = C.c_double(), C.c_double(), C.c_double()
+        db = np.empty(self.m_atoms, dtype=np.complex128)
+        ct = np.empty(self.m_atoms, dtype=np.complex128)
+        self._check(self._lib.osar_unroll_grad(
+            self._h, int(steps), int(ckpt_every), float(lam), float(tau),
+            float(t0), _dptr(c0v.view(np.float64)), _dptr(ctv.view(np.float64)),
+            C.byref(loss), C.byref(dl), C.byref(dt), _dptr(db.view(np.float64)),
+            _dptr(ct.view(np.float64))))
+        return {"loss": loss.value, "d_lambda": dl.value, "d_tau": dt.value,
+                "d_b": db, "c_T": ct}
+
+    def data_grad(self, gamma, d_b) -> np.ndarray:
+        """dL/dd_s = G_s dL/db for the pulse at gamma (the forward model
+        applied to the b-gradient)."""
+        return self.simulate_pulse(gamma, d_b)
 
     def synchronize(self):
         self._check(self._lib.osar_synchronize(self._h))
