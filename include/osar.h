@@ -256,6 +256,62 @@ osar_status osar_save(osar_ctx* ctx, const char* path);
 osar_status osar_load(const char* path, const osar_config* cfg,
                       osar_ctx** out);
 
+/* ------------------------------------------------------------------------
+ * Batching form: many independent online reconstructions of uneven size
+ * (several platforms or image patches) in one context.  Each scene keeps its
+ * own Gram, data vector, warm start, lambda, L and momentum, exactly as a
+ * separate osar_ctx would; the per-pulse work of all scenes runs as single
+ * launches (one persistent tensor-core launch covers every scene's Gram
+ * blocks) and FISTA bursts are replayed from CUDA graphs captured per step
+ * count.  Scenes use the pixel basis and one precision; frequencies, grids,
+ * lambda settings and power-iteration counts may differ per scene.
+ * ------------------------------------------------------------------------ */
+typedef struct osar_batch osar_batch;
+
+/* Create a batch from n_scenes configs (copied).  cuda_stream as in
+   osar_config.  Errors: OSAR_E_INVALID (non-identity dictionary, mixed
+   precision, bad sizes), OSAR_E_OOM, OSAR_E_CUDA. */
+osar_status osar_batch_create(const osar_config* cfgs, int32_t n_scenes,
+                              void* cuda_stream, osar_batch** out);
+osar_status osar_batch_destroy(osar_batch* batch);
+
+/* One pulse for every scene with active[s] != 0 (Eqs. 12-13, lambda and L
+   per scene); scenes with active[s] == 0 keep their state and skip the next
+   bursts.  gammas_xyz: n_scenes x 3 positions; d_c128: n_scenes rows of
+   d_stride complex samples, row s holding scene s's n_freq samples (host).
+   Asynchronous; inputs are staged before return. */
+osar_status osar_batch_push(osar_batch* batch, const int32_t* active,
+                            const double* gammas_xyz, const double* d_c128,
+                            int32_t d_stride);
+
+/* Up to max_iters steps of Algorithm 1 for every scene active in the last
+   push (same semantics per scene as osar_iterate, including tol).  iters
+   (nullable, n_scenes) receives each scene's steps in this call and
+   synchronises. */
+osar_status osar_batch_iterate(osar_batch* batch, int32_t max_iters, double tol,
+                               int32_t* iters);
+
+/* c_hat of one scene (M complex, host); synchronises. */
+osar_status osar_batch_get_coeffs(osar_batch* batch, int32_t scene,
+                                  double* out_c128);
+
+/* Pulse count, L, lambda and t of one scene; synchronises. */
+osar_status osar_batch_get_state(osar_batch* batch, int32_t scene, int32_t* n,
+                                 double* lipschitz, double* lambda, double* t);
+
+/* Choose the matvec work-item size (blocks per segment) by timing the
+   candidates 1, 2, 4, 8, 16 on the device; the choice is cached in the text
+   file named by the environment variable OSAR_TUNE_CACHE (when set) and
+   reused by later batches of the same shape.  chosen (nullable). */
+osar_status osar_batch_autotune(osar_batch* batch, int32_t* chosen);
+
+/* Scene count, device bytes, kernel launches so far, segment size. */
+osar_status osar_batch_info(const osar_batch* batch, int32_t* n_scenes,
+                            int64_t* device_bytes, int64_t* launches,
+                            int32_t* segment_blocks);
+osar_status osar_batch_synchronize(osar_batch* batch);
+const char* osar_batch_last_error(const osar_batch* batch);
+
 /* One-line description of the last error on ctx (or of the last failed
    osar_create when ctx is NULL).  Never NULL. */
 const char* osar_last_error(const osar_ctx* ctx);

@@ -85,8 +85,8 @@ struct osar_ctx {
   double* bmax = nullptr;      // per-block max |b_j|^2 (data update)
   float2* d32 = nullptr;       // staged pulse data in FP32 (Kp)
   int nseg = 0;
-  int2* gram_tiles = nullptr;  // upper blocks in L2-friendly order
-  int2* dict_tiles = nullptr;  // (atom block, frequency block | slice << 16)
+  int4* gram_tiles = nullptr;  // (I, J, packed block, 0), L2-friendly order
+  int4* dict_tiles = nullptr;  // (atom block, frequency block | slice << 16, 0, 0)
   int n_dict_tiles = 0;
   int dict_slices = 1;         // split-K slices of the dictionary product
   float2* dict_part = nullptr; // split: FP32 slice partials (slices x Mp x Kp)

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256)
     k_cgemm_tn(const typename Cx<T>::T2* __restrict__ P, int ldp,
                const typename Cx<T>::T2* __restrict__ Q, int ldq, int kdim,
                typename Cx<T>::T2* __restrict__ C, int ldc,
-               const int2* __restrict__ blocks, int nb) {
+               const int4* __restrict__ blocks) {
   using T2 = typename Cx<T>::T2;
   __shared__ T2 As[SK][ST + 1];
   __shared__ T2 Bs[SK][ST + 1];
@@ -44,12 +44,12 @@ __global__ void __launch_bounds__(256)
   T2* out;
   int ldo;
   if (PACKED) {
-    int2 blk = blocks[blockIdx.x];
+    int4 blk = blocks[blockIdx.x];  // (row block, column block, packed block)
     int sub = blockIdx.y;  // 4 sub-tiles per 128 x 128 block
     row0 = blk.x * BLK + (sub >> 1) * ST;
     col0 = blk.y * BLK + (sub & 1) * ST;
     // column-major block: entry (r, c) at c * BLK + r
-    out = C + packed_block(blk.x, blk.y, nb) * (int64_t)(BLK * BLK) +
+    out = C + (int64_t)blk.z * (BLK * BLK) +
           (int64_t)((sub & 1) * ST) * BLK + (sub >> 1) * ST;
     ldo = BLK;
   } else {
@@ -126,11 +126,11 @@ cudaError_t launch_dict_simt(osar_ctx* ctx) {
   if (ctx->prec == OSAR_FP64)
     k_cgemm_tn<double, false, false><<<grid, 256, 0, ctx->stream>>>(
         (const double2*)ctx->D, ctx->Np, (const double2*)ctx->F, ctx->Np,
-        ctx->Np, (double2*)ctx->A, ctx->Kp, nullptr, 0);
+        ctx->Np, (double2*)ctx->A, ctx->Kp, nullptr);
   else
     k_cgemm_tn<float, false, false><<<grid, 256, 0, ctx->stream>>>(
         (const float2*)ctx->D, ctx->Np, (const float2*)ctx->F, ctx->Np,
-        ctx->Np, (float2*)ctx->A, ctx->Kp, nullptr, 0);
+        ctx->Np, (float2*)ctx->A, ctx->Kp, nullptr);
   prof_end(ctx, &ev);
   ctx->launches++;
   return cudaGetLastError();
@@ -143,13 +143,29 @@ cudaError_t launch_gram_simt(osar_ctx* ctx) {
   if (ctx->prec == OSAR_FP64)
     k_cgemm_tn<double, true, true><<<grid, 256, 0, ctx->stream>>>(
         (const double2*)ctx->A, ctx->Kp, (const double2*)ctx->A, ctx->Kp,
-        ctx->Kp, (double2*)ctx->g_hi, 0, ctx->gram_tiles, ctx->nb);
+        ctx->Kp, (double2*)ctx->g_hi, 0, ctx->gram_tiles);
   else
     k_cgemm_tn<float, true, true><<<grid, 256, 0, ctx->stream>>>(
         (const float2*)ctx->A, ctx->Kp, (const float2*)ctx->A, ctx->Kp,
-        ctx->Kp, (float2*)ctx->g_hi, 0, ctx->gram_tiles, ctx->nb);
+        ctx->Kp, (float2*)ctx->g_hi, 0, ctx->gram_tiles);
   prof_end(ctx, &ev);
   ctx->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_simt_tiles(cudaStream_t st, int prec, const void* A,
+                                   int kp, void* g_hi, const int4* tiles,
+                                   int n_tiles) {
+  if (n_tiles <= 0) return cudaSuccess;
+  dim3 grid((unsigned)n_tiles, 4);
+  if (prec == OSAR_FP64)
+    k_cgemm_tn<double, true, true><<<grid, 256, 0, st>>>(
+        (const double2*)A, kp, (const double2*)A, kp, kp, (double2*)g_hi, 0,
+        tiles);
+  else
+    k_cgemm_tn<float, true, true><<<grid, 256, 0, st>>>(
+        (const float2*)A, kp, (const float2*)A, kp, kp, (float2*)g_hi, 0,
+        tiles);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,10 @@ constexpr int TC_SMEM = TC_STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 struct TcParams {
-  const int2* tiles;  // (row block, column block | slice << 16)
+  // (A row block, B row block | slice << 16, output block, 0); row blocks
+  // index the operand tensors' rows in units of 128, the output block is the
+  // packed Gram block to update (Gram mode)
+  const int4* tiles;
   int n_tiles;
   int k_chunks;    // KC chunks per half of the reduction (whole K)
   int k_slice;     // KC chunks per half handled by one tile
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t ph = 0;
       bool ok = true;
       for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x) {
-        const int2 tile = p.tiles[t];
+        const int4 tile = p.tiles[t];
         const int ra = tile.x * BLK, rb = (tile.y & 0xFFFF) * BLK;
         const int k0 = (tile.y >> 16) * p.k_slice;
         for (int kc = 0; kc < total_k; ++kc) {
@@ -264,13 +267,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int acc = 0;
     uint32_t aph = 0;
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
-      const int2 tile = p.tiles[t];
+      const int4 tile = p.tiles[t];
       const int tj = tile.y & 0xFFFF, slice = tile.y >> 16;
       float2 h0[16], l0[16], h1[16], l1[16];
       float2* gh = nullptr;
       float2* gl = nullptr;
       if (p.mode == 1) {
-        const int64_t off = packed_block(tile.x, tj, p.nb) * (int64_t)(BLK * BLK) +
+        const int64_t off = (int64_t)tile.z * (BLK * BLK) +
                             (int64_t)(colh * 64) * BLK + row;
         gh = p.g_hi + off;
         gl = comp ? p.g_lo + off : nullptr;
@@ -485,6 +488,42 @@ cudaError_t launch_gram_tc(osar_ctx* ctx) {
   p.nb = ctx->nb;
   p.err = &ctx->scal->error;
   return launch_tc(ctx, ctx->map_a_rows1, ctx->map_a_rows2, p, KCL_GRAM);
+}
+
+bool encode_plane_map(CUtensorMap* m, void* base, int cols, int rows,
+                      int planes, int box_planes, std::string* err) {
+  return encode_planes(m, base, cols, rows, planes, box_planes, err);
+}
+
+// Gram update over an explicit tile list (used by the batching form, whose
+// tiles span many scenes' stacked operand rows and packed Gram blocks).
+cudaError_t launch_gram_tc_tiles(cudaStream_t st, int sm_count,
+                                 const CUtensorMap& m1, const CUtensorMap& m2,
+                                 const int4* tiles, int n_tiles, float2* g_hi,
+                                 float2* g_lo, int kp, int* err) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(
+        k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  TcParams p = {};
+  p.tiles = tiles;
+  p.n_tiles = n_tiles;
+  p.k_chunks = kp / KC;
+  p.k_slice = p.k_chunks;
+  p.a_lo = 3;
+  p.b_lo = 3;
+  p.neg_second = 0;
+  p.mode = 1;
+  p.g_hi = g_hi;
+  p.g_lo = g_lo;
+  p.err = err;
+  const int grid = n_tiles < sm_count ? n_tiles : sm_count;
+  if (grid <= 0) return cudaSuccess;
+  k_tc_cgemm<<<grid, TC_THREADS, TC_SMEM, st>>>(m1, m2, p);
+  return cudaGetLastError();
 }
 
 }  // namespace osar

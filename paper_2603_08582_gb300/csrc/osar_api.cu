@@ -118,8 +118,8 @@ osar_status validate(const osar_config* c, std::string* why) {
 }
 
 void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
-                  std::vector<int>& seg_begin, std::vector<int2>& gram_tiles,
-                  std::vector<int2>& dict_tiles) {
+                  std::vector<int>& seg_begin, std::vector<int4>& gram_tiles,
+                  std::vector<int4>& dict_tiles) {
   const int nb = ctx->nb;
   // matvec segments: runs of S blocks of one block column
   int64_t target = (int64_t)ctx->sm_count * 2 * 12;
@@ -142,7 +142,8 @@ void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
     for (int bj = bi; bj < nb; bj += SB)
       for (int I = bi; I < bi + SB && I < nb; ++I)
         for (int J = (bj > I ? bj : I); J < bj + SB && J < nb; ++J)
-          gram_tiles.push_back(make_int2(I, J));
+          gram_tiles.push_back(
+              make_int4(I, J, (int)packed_block(I, J, nb), 0));
   if (ctx->dict) {
     // split-K slices only on the tensor-core path; the (atom, frequency)
     // tiles of one atom block are adjacent so its dictionary rows stay in L2
@@ -150,7 +151,7 @@ void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
     for (int I = 0; I < nb; ++I)
       for (int sl = 0; sl < S; ++sl)
         for (int J = 0; J < ctx->Kp / BLK; ++J)
-          dict_tiles.push_back(make_int2(I, J | (sl << 16)));
+          dict_tiles.push_back(make_int4(I, J | (sl << 16), 0, 0));
   }
 }
 
@@ -195,7 +196,7 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
 
   std::vector<int4> segs;
   std::vector<int> seg_begin;
-  std::vector<int2> gtiles, dtiles;
+  std::vector<int4> gtiles, dtiles;
   build_tables(ctx, segs, seg_begin, gtiles, dtiles);
   ctx->nseg = (int)segs.size();
   ctx->n_dict_tiles = (int)dtiles.size();
@@ -230,8 +231,8 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   AL(ctx->d32, 8 * Kp);
   AL(ctx->segs, sizeof(int4) * segs.size());
   AL(ctx->seg_begin, sizeof(int) * seg_begin.size());
-  AL(ctx->gram_tiles, sizeof(int2) * gtiles.size());
-  if (ctx->dict) AL(ctx->dict_tiles, sizeof(int2) * (dtiles.size() ? dtiles.size() : 1));
+  AL(ctx->gram_tiles, sizeof(int4) * gtiles.size());
+  if (ctx->dict) AL(ctx->dict_tiles, sizeof(int4) * (dtiles.size() ? dtiles.size() : 1));
   if (ctx->prec == OSAR_SPLIT_BF16) {
     AL(ctx->Apl, 2 * 6 * Mp * Kp);
     if (ctx->dict) {
@@ -266,11 +267,11 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
                         ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->gram_tiles, gtiles.data(),
-                        sizeof(int2) * gtiles.size(), cudaMemcpyHostToDevice,
+                        sizeof(int4) * gtiles.size(), cudaMemcpyHostToDevice,
                         ctx->stream);
   if (e == cudaSuccess && ctx->dict && !dtiles.empty())
     e = cudaMemcpyAsync(ctx->dict_tiles, dtiles.data(),
-                        sizeof(int2) * dtiles.size(), cudaMemcpyHostToDevice,
+                        sizeof(int4) * dtiles.size(), cudaMemcpyHostToDevice,
                         ctx->stream);
   // initial scalars and power vector v = 1/sqrt(M) on the M real atoms
   DevScalars s0 = {};

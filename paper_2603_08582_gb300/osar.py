@@ -39,6 +39,10 @@ EXPORTS = [
     "osar_profile_read", "osar_profile_reset", "osar_launch_count",
     "osar_device_bytes", "osar_save", "osar_load", "osar_last_error",
     "osar_version",
+    "osar_batch_create", "osar_batch_destroy", "osar_batch_push",
+    "osar_batch_iterate", "osar_batch_get_coeffs", "osar_batch_get_state",
+    "osar_batch_autotune", "osar_batch_info", "osar_batch_synchronize",
+    "osar_batch_last_error",
 ]
 
 
@@ -108,6 +112,17 @@ def load_library(path: str = LIB_PATH):
         "osar_load": (I32, [C.c_char_p, C.POINTER(OsarConfig), C.POINTER(P)]),
         "osar_last_error": (C.c_char_p, [P]),
         "osar_version": (C.c_char_p, []),
+        "osar_batch_create": (I32, [C.POINTER(OsarConfig), I32, P, C.POINTER(P)]),
+        "osar_batch_destroy": (I32, [P]),
+        "osar_batch_push": (I32, [P, C.POINTER(I32), D, D, I32]),
+        "osar_batch_iterate": (I32, [P, I32, C.c_double, C.POINTER(I32)]),
+        "osar_batch_get_coeffs": (I32, [P, I32, D]),
+        "osar_batch_get_state": (I32, [P, I32, C.POINTER(I32), D, D, D]),
+        "osar_batch_autotune": (I32, [P, C.POINTER(I32)]),
+        "osar_batch_info": (I32, [P, C.POINTER(I32), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int64), C.POINTER(I32)]),
+        "osar_batch_synchronize": (I32, [P]),
+        "osar_batch_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -349,6 +364,93 @@ class Osar:
         if st != OSAR_OK:
             raise OsarError(st, lib.osar_last_error(None).decode())
         return cls(cfg, _handle=h)
+
+
+class OsarBatch:
+    """Many independent online reconstructions of uneven size (batching
+    form); scene s behaves like its own Osar context."""
+
+    def __init__(self, cfgs, stream=None):
+        self._lib = load_library()
+        self._h = None
+        self.cfgs = list(cfgs)
+        arr = (OsarConfig * len(self.cfgs))(*self.cfgs)
+        h = C.c_void_p()
+        st = self._lib.osar_batch_create(arr, len(self.cfgs),
+                                         C.c_void_p(stream) if stream else None,
+                                         C.byref(h))
+        if st != OSAR_OK:
+            raise OsarError(st, self._lib.osar_batch_last_error(None).decode())
+        self._h = h
+        self.n_scenes = len(self.cfgs)
+        self.m_atoms = [c.nx * c.ny for c in self.cfgs]
+        self.n_freq = [c.n_freq for c in self.cfgs]
+        self.stride = max(self.n_freq)
+
+    def _check(self, st):
+        if st != OSAR_OK:
+            raise OsarError(st, self._lib.osar_batch_last_error(self._h).decode())
+
+    def close(self):
+        if self._h is not None:
+            self._lib.osar_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, active, gammas, data):
+        """active: n_scenes flags; gammas: n_scenes x 3; data: list of the
+        active scenes' pulse samples (entries of inactive scenes ignored)."""
+        S = self.n_scenes
+        act = np.ascontiguousarray(np.asarray(active, dtype=np.int32))
+        gam = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64).reshape(S, 3))
+        d = np.zeros((S, self.stride), dtype=np.complex128)
+        for s in range(S):
+            if act[s]:
+                d[s, :self.n_freq[s]] = data[s]
+        self._check(self._lib.osar_batch_push(
+            self._h, act.ctypes.data_as(C.POINTER(C.c_int32)), _dptr(gam),
+            _dptr(d.view(np.float64)), self.stride))
+
+    def iterate(self, max_iters, tol=0.0, want_counts=True):
+        cnt = np.zeros(self.n_scenes, dtype=np.int32)
+        self._check(self._lib.osar_batch_iterate(
+            self._h, int(max_iters), float(tol),
+            cnt.ctypes.data_as(C.POINTER(C.c_int32)) if want_counts else None))
+        return cnt if want_counts else None
+
+    def coeffs(self, scene):
+        out = np.empty(self.m_atoms[scene], dtype=np.complex128)
+        self._check(self._lib.osar_batch_get_coeffs(self._h, int(scene),
+                                                    _dptr(out.view(np.float64))))
+        return out
+
+    def state(self, scene):
+        n = C.c_int32()
+        lip, lam, t = C.c_double(), C.c_double(), C.c_double()
+        self._check(self._lib.osar_batch_get_state(self._h, int(scene), C.byref(n),
+                                                   C.byref(lip), C.byref(lam), C.byref(t)))
+        return {"n": n.value, "lipschitz": lip.value, "lambda": lam.value, "t": t.value}
+
+    def autotune(self):
+        ch = C.c_int32()
+        self._check(self._lib.osar_batch_autotune(self._h, C.byref(ch)))
+        return ch.value
+
+    def info(self):
+        n, seg = C.c_int32(), C.c_int32()
+        b, l = C.c_int64(), C.c_int64()
+        self._check(self._lib.osar_batch_info(self._h, C.byref(n), C.byref(b),
+                                              C.byref(l), C.byref(seg)))
+        return {"n_scenes": n.value, "device_bytes": b.value, "launches": l.value,
+                "segment_blocks": seg.value}
+
+    def synchronize(self):
+        self._check(self._lib.osar_batch_synchronize(self._h))
 
 
 def version() -> str:
