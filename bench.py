@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-pulses", type=int, default=2)
+    ap.add_argument("--forms", action="store_true",
+                    help="also time the other configurations (32x32 FP64, the "
+                         "64x64 adjoint, the 96-scene batch, the 256x256 form)")
     ap.add_argument("--workload", choices=["c2", "probe8k"], default="c2",
                     help="c2: the 128x128 headline workload; probe8k: a "
                          "64x128 pixel-basis scene (M = 8192, 272 MB packed "
@@ -140,7 +143,7 @@ def profiled_traffic(kind: str):
     vals = {}
     for ln in text.splitlines():
         if ":" in ln and ln.strip().startswith("- "):
-            k, v = ln.strip()[2:].split(":", 1)
+            k, v = ln.strip()[2:].rsplit(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("matvec.cuh sha256[:16]") != kernel_source_hash():
         return None
@@ -200,9 +203,9 @@ def run_ours(args):
     W, K = args.warmup, args.steps
     stream = torch.cuda.Stream()
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream)
-    total = W + 2 * K
+    total = W + K + 1
     if total > w.n_pulses:
-        raise SystemExit(f"warmup + 2*steps must be <= {w.n_pulses} pulses")
+        raise SystemExit(f"warmup + steps must be < {w.n_pulses} pulses")
     track, data = pulse_data(ctx, w, total)
     d_dev = torch.from_numpy(data).to(f"cuda:{local_rank}")
     torch.cuda.synchronize()
@@ -240,17 +243,38 @@ def run_ours(args):
         prof = {k: ctx.profile_read(k) for k in osar.KERNEL_CLASSES}
         ctx.profile_enable(False)
 
-        # end to end: host pulses in, coefficients back, every step
-        pinned = torch.from_numpy(data[W + K:W + 2 * K].copy()).pin_memory().numpy()
+        # time to tolerance: the next pulse with its burst run until the
+        # stop rule |c - z| <= tol |c| holds (at most 2000 steps)
+        ev2 = torch.cuda.Event(enable_timing=True)
+        ev3 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev2.record(stream)
+        ctx.push_pulse_dev(track[W + K], d_ptr + (W + K) * row)
+        steps_tt = ctx.iterate(2000, TOL)
+        ev3.record(stream)
+        torch.cuda.synchronize()
+        ttt = {"tol": TOL, "pulse": W + K + 1, "steps": int(steps_tt),
+               "ms": round(ev2.elapsed_time(ev3), 3),
+               "converged": bool(steps_tt < 2000)}
+        ctx.close()
+
+        # end to end on a second context, the same pulses: host data in,
+        # coefficients back, every step
+        ctx_e = make_ctx(w, "split_bf16", stream.cuda_stream)
+        for s in range(W):
+            ctx_e.push_pulse_dev(track[s], d_ptr + s * row)
+            ctx_e.iterate(INNER_STEPS, TOL, want_count=False)
+        pinned = torch.from_numpy(data[W:W + K].copy()).pin_memory().numpy()
         iters = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for q, s in enumerate(range(W + K, W + 2 * K)):
-            ctx.push_pulse(track[s], pinned[q])
-            iters.append(ctx.iterate(INNER_STEPS, TOL))
-            c_hat = ctx.coeffs()
+        for q, s in enumerate(range(W, W + K)):
+            ctx_e.push_pulse(track[s], pinned[q])
+            iters.append(ctx_e.iterate(INNER_STEPS, TOL))
+            c_hat = ctx_e.coeffs()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
+        ctx_e.close()
 
     ms_t = torch.tensor([ms], device=f"cuda:{local_rank}")
     e2e_t = torch.tensor([e2e_s], device=f"cuda:{local_rank}")
@@ -324,6 +348,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": w.n_freq * 16 + 24,
                 "d2h_bytes_per_step": w.m_atoms * 16 + 4,
                 "mean_iters_per_pulse": round(float(np.mean(iters)), 2)},
+        "time_to_tol": ttt,
         "gpu_launches": int(launches),
         "roofline": roofline,
         "tensor_rooflines": tens,
@@ -334,6 +359,8 @@ def run_ours(args):
         line["speedup_vs_fp64_path"] = round(value / fp64["value"], 2)
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if args.forms and rank == 0:
+        line["forms"] = run_forms(stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -367,6 +394,122 @@ def run_fp64_path(w, track, data, stream, pulses):
     return {"value": round(pulses / (ms / 1e3), 4), "unit": "pulses/s",
             "pulses_timed": pulses, "ms_per_pulse": round(ms / pulses, 2),
             "dtype": "f64"}
+
+
+# -------------------------------------------------------- other forms ---
+
+def _time(fn, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _pixel_ctx(w, prec, stream):
+    from paper_2603_08582_gb300 import osar
+    return osar.Osar(osar.make_config(
+        w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz, pixel_m=w.pixel_m,
+        precision=prec, lam=w.lambda_rel, stream=stream.cuda_stream))
+
+
+def _sim_pulses(ctx, w, n):
+    from paper_2603_08582_gb300 import synth
+    track = synth.workload_track(w)
+    c_true = synth.workload_scene(w)
+    noise = synth.unit_noise(w.n_pulses, w.n_freq, w.seed)
+    clean = np.stack([ctx.simulate_pulse(track[s], c_true) for s in range(n)])
+    return track, clean + synth.scale_noise(clean, noise[:n], w.snr_db), c_true
+
+
+def run_forms(stream):
+    """Pulses/s (or gradient time) of the other configurations, device-timed
+    with CUDA events on the library's stream."""
+    import torch
+    from paper_2603_08582_gb300 import osar, synth
+    out = {}
+    wl = synth.workloads()
+    with torch.cuda.stream(stream):
+        # 32 x 32 pixel basis, FP64 (plain method) and split-BF16
+        w = wl["c1_32x32_fp64"]
+        for prec in ("fp64", "split_bf16"):
+            ctx = _pixel_ctx(w, prec, stream)
+            track, data, _ = _sim_pulses(ctx, w, w.n_pulses)
+
+            def run(c=ctx, tr=track, dd=data):
+                for s in range(w.n_pulses):
+                    c.push_pulse(tr[s], dd[s])
+                    c.iterate(w.inner_steps, 0.0, want_count=False)
+            ms = _time(run, stream)
+            out[f"c1_32x32_{prec}"] = {"pulses": w.n_pulses, "ms": round(ms, 2),
+                                       "pulses_per_s": round(w.n_pulses / (ms / 1e3), 1)}
+            ctx.close()
+        # 64 x 64 differentiation form: gradient through T = 64 steps
+        w = wl["c3_64x64_adjoint"]
+        T, C = w.extra["unroll_T"], w.extra["checkpoint_every"]
+        for prec in ("fp64", "fp32"):
+            ctx = _pixel_ctx(w, prec, stream)
+            track, data, c_true = _sim_pulses(ctx, w, w.n_pulses)
+            for s in range(w.n_pulses):
+                ctx.push_pulse(track[s], data[s])
+            st = ctx.state()
+            c0 = np.zeros(w.m_atoms, complex)
+            ctx.unroll_grad(T, C, st["lambda"], 1.0 / st["lipschitz"], c0, c_true)
+            ms = _time(lambda: ctx.unroll_grad(T, C, st["lambda"], 1.0 / st["lipschitz"],
+                                               c0, c_true), stream)
+            out[f"c3_adjoint_{prec}"] = {"T": T, "checkpoint_every": C,
+                                         "ms_per_gradient": round(ms, 3)}
+            ctx.close()
+        # 96 uneven scenes in one batch: scene-pulses per second
+        ws = synth.batch_workloads(96)
+        tracks = [synth.workload_track(x) for x in ws]
+        rng = np.random.default_rng(0)
+        for prec, pulses in (("split_bf16", 6), ("fp32", 6), ("fp64", 1)):
+            cfgs = [osar.make_config(x.nx, x.ny, x.n_freq, x.f_lo_hz, x.f_hi_hz,
+                                     precision=prec) for x in ws]
+            b = osar.OsarBatch(cfgs, stream=stream.cuda_stream)
+            seg = b.autotune()
+            datas = [[rng.standard_normal(x.n_freq) + 1j * rng.standard_normal(x.n_freq)
+                      for x in ws] for _ in range(pulses + 1)]
+            b.push([1] * len(ws), np.stack([t[0] for t in tracks]), datas[0])
+            b.iterate(20, 0.0, want_counts=False)
+
+            def runb(bb=b, dd=datas):
+                for s in range(1, pulses + 1):
+                    bb.push([1] * len(ws), np.stack([t[s] for t in tracks]), dd[s])
+                    bb.iterate(20, 0.0, want_counts=False)
+            ms = _time(runb, stream)
+            out[f"c4_batch96_{prec}"] = {
+                "batch_pulses": pulses, "scene_pulses_per_s": round(96 * pulses / (ms / 1e3), 1),
+                "ms_per_batch_pulse": round(ms / pulses, 2), "segment_blocks": seg,
+                "device_gb": round(b.info()["device_bytes"] / 1e9, 2)}
+            b.close()
+        if "c4_batch96_fp64" in out:
+            base = out["c4_batch96_fp64"]["scene_pulses_per_s"]
+            for prec in ("split_bf16", "fp32"):
+                out[f"c4_batch96_{prec}"]["speedup_vs_fp64"] = round(
+                    out[f"c4_batch96_{prec}"]["scene_pulses_per_s"] / base, 1)
+        # 256 x 256 large online form, split-BF16, 10 steps per pulse
+        w = wl["c5_256x256_split_bf16"]
+        ctx = _pixel_ctx(w, "split_bf16", stream)
+        track, data, _ = _sim_pulses(ctx, w, 5)
+        ctx.push_pulse(track[0], data[0])
+        ctx.iterate(w.inner_steps, 0.0, want_count=False)
+
+        def run5():
+            for s in range(1, 5):
+                ctx.push_pulse(track[s], data[s])
+                ctx.iterate(w.inner_steps, 0.0, want_count=False)
+        ms = _time(run5, stream)
+        out["c5_256x256_split_bf16"] = {"pulses": 4, "ms_per_pulse": round(ms / 4, 2),
+                                        "pulses_per_s": round(4 / (ms / 1e3), 2),
+                                        "device_gb": round(ctx.device_bytes() / 1e9, 1)}
+        ctx.close()
+    return out
 
 
 # ------------------------------------------------------------ CPU oracle ---

@@ -67,7 +67,7 @@ struct osar_batch {
   double2* part = nullptr;          // per finalize item
   double* bmax = nullptr;
   void* g_hi = nullptr;
-  float2* g_lo = nullptr;
+  __nv_bfloat162* g_lo = nullptr;
   void* segpart = nullptr;
   void* tilepart = nullptr;
   int4* segs = nullptr;             // (J, I0, I1, slot), scene-local J, I
@@ -110,7 +110,7 @@ bool batch_make_tensor_maps(osar_batch* B, std::string* err);
 cudaError_t launch_gram_tc_tiles(cudaStream_t st, int sm_count,
                                  const CUtensorMap& m1, const CUtensorMap& m2,
                                  const int4* tiles, int n_tiles, float2* g_hi,
-                                 float2* g_lo, int kp, int* err);
+                                 __nv_bfloat162* g_lo, int kp, int* err);
 cudaError_t launch_gram_simt_tiles(cudaStream_t st, int prec, const void* A,
                                    int kp, void* g_hi, const int4* tiles,
                                    int n_tiles);

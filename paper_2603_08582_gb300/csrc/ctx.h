@@ -77,7 +77,8 @@ struct osar_ctx {
   double2* d_dev = nullptr;    // staged pulse data (Kp)
   ulonglong2* turns = nullptr; // per-pixel fixed-point phase terms (Np)
   void* g_hi = nullptr;        // packed Gram, float2 or double2 per entry
-  float2* g_lo = nullptr;      // compensation word (split-BF16, compensated)
+  __nv_bfloat162* g_lo = nullptr;  // TwoSum compensation word (split-BF16),
+                                   // bf16 (re, im) per entry
   void* segpart = nullptr;     // matvec segment partials (nseg x BLK)
   void* tilepart = nullptr;    // matvec per-block partials (nblk x BLK)
   int4* segs = nullptr;        // matvec work items (J, I0, I1, slot)

@@ -41,6 +41,22 @@ namespace {
 //   t' = (1 + sqrt(1 + 4 t^2)) / 2,  z' = c + (t - 1)/t' (c - c_prev).
 // The last CTA then sets t <- t', counts the step and applies the stop rule
 // |c - z|_2 <= tol |c|_2 to the whole vector.
+// Shrink factor max(0, 1 - alpha/|u|): FP64 on the FP64 path; on the
+// FP32-Gram paths (whose matvec is FP32 anyway) an FP32 reciprocal square
+// root, since GB300's FP64 pipes are ~1/64 of its FP32 rate.
+template <typename T2>
+__device__ __forceinline__ double shrink_keep(double mag2, double alpha);
+template <>
+__device__ __forceinline__ double shrink_keep<double2>(double mag2, double alpha) {
+  const double mag = sqrt(mag2);
+  return mag > alpha ? 1.0 - alpha / mag : 0.0;
+}
+template <>
+__device__ __forceinline__ double shrink_keep<float2>(double mag2, double alpha) {
+  if (!(mag2 > alpha * alpha)) return 0.0;
+  return (double)(1.0f - (float)alpha * rsqrtf((float)mag2));
+}
+
 template <typename T2, typename Acc>
 __global__ void __launch_bounds__(FIN_THREADS)
     k_fista_finalize(const T2* __restrict__ segpart,
@@ -50,19 +66,23 @@ __global__ void __launch_bounds__(FIN_THREADS)
                      double2* __restrict__ z, T2* __restrict__ zt,
                      double2* __restrict__ part, DevScalars* sc) {
   if (sc->converged) return;
+  __shared__ double sh[3];  // tau, alpha, beta
+  if (threadIdx.x == 0) {
+    const double t = sc->t, tau = sc->tau;
+    const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    sh[0] = tau;
+    sh[1] = sc->lambda * tau;
+    sh[2] = (t - 1.0) / t_next;
+  }
   const int K = blockIdx.x, i = threadIdx.x, idx = K * BLK + i;
   const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
   double p0 = 0.0, p1 = 0.0;
   if (i < BLK) {
-    const double tau = sc->tau, lam = sc->lambda, t = sc->t;
-    const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    const double beta = (t - 1.0) / t_next;
+    const double tau = sh[0], alpha = sh[1], beta = sh[2];
     const double2 zk = z[idx], bk = b[idx], cprev = c[idx];
     const double ur = zk.x - tau * (y.x - bk.x);
     const double ui = zk.y - tau * (y.y - bk.y);
-    const double mag = hypot(ur, ui);
-    const double alpha = lam * tau;
-    const double keep = mag > alpha ? 1.0 - alpha / mag : 0.0;
+    const double keep = shrink_keep<T2>(ur * ur + ui * ui, alpha);
     const double cr = ur * keep, ci = ui * keep;
     const double2 zn = make_double2(cr + beta * (cr - cprev.x),
                                     ci + beta * (ci - cprev.y));
@@ -89,17 +109,17 @@ __global__ void __launch_bounds__(FIN_THREADS)
   }
 }
 
-// Power step: w = A v; the last CTA forms mu = Re(v^H A v) (v has unit norm),
-// normalises v <- w / |w|, and on the last step of a pulse sets
+// Power step: w = A v; the last CTA forms mu = Re(v^H A v) (v has unit
+// norm) and 1/|w|, and on the last step of a pulse sets
 // L_n = max(L_{n-1}, (1 + margin) mu) and tau = 1/L_n.
 template <typename T2, typename Acc>
 __global__ void __launch_bounds__(FIN_THREADS)
     k_power_finalize(const T2* __restrict__ segpart,
                      const T2* __restrict__ tilepart,
                      const int* __restrict__ seg_begin, int nb,
-                     double2* __restrict__ v, T2* __restrict__ vt,
-                     double2* __restrict__ w, double2* __restrict__ part,
-                     DevScalars* sc, int last_step, double margin) {
+                     const double2* __restrict__ v, double2* __restrict__ w,
+                     double2* __restrict__ part, DevScalars* sc, int last_step,
+                     double margin) {
   const int K = blockIdx.x, i = threadIdx.x, idx = K * BLK + i;
   const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
   double p0 = 0.0, p1 = 0.0;
@@ -113,12 +133,10 @@ __global__ void __launch_bounds__(FIN_THREADS)
   if (i == 0) part[K] = s;
   if (!last_block(&sc->done, gridDim.x)) return;
   const double2 tot = sum_parts(part, nb);
-  __shared__ double inv_s;
   if (i == 0) {
     const double mu = tot.x;
     sc->mu = mu;
-    inv_s = tot.y > 0.0 ? 1.0 / sqrt(tot.y) : 0.0;
-    sc->inv_norm = inv_s;
+    sc->inv_norm = tot.y > 0.0 ? 1.0 / sqrt(tot.y) : 0.0;
     if (last_step) {
       const double l = (1.0 + margin) * mu;
       if (l > sc->lip) sc->lip = l;
@@ -126,19 +144,23 @@ __global__ void __launch_bounds__(FIN_THREADS)
     }
     sc->done = 0;
   }
-  __syncthreads();
-  const double inv = inv_s;
-  if (inv > 0.0) {
-    for (int k = i; k < nb * BLK; k += blockDim.x) {
-      const double2 yw = __ldcg(w + k);
-      const double2 nv = make_double2(yw.x * inv, yw.y * inv);
-      v[k] = nv;
-      T2 t;
-      t.x = nv.x;
-      t.y = nv.y;
-      vt[k] = t;
-    }
-  }
+}
+
+// v <- w / |w| and its working-precision copy (v kept when |w| = 0).
+template <typename T2>
+__global__ void k_power_normalize(const double2* __restrict__ w,
+                                  double2* __restrict__ v, T2* __restrict__ vt,
+                                  int n, const DevScalars* __restrict__ sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double s = sc->inv_norm;
+  if (i >= n || s == 0.0) return;
+  const double2 y = w[i];
+  const double2 nv = make_double2(y.x * s, y.y * s);
+  v[i] = nv;
+  T2 t;
+  t.x = nv.x;
+  t.y = nv.y;
+  vt[i] = t;
 }
 
 // y = A x for osar_gram_apply.
@@ -328,7 +350,7 @@ __device__ __forceinline__ int64_t stored_index(int i, int j, int nb,
 // packed upper blocks plus the optional compensation word.
 template <typename T2>
 __global__ void k_gram_expand(const T2* __restrict__ G,
-                              const float2* __restrict__ Glo, int nb, int M,
+                              const __nv_bfloat162* __restrict__ Glo, int nb, int M,
                               int r0, int rows, double2* __restrict__ out) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (int64_t)rows * M) return;
@@ -338,15 +360,16 @@ __global__ void k_gram_expand(const T2* __restrict__ G,
   const int64_t o = stored_index(i, j, nb, &upper);
   double re = (double)G[o].x, im = (double)G[o].y;
   if (Glo) {
-    re += (double)Glo[o].x;
-    im += (double)Glo[o].y;
+    const float2 lo = __bfloat1622float2(Glo[o]);
+    re += (double)lo.x;
+    im += (double)lo.y;
   }
   out[gid] = make_double2(re, upper ? im : -im);
 }
 
 template <typename T2>
 __global__ void k_gram_entries(const T2* __restrict__ G,
-                               const float2* __restrict__ Glo, int nb,
+                               const __nv_bfloat162* __restrict__ Glo, int nb,
                                const int2* __restrict__ rc, int count,
                                double2* __restrict__ out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -355,8 +378,9 @@ __global__ void k_gram_entries(const T2* __restrict__ G,
   const int64_t o = stored_index(rc[q].x, rc[q].y, nb, &upper);
   double re = (double)G[o].x, im = (double)G[o].y;
   if (Glo) {
-    re += (double)Glo[o].x;
-    im += (double)Glo[o].y;
+    const float2 lo = __bfloat1622float2(Glo[o]);
+    re += (double)lo.x;
+    im += (double)lo.y;
   }
   out[q] = make_double2(re, upper ? im : -im);
 }
@@ -446,18 +470,23 @@ cudaError_t launch_power_steps(osar_ctx* ctx, int steps) {
     ProfEvent ev;
     prof_begin(ctx, KCL_POWFIN, &ev);
     const int last = s == steps - 1 ? 1 : 0;
-    if (ctx->prec == OSAR_FP64)
+    if (ctx->prec == OSAR_FP64) {
       k_power_finalize<double2, double><<<nb, FIN_THREADS, 0, ctx->stream>>>(
           (const double2*)ctx->segpart, (const double2*)ctx->tilepart,
-          ctx->seg_begin, ctx->nb, ctx->v, (double2*)ctx->vt, ctx->w, ctx->part,
-          ctx->scal, last, ctx->cfg.lipschitz_margin);
-    else
+          ctx->seg_begin, ctx->nb, ctx->v, ctx->w, ctx->part, ctx->scal, last,
+          ctx->cfg.lipschitz_margin);
+      k_power_normalize<double2><<<nb, BLK, 0, ctx->stream>>>(
+          ctx->w, ctx->v, (double2*)ctx->vt, ctx->Mp, ctx->scal);
+    } else {
       k_power_finalize<float2, float><<<nb, FIN_THREADS, 0, ctx->stream>>>(
           (const float2*)ctx->segpart, (const float2*)ctx->tilepart,
-          ctx->seg_begin, ctx->nb, ctx->v, (float2*)ctx->vt, ctx->w, ctx->part,
-          ctx->scal, last, ctx->cfg.lipschitz_margin);
+          ctx->seg_begin, ctx->nb, ctx->v, ctx->w, ctx->part, ctx->scal, last,
+          ctx->cfg.lipschitz_margin);
+      k_power_normalize<float2><<<nb, BLK, 0, ctx->stream>>>(
+          ctx->w, ctx->v, (float2*)ctx->vt, ctx->Mp, ctx->scal);
+    }
     prof_end(ctx, &ev);
-    ctx->launches++;
+    ctx->launches += 2;
   }
   return cudaGetLastError();
 }

@@ -73,33 +73,33 @@ struct TcParams {
   int part_ld;
   int64_t part_slice;
   float2* g_hi;
-  float2* g_lo;
+  __nv_bfloat162* g_lo;  // compensation word, bf16 (re, im), or NULL
   int nb;
   int* err;
 };
 
 // One 16-column piece of the Gram read-modify-write for this thread's row:
-// (hi, lo) += delta with an error-free TwoSum.  Blocks are column-major, so
-// entry (row, c) is at c * 128 + row and the 32 lanes of a warp (32
-// consecutive rows) touch 256 contiguous bytes per access.
-__device__ __forceinline__ void gram_piece(float2* gh, float2* gl,
+// hi + lo += delta with an error-free TwoSum, the new rounding error kept as
+// the bf16 compensation word.  (Keeping 8 bits of an error that is at most
+// half an FP32 ulp of hi still leaves the pair 2^-33-accurate, far below the
+// 2^-17 of the split-BF16 products, and saves a quarter of the traffic.)
+// Blocks are column-major, so entry (row, c) is at c * 128 + row and the 32
+// lanes of a warp (32 consecutive rows) touch contiguous bytes per access.
+__device__ __forceinline__ void gram_piece(float2* gh, __nv_bfloat162* gl,
                                            const float2 (&h)[16],
-                                           const float2 (&l)[16],
+                                           const __nv_bfloat162 (&l)[16],
                                            const float* re, const float* im,
                                            bool comp) {
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     float2 hv = h[q];
     if (comp) {
-      float2 lv = l[q];
-      float s, e;
-      two_sum(hv.x, __fadd_rn(re[q], lv.x), s, e);
-      hv.x = s;
-      lv.x = e;
-      two_sum(hv.y, __fadd_rn(im[q], lv.y), s, e);
-      hv.y = s;
-      lv.y = e;
-      gl[q * BLK] = lv;
+      const float2 lv = __bfloat1622float2(l[q]);
+      float s0, e0, s1, e1;
+      two_sum(hv.x, __fadd_rn(re[q], lv.x), s0, e0);
+      two_sum(hv.y, __fadd_rn(im[q], lv.y), s1, e1);
+      hv = make_float2(s0, s1);
+      gl[q * BLK] = __floats2bfloat162_rn(e0, e1);
     } else {
       hv.x += re[q];
       hv.y += im[q];
@@ -108,8 +108,9 @@ __device__ __forceinline__ void gram_piece(float2* gh, float2* gl,
   }
 }
 
-__device__ __forceinline__ void load_piece(const float2* gh, const float2* gl,
-                                           float2 (&h)[16], float2 (&l)[16],
+__device__ __forceinline__ void load_piece(const float2* gh,
+                                           const __nv_bfloat162* gl,
+                                           float2 (&h)[16], __nv_bfloat162 (&l)[16],
                                            bool comp) {
 #pragma unroll
   for (int q = 0; q < 16; ++q) h[q] = gh[q * BLK];
@@ -269,9 +270,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
       const int4 tile = p.tiles[t];
       const int tj = tile.y & 0xFFFF, slice = tile.y >> 16;
-      float2 h0[16], l0[16], h1[16], l1[16];
+      float2 h0[16], h1[16];
+      __nv_bfloat162 l0[16], l1[16];
       float2* gh = nullptr;
-      float2* gl = nullptr;
+      __nv_bfloat162* gl = nullptr;
       if (p.mode == 1) {
         const int64_t off = (int64_t)tile.z * (BLK * BLK) +
                             (int64_t)(colh * 64) * BLK + row;
@@ -500,7 +502,7 @@ bool encode_plane_map(CUtensorMap* m, void* base, int cols, int rows,
 cudaError_t launch_gram_tc_tiles(cudaStream_t st, int sm_count,
                                  const CUtensorMap& m1, const CUtensorMap& m2,
                                  const int4* tiles, int n_tiles, float2* g_hi,
-                                 float2* g_lo, int kp, int* err) {
+                                 __nv_bfloat162* g_lo, int kp, int* err) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(

@@ -221,7 +221,7 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   AL(ctx->turns, 16 * Np);
   AL(ctx->g_hi, cplx * bb * ctx->nblk);
   if (ctx->prec == OSAR_SPLIT_BF16 && cfg->compensated)
-    AL(ctx->g_lo, 8 * bb * ctx->nblk);
+    AL(ctx->g_lo, 4 * bb * ctx->nblk);
   AL(ctx->segpart, cplx * BLK * (int64_t)ctx->nseg);
   AL(ctx->tilepart, cplx * BLK * ctx->nblk);
   AL(ctx->zt, cplx * Mp);
@@ -740,7 +740,7 @@ osar_status osar_save(osar_ctx* ctx, const char* path) {
   if (!f) return fail(ctx, OSAR_E_IO, std::string("cannot open ") + path);
   CkptHeader h = {};
   std::memcpy(h.magic, "OSARCKP", 8);
-  h.version = 2;
+  h.version = 3;
   h.M = ctx->M;
   h.N = ctx->N;
   h.K = ctx->K;
@@ -765,7 +765,7 @@ osar_status osar_save(osar_ctx* ctx, const char* path) {
   if (st == OSAR_OK) st = write_dev(ctx, f, ctx->z, vec);
   if (st == OSAR_OK) st = write_dev(ctx, f, ctx->v, vec);
   if (st == OSAR_OK) st = write_dev(ctx, f, ctx->g_hi, gb);
-  if (st == OSAR_OK && ctx->g_lo) st = write_dev(ctx, f, ctx->g_lo, (size_t)8 * BLK * BLK * ctx->nblk);
+  if (st == OSAR_OK && ctx->g_lo) st = write_dev(ctx, f, ctx->g_lo, (size_t)4 * BLK * BLK * ctx->nblk);
   if (fclose(f) != 0 && st == OSAR_OK) st = fail(ctx, OSAR_E_IO, "checkpoint close failed");
   return st;
 }
@@ -778,7 +778,7 @@ osar_status osar_load(const char* path, const osar_config* cfg, osar_ctx** out) 
   if (!f) return fail(nullptr, OSAR_E_IO, std::string("cannot open ") + path);
   CkptHeader h;
   if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "OSARCKP", 8) != 0 ||
-      h.version != 2) {
+      h.version != 3) {
     fclose(f);
     return fail(nullptr, OSAR_E_IO, "not an osar checkpoint");
   }
@@ -804,7 +804,7 @@ osar_status osar_load(const char* path, const osar_config* cfg, osar_ctx** out) 
   if (st == OSAR_OK) st = read_dev(ctx, f, ctx->v, vec);
   if (st == OSAR_OK) st = read_dev(ctx, f, ctx->g_hi, gb);
   if (st == OSAR_OK && ctx->g_lo)
-    st = read_dev(ctx, f, ctx->g_lo, (size_t)8 * BLK * BLK * ctx->nblk);
+    st = read_dev(ctx, f, ctx->g_lo, (size_t)4 * BLK * BLK * ctx->nblk);
   fclose(f);
   if (st == OSAR_OK) {
     cudaError_t e = launch_set_working(ctx);

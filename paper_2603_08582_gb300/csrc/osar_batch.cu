@@ -292,7 +292,7 @@ osar_status osar_batch_create(const osar_config* cfgs, int32_t n_scenes,
   BA(B->bmax, sizeof(double) * items);
   BA(B->g_hi, cplx * BLK * BLK * blocks);
   if (prec == OSAR_SPLIT_BF16 && cfgs[0].compensated)
-    BA(B->g_lo, 8 * (size_t)BLK * BLK * blocks);
+    BA(B->g_lo, 4 * (size_t)BLK * BLK * blocks);
   BA(B->segpart, cplx * BLK * blocks);   // enough for 1-block segments
   BA(B->tilepart, cplx * BLK * blocks);
   BA(B->segs, sizeof(int4) * blocks);
