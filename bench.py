@@ -59,6 +59,23 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """Largest value of x over all ranks (the job's time is its slowest
+    rank's); identity without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank runs its own replica of the workload)."""
+    return world * units_per_rank / seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -276,15 +293,10 @@ def run_ours(args):
         e2e_s = time.perf_counter() - t0
         ctx_e.close()
 
-    ms_t = torch.tensor([ms], device=f"cuda:{local_rank}")
-    e2e_t = torch.tensor([e2e_s], device=f"cuda:{local_rank}")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    e2e_s = float(e2e_t.item())
-    value = world * K / (ms / 1e3)
-    e2e_value = world * K / e2e_s
+    ms = max_over_ranks(ms, f"cuda:{local_rank}")
+    e2e_s = max_over_ranks(e2e_s, f"cuda:{local_rank}")
+    value = whole_job_rate(K, world, ms / 1e3)
+    e2e_value = whole_job_rate(K, world, e2e_s)
 
     peaks, peak_src = measured_peaks()
     nblk = ctx_blocks(w.m_atoms)
