@@ -107,11 +107,23 @@ typedef struct {
   int32_t compensated;
   /* cudaStream_t for all work; NULL => a library-owned non-blocking stream */
   void* cuda_stream;
+  /* Dictionary models only.  1: the phase synthesis and dictionary product
+     of a pushed pulse run on a second, library-owned stream, on at most
+     synth_ctas SMs, beside the FISTA burst of the previous pulse that is
+     still streaming the Gram on cuda_stream; the pulse's data update waits
+     for them.  Results are bitwise identical to 0, which runs every step of
+     a push on cuda_stream.  Ignored while cuda_stream is being captured. */
+  int32_t overlap_synthesis;
+  /* SMs given to the overlapped dictionary product; 0 = chosen per pulse
+     from the problem shape and the last burst's length, so that the product
+     ends about when the burst does */
+  int32_t synth_ctas;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
    9.9-10.1 GHz, identity dictionary, FP64, lambda = 0.05 relative,
-   30 / 4 power steps, margin 0.01, carried momentum, compensated = 1. */
+   30 / 4 power steps, margin 0.01, carried momentum, compensated = 1,
+   overlap_synthesis = 1, synth_ctas = 0 (automatic). */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128
@@ -153,6 +165,23 @@ osar_status osar_get_coeffs(osar_ctx* ctx, double* out_c128);
 
 /* Copy c_hat (M complex128) into device memory out_dev; asynchronous. */
 osar_status osar_get_coeffs_dev(osar_ctx* ctx, void* out_dev_c128);
+
+/* Queue a copy of c_hat (M complex, interleaved doubles) into host memory
+   on the context's stream and return at once; the copy has landed when
+   osar_wait_coeffs(ctx, slot) returns.  slot in [0, OSAR_COPY_SLOTS) names
+   the copy, so that the image of pulse s can be read while pulse s + 1 is
+   already queued.  out_c128 should be pinned (page-locked) memory: CUDA
+   copies into pageable memory before returning.  The buffer belongs to the
+   caller and must stay valid until the wait.  No paper counterpart.
+   Errors: OSAR_E_INVALID (NULL buffer, slot out of range). */
+#define OSAR_COPY_SLOTS 4
+osar_status osar_get_coeffs_async(osar_ctx* ctx, double* out_c128,
+                                  int32_t slot);
+
+/* Wait for the last copy queued on `slot` by osar_get_coeffs_async (returns
+   at once when none was queued).  Errors: OSAR_E_INVALID (slot out of
+   range), OSAR_E_TIMEOUT (a bounded device wait gave up). */
+osar_status osar_wait_coeffs(osar_ctx* ctx, int32_t slot);
 
 /* Pulse count n, L_n, lambda_n, momentum t; synchronises.  Any pointer may
    be NULL. */
@@ -226,18 +255,28 @@ osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
                              double* loss, double* d_lambda, double* d_tau,
                              double* d_b_c128, double* c_T_c128);
 
-/* Wait for all work queued on the context's stream. */
+/* Wait for all work queued on the context's stream (and on its side
+   stream, see overlap_synthesis). */
 osar_status osar_synchronize(osar_ctx* ctx);
 
 /* Per-kernel device timing.  When enabled, CUDA events bracket every
    launch of the listed kernel classes on the context's stream; reading the
    counters synchronises.  kernel: 0 phase, 1 dictionary GEMM, 2 Gram GEMM,
    3 data-vector update, 4 matvec (FISTA and power steps), 5 FISTA finalize,
-   6 power finalize, 7 scalar steps.  launches / total_ms may be NULL. */
+   6 power finalize, 7 scalar steps.  launches / total_ms may be NULL.
+   Phase and dictionary launches of an overlapped push are bracketed on the
+   side stream, so their time includes sharing the GPU with the burst. */
 osar_status osar_profile_enable(osar_ctx* ctx, int32_t on);
 osar_status osar_profile_read(osar_ctx* ctx, int32_t kernel,
                               int64_t* launches, double* total_ms);
+/* Clears the timing counters, the launch count and the pass count. */
 osar_status osar_profile_reset(osar_ctx* ctx);
+
+/* Gram passes that did work since the last osar_profile_reset: one per
+   power step and one per FISTA step that ran (steps skipped after the stop
+   rule held launch a matvec that returns at once and are not counted).
+   Synchronises.  No paper counterpart: instrumentation for the roofline. */
+osar_status osar_profile_passes(osar_ctx* ctx, int64_t* passes);
 
 /* Total library kernel launches issued on this context since creation
    (or since the last reset); no synchronisation. */

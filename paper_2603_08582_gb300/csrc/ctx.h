@@ -1,12 +1,15 @@
 // Host-side context of libosar and the launchers each kernel file exports.
 #pragma once
 
+#include <cstddef>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "osar.h"
@@ -33,7 +36,16 @@ struct DevScalars {
   int32_t error;    // device-side error code (bounded waits)
   uint32_t done;    // blocks finished in the current grid (last-block steps)
   uint32_t pad;
+  uint32_t mvq[2];  // matvec work queue: next item, CTAs finished
+  unsigned long long passes;  // Gram passes that did work (instrumentation)
 };
+
+// Device address of the matvec work queue inside a device-resident
+// DevScalars (pointer arithmetic only; the host never reads it).
+inline unsigned* matvec_queue(DevScalars* s) {
+  return reinterpret_cast<unsigned*>(reinterpret_cast<char*>(s) +
+                                     offsetof(DevScalars, mvq));
+}
 
 enum KernelClass {
   KCL_PHASE = 0, KCL_DICT = 1, KCL_GRAM = 2, KCL_BUPD = 3, KCL_MATVEC = 4,
@@ -102,6 +114,17 @@ struct osar_ctx {
   CUtensorMap map_a_rows2;     // Apl, box (KC, 128, 2)
   CUtensorMap map_d_rows1;     // Dpl, box (KC, 128, 1)
   CUtensorMap map_f_rows2;     // Fpl, box (KC, 128, 2)
+  // overlapped synthesis (dictionary models): the next pulse's phase and
+  // dictionary product on a side stream while the current burst runs
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_free = nullptr;   // main: last reader of the synthesis buffers done
+  cudaEvent_t ev_synth = nullptr;  // side: synthesis of the pushed pulse done
+  cudaEvent_t ev_iters = nullptr;  // main: burst step count copied to h_iters
+  int32_t* h_iters = nullptr;      // pinned copy of the last burst's step count
+  int iters_est = 20;              // FISTA steps expected in a burst
+  bool free_stale = false;         // ev_free predates a captured push
+  // osar_get_coeffs_async completion events (OSAR_COPY_SLOTS)
+  cudaEvent_t copy_ev[4] = {};
   // pinned staging ring for pulse data (slots of Kp complex)
   static constexpr int RING = 8;
   double2* h_ring = nullptr;
@@ -149,7 +172,9 @@ cudaError_t launch_gram_simt(osar_ctx* ctx);
 
 // ---- k_gemm_tc.cu ----------------------------------------------------------
 bool make_tensor_maps(osar_ctx* ctx, std::string* err);
-cudaError_t launch_dict_tc(osar_ctx* ctx);
+// grid_cap > 0: at most that many CTAs for the product (the reduction that
+// follows is a short full-grid kernel)
+cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap);
 int dict_slices(int np);
 cudaError_t launch_gram_tc(osar_ctx* ctx);
 

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
     const double t = sc->t;
     sc->t = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
     sc->iters += 1;
+    sc->passes += 1;
     if (sc->tol > 0.0 && sqrt(tot.x) <= sc->tol * sqrt(tot.y)) sc->converged = 1;
     sc->done = 0;
   }
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
       if (l > sc->lip) sc->lip = l;
       sc->tau = sc->lip > 0.0 ? 1.0 / sc->lip : 0.0;
     }
+    sc->passes += 1;
     sc->done = 0;
   }
 }
@@ -411,9 +413,19 @@ __global__ void __launch_bounds__(FIN_THREADS)
   if (i < BLK && K * BLK + i < m_valid) y[K * BLK + i] = v;
 }
 
-unsigned grid_matvec(const osar_ctx* ctx) {
-  int g = 2 * ctx->sm_count;
-  return (unsigned)(ctx->nseg < g ? ctx->nseg : g);
+// One matvec launch: one CTA per SM (the shared-memory ring fills an SM),
+// at most one per segment.
+template <typename T>
+void launch_mv(osar_ctx* ctx, const void* xt, void* segp, void* tilep,
+               int gated) {
+  using T2 = typename Vec<T>::T2;
+  cudaFuncSetAttribute(k_matvec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Mv<T>::SMEM);
+  const unsigned grid =
+      (unsigned)(ctx->nseg < ctx->sm_count ? ctx->nseg : ctx->sm_count);
+  k_matvec<T><<<grid, Mv<T>::THREADS, Mv<T>::SMEM, ctx->stream>>>(
+      (const T2*)ctx->g_hi, (const T2*)xt, (T2*)segp, (T2*)tilep, ctx->segs,
+      ctx->nseg, ctx->nb, ctx->scal, gated, matvec_queue(ctx->scal));
 }
 
 // Launch the matvec on the working-precision copy of a vector.
@@ -421,15 +433,9 @@ void matvec(osar_ctx* ctx, const void* xt, int gated) {
   ProfEvent ev;
   prof_begin(ctx, KCL_MATVEC, &ev);
   if (ctx->prec == OSAR_FP64)
-    k_matvec<double><<<grid_matvec(ctx), 256, 0, ctx->stream>>>(
-        (const double2*)ctx->g_hi, (const double2*)xt, (double2*)ctx->segpart,
-        (double2*)ctx->tilepart, ctx->segs, ctx->nseg, ctx->nb, ctx->scal,
-        gated);
+    launch_mv<double>(ctx, xt, ctx->segpart, ctx->tilepart, gated);
   else
-    k_matvec<float><<<grid_matvec(ctx), 256, 0, ctx->stream>>>(
-        (const float2*)ctx->g_hi, (const float2*)xt, (float2*)ctx->segpart,
-        (float2*)ctx->tilepart, ctx->segs, ctx->nseg, ctx->nb, ctx->scal,
-        gated);
+    launch_mv<float>(ctx, xt, ctx->segpart, ctx->tilepart, gated);
   prof_end(ctx, &ev);
   ctx->launches++;
 }
@@ -607,13 +613,10 @@ cudaError_t launch_gram_apply_scratch(osar_ctx* ctx, const double2* x,
   void* segp = base + al(cplx * ctx->Mp);
   void* tilep = base + al(cplx * ctx->Mp) + al(cplx * BLK * (size_t)ctx->nseg);
   const unsigned g = (unsigned)((ctx->Mp + 255) / 256);
-  const unsigned gm = grid_matvec(ctx);
   if (ctx->prec == OSAR_FP64) {
     k_to_working_bounded<double2><<<g, 256, 0, ctx->stream>>>(
         x, (double2*)xt, ctx->M, ctx->Mp);
-    k_matvec<double><<<gm, 256, 0, ctx->stream>>>(
-        (const double2*)ctx->g_hi, (const double2*)xt, (double2*)segp,
-        (double2*)tilep, ctx->segs, ctx->nseg, ctx->nb, ctx->scal, 0);
+    launch_mv<double>(ctx, xt, segp, tilep, 0);
     k_apply_finalize_bounded<double2, double>
         <<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
             (const double2*)segp, (const double2*)tilep, ctx->seg_begin,
@@ -621,9 +624,7 @@ cudaError_t launch_gram_apply_scratch(osar_ctx* ctx, const double2* x,
   } else {
     k_to_working_bounded<float2><<<g, 256, 0, ctx->stream>>>(
         x, (float2*)xt, ctx->M, ctx->Mp);
-    k_matvec<float><<<gm, 256, 0, ctx->stream>>>(
-        (const float2*)ctx->g_hi, (const float2*)xt, (float2*)segp,
-        (float2*)tilep, ctx->segs, ctx->nseg, ctx->nb, ctx->scal, 0);
+    launch_mv<float>(ctx, xt, segp, tilep, 0);
     k_apply_finalize_bounded<float2, float>
         <<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
             (const float2*)segp, (const float2*)tilep, ctx->seg_begin, ctx->nb,

@@ -405,8 +405,10 @@ bool encode_planes(CUtensorMap* m, void* base, int cols, int rows, int planes,
   return true;
 }
 
+// grid_cap > 0 limits the persistent grid to that many CTAs (one per SM).
 cudaError_t launch_tc(osar_ctx* ctx, const CUtensorMap& ma,
-                      const CUtensorMap& mb, const TcParams& p, int kind) {
+                      const CUtensorMap& mb, const TcParams& p, int kind,
+                      int grid_cap = 0) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(
@@ -415,6 +417,7 @@ cudaError_t launch_tc(osar_ctx* ctx, const CUtensorMap& ma,
     attr_set = true;
   }
   int grid = p.n_tiles < ctx->sm_count ? p.n_tiles : ctx->sm_count;
+  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
   if (grid <= 0) return cudaSuccess;
   ProfEvent ev;
   prof_begin(ctx, kind, &ev);
@@ -447,7 +450,7 @@ int dict_slices(int np) {
   return s;
 }
 
-cudaError_t launch_dict_tc(osar_ctx* ctx) {
+cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap) {
   TcParams p = {};
   p.tiles = ctx->dict_tiles;
   p.n_tiles = ctx->n_dict_tiles;
@@ -462,7 +465,8 @@ cudaError_t launch_dict_tc(osar_ctx* ctx) {
   p.part_slice = (int64_t)ctx->Mp * ctx->Kp;
   p.nb = ctx->nb;
   p.err = &ctx->scal->error;
-  cudaError_t e = launch_tc(ctx, ctx->map_d_rows1, ctx->map_f_rows2, p, KCL_DICT);
+  cudaError_t e =
+      launch_tc(ctx, ctx->map_d_rows1, ctx->map_f_rows2, p, KCL_DICT, grid_cap);
   if (e != cudaSuccess) return e;
   const int64_t groups = (int64_t)ctx->Mp * ctx->Kp / 8;
   ProfEvent ev;

@@ -51,101 +51,266 @@ __device__ __forceinline__ void load4(const double2* p, double2 (&g)[4]) {
   for (int c = 0; c < 4; ++c) g[c] = __ldcs(p + c);
 }
 
+// Shared-memory pipeline of the matvec.  A stage holds one chunk of CC
+// stored columns of a block (32 KB), the block's x_I (128 entries) and the
+// chunk's x_J entries, all brought in by TMA bulk copies issued by one
+// producer thread; 8 consumer warps work on every chunk.
+// Four consecutive complex entries of one stored column, from shared memory.
+__device__ __forceinline__ void load4_smem(const float2* p, float2 (&g)[4]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  const float4 a = q[0], b = q[1];
+  g[0] = make_float2(a.x, a.y);
+  g[1] = make_float2(a.z, a.w);
+  g[2] = make_float2(b.x, b.y);
+  g[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4_smem(const double2* p, double2 (&g)[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) g[c] = p[c];
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256, 2)
+struct Mv {
+  using T2 = typename Vec<T>::T2;
+  static constexpr int CC = 32768 / (BLK * (int)sizeof(T2));  // 32 f32 / 16 f64
+  static constexpr int CHUNKS = BLK / CC;                      // per block
+  static constexpr int WC = CC / 8;                            // columns per warp and chunk
+  static constexpr int G_BYTES = CC * BLK * (int)sizeof(T2);
+  static constexpr int XI_BYTES = BLK * (int)sizeof(T2);
+  static constexpr int XJ_BYTES = CC * (int)sizeof(T2);
+  static constexpr int STAGE = G_BYTES + XI_BYTES + XJ_BYTES;
+  static constexpr int NST = sizeof(T) == 4 ? 6 : 5;           // ring depth
+  static constexpr int RED_BYTES = 2 * 8 * BLK * (int)sizeof(T2);
+  static constexpr int SMEM = NST * STAGE + RED_BYTES + 2 * NST * 8 +
+                              NST * 16 + 16;
+  static constexpr int THREADS = 288;  // producer warp + 8 consumer warps
+};
+static_assert(Mv<float>::CHUNKS * Mv<float>::WC == 16, "16 columns per thread");
+static_assert(Mv<double>::CHUNKS * Mv<double>::WC == 16, "16 columns per thread");
+static_assert(Mv<float>::SMEM <= 227 * 1024 && Mv<double>::SMEM <= 227 * 1024,
+              "matvec ring exceeds shared memory");
+
+constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
+
+// One Gram pass.  Each thread accumulates y_J over 16 of the block's stored
+// columns (chunk k, warp w: columns k*CC + w*WC + j) for the whole segment
+// and y_I over its 4 rows for one block; the same sums as the definition at
+// the top, in a fixed order, so the result does not depend on the grid or
+// on which CTA takes which segment.  Segments are handed out dynamically
+// (first by block index, then from an atomic ticket), so the kernel spreads
+// over whatever SMs are free, e.g. beside the next pulse's dictionary
+// product.  Every wait is bounded; on a timeout the CTA records the error,
+// stops at the next per-block barrier and drains its copies in flight.
+template <typename T>
+__global__ void __launch_bounds__(288, 1)
     k_matvec(const typename Vec<T>::T2* __restrict__ G,
              const typename Vec<T>::T2* __restrict__ x,
              typename Vec<T>::T2* __restrict__ segpart,
              typename Vec<T>::T2* __restrict__ tilepart,
              const int4* __restrict__ segs, int nseg, int nb,
-             const DevScalars* __restrict__ sc, int gated) {
+             DevScalars* __restrict__ sc, int gated,
+             unsigned* __restrict__ queue) {
+  using C = Mv<T>;
   using T2 = typename Vec<T>::T2;
-  constexpr int RB = sizeof(T) == 4 ? 8 : 4;  // stored columns per load batch
   if (gated && sc->converged) return;
-  __shared__ T2 xs[BLK];
-  __shared__ T2 red[8][BLK];
+  extern __shared__ __align__(128) uint8_t mv_smem[];
+  T2* red = reinterpret_cast<T2*>(mv_smem + C::NST * C::STAGE);  // [2][8][BLK]
+  uint64_t* full = reinterpret_cast<uint64_t*>(mv_smem + C::NST * C::STAGE +
+                                               C::RED_BYTES);
+  uint64_t* empty = full + C::NST;
+  int4* meta = reinterpret_cast<int4*>(empty + C::NST);  // (I, J, slot, flags)
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(meta + C::NST);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int s = blockIdx.x; s < nseg; s += gridDim.x) {
-    const int4 sg = segs[s];
-    const int J = sg.x;
-    __syncthreads();
-    if (threadIdx.x < BLK) xs[threadIdx.x] = x[J * BLK + threadIdx.x];
-    __syncthreads();
-    T br[16], bi[16];  // y_J partials of this warp's 16 columns
-#pragma unroll
-    for (int c = 0; c < 16; ++c) br[c] = bi[c] = T(0);
-    for (int I = sg.y; I < sg.z; ++I) {
-      const T2* blk = G + packed_block(I, J, nb) * (int64_t)(BLK * BLK) +
-                      (int64_t)(warp * 16) * BLK + lane * 4;
-      T2 xi[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) xi[q] = x[I * BLK + lane * 4 + q];
-      T ar[4], ai[4];  // y_I partials of this lane's 4 rows
-#pragma unroll
-      for (int q = 0; q < 4; ++q) ar[q] = ai[q] = T(0);
-#pragma unroll
-      for (int c0 = 0; c0 < 16; c0 += RB) {
-        T2 g[RB][4];
-#pragma unroll
-        for (int c = 0; c < RB; ++c) load4(blk + (int64_t)(c0 + c) * BLK, g[c]);
-#pragma unroll
-        for (int c = 0; c < RB; ++c) {
-          const T2 xj = xs[warp * 16 + c0 + c];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const T2 e = g[c][q];
-            // y_J[c] += conj(e) x_I[r]
-            br[c0 + c] = fma(e.x, xi[q].x, br[c0 + c]);
-            br[c0 + c] = fma(e.y, xi[q].y, br[c0 + c]);
-            bi[c0 + c] = fma(e.x, xi[q].y, bi[c0 + c]);
-            bi[c0 + c] = fma(-e.y, xi[q].x, bi[c0 + c]);
-            // y_I[r] += e x_J[c]
-            ar[q] = fma(e.x, xj.x, ar[q]);
-            ar[q] = fma(-e.y, xj.y, ar[q]);
-            ai[q] = fma(e.x, xj.y, ai[q]);
-            ai[q] = fma(e.y, xj.x, ai[q]);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < C::NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 8);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    if (lane != 0) return;
+    // ------------------------------------------------------------ producer
+    const uint64_t stream_policy = l2_policy_evict_first();
+    uint32_t issued[C::NST];
+    for (int i = 0; i < C::NST; ++i) issued[i] = 0;
+    int stage = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    int s = blockIdx.x;
+    int s_next = nseg;
+    if (s < nseg) s_next = (int)gridDim.x + (int)atomicAdd(&queue[0], 1u);
+    while (ok && s < nseg) {
+      const int4 sg = segs[s];
+      for (int I = sg.y; ok && I < sg.z; ++I) {
+        const T2* blk = G + packed_block(I, sg.x, nb) * (int64_t)(BLK * BLK);
+        for (int k = 0; k < C::CHUNKS; ++k) {
+          if (!mbar_wait_bounded(&empty[stage], ph ^ 1, abort_flag, &sc->error,
+                                 MV_WAIT_LIMIT_NS)) {
+            ok = false;
+            break;
+          }
+          if (k == 0)
+            meta[stage] = make_int4(I, sg.x, sg.w,
+                                    (I == sg.y ? 1 : 0) | (I == sg.z - 1 ? 2 : 0));
+          uint8_t* st = mv_smem + stage * C::STAGE;
+          mbar_expect_tx(&full[stage], C::STAGE);
+          bulk_load_hint(st, blk + (int64_t)k * C::CC * BLK, C::G_BYTES,
+                         &full[stage], stream_policy);
+          bulk_load(st + C::G_BYTES, x + (int64_t)I * BLK, C::XI_BYTES, &full[stage]);
+          bulk_load(st + C::G_BYTES + C::XI_BYTES,
+                    x + (int64_t)sg.x * BLK + k * C::CC, C::XJ_BYTES, &full[stage]);
+          issued[stage]++;
+          if (++stage == C::NST) {
+            stage = 0;
+            ph ^= 1;
           }
         }
       }
-      if (I != J) {
+      s = s_next;
+      if (s < nseg) s_next = (int)gridDim.x + (int)atomicAdd(&queue[0], 1u);
+    }
+    // end of work: a stage whose meta says so (no copy); its earlier copies
+    // have landed, since the consumers released it
+    int sentinel = -1;
+    if (ok && mbar_wait_bounded(&empty[stage], ph ^ 1, abort_flag, &sc->error,
+                                MV_WAIT_LIMIT_NS)) {
+      meta[stage] = make_int4(-1, 0, 0, 0);
+      mbar_arrive(&full[stage]);
+      sentinel = stage;
+    }
+    // the last CTA to leave resets the ticket counter for the next launch
+    __threadfence();
+    if (atomicAdd(&queue[1], 1u) == gridDim.x - 1) {
+      queue[0] = 0;
+      queue[1] = 0;
+      __threadfence();
+    }
+    // every copy this thread issued lands before the CTA exits
+    volatile int no_abort = 0;
+    for (int i = 0; i < C::NST; ++i)
+      if (issued[i] && i != sentinel)
+        mbar_wait_bounded(&full[i], (issued[i] - 1) & 1, &no_abort, &sc->error,
+                          MV_WAIT_LIMIT_NS);
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  const int cw = warp - 1;
+  int stage = 0, rp = 0;
+  uint32_t ph = 0;
+  T br[16], bi[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) br[c] = bi[c] = T(0);
+  for (;;) {
+    bool ok = !*abort_flag && mbar_wait_bounded(&full[stage], ph, abort_flag,
+                                                &sc->error, MV_WAIT_LIMIT_NS);
+    const int4 m = ok ? meta[stage] : make_int4(-1, 0, 0, 0);
+    const bool work = ok && m.x >= 0;
+    if (work) {
+      const int I = m.x, J = m.y;
+      if (m.w & 1) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) br[c] = bi[c] = T(0);
+      }
+      const T2* xis = reinterpret_cast<const T2*>(mv_smem + stage * C::STAGE +
+                                                  C::G_BYTES);
+      T2 xi[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xi[q] = xis[lane * 4 + q];
+      T ar[4], ai[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ar[q] = ai[q] = T(0);
+#pragma unroll
+      for (int k = 0; k < C::CHUNKS; ++k) {
+        if (k > 0 && ok)
+          ok = !*abort_flag && mbar_wait_bounded(&full[stage], ph, abort_flag,
+                                                 &sc->error, MV_WAIT_LIMIT_NS);
+        if (ok) {
+          const uint8_t* st = mv_smem + stage * C::STAGE;
+          const T2* gs = reinterpret_cast<const T2*>(st);
+          const T2* xjs = reinterpret_cast<const T2*>(st + C::G_BYTES + C::XI_BYTES);
+#pragma unroll
+          for (int j = 0; j < C::WC; ++j) {
+            const int col = cw * C::WC + j;
+            const T2 xj = xjs[col];
+            T2 g[4];
+            load4_smem(gs + col * BLK + lane * 4, g);
+            const int a = k * C::WC + j;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const T2 e = g[q];
+              // y_J[c] += conj(e) x_I[r]
+              br[a] = fma(e.x, xi[q].x, br[a]);
+              br[a] = fma(e.y, xi[q].y, br[a]);
+              bi[a] = fma(e.x, xi[q].y, bi[a]);
+              bi[a] = fma(-e.y, xi[q].x, bi[a]);
+              // y_I[r] += e x_J[c]
+              ar[q] = fma(e.x, xj.x, ar[q]);
+              ar[q] = fma(-e.y, xj.y, ar[q]);
+              ai[q] = fma(e.x, xj.y, ai[q]);
+              ai[q] = fma(e.y, xj.x, ai[q]);
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[stage]);
+        }
+        if (++stage == C::NST) {
+          stage = 0;
+          ph ^= 1;
+        }
+      }
+      if (ok && I != J) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           T2 v;
           v.x = ar[q];
           v.y = ai[q];
-          red[warp][lane * 4 + q] = v;
+          red[(rp * 8 + cw) * BLK + lane * 4 + q] = v;
         }
-        __syncthreads();
-        if (threadIdx.x < BLK) {
-          T sr = 0, si = 0;
+      }
+      if (ok && (m.w & 2)) {
+        // segment done: y_J over all rows of its blocks, one lane per column
 #pragma unroll
-          for (int w = 0; w < 8; ++w) {
-            sr += red[w][threadIdx.x].x;
-            si += red[w][threadIdx.x].y;
+        for (int a = 0; a < 16; ++a) {
+          T vr = br[a], vi = bi[a];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            vr += __shfl_xor_sync(0xffffffffu, vr, o);
+            vi += __shfl_xor_sync(0xffffffffu, vi, o);
           }
-          T2 v;
-          v.x = sr;
-          v.y = si;
-          tilepart[packed_block(I, J, nb) * BLK + threadIdx.x] = v;
+          if (lane == a) {
+            T2 v;
+            v.x = vr;
+            v.y = vi;
+            const int col = (a / C::WC) * C::CC + cw * C::WC + (a % C::WC);
+            segpart[(int64_t)m.z * BLK + col] = v;
+          }
         }
-        __syncthreads();
       }
     }
+    // Per-block barrier of the consumer warps: the block partial is summed
+    // over the warps in a fixed order, and the loop ends here for everyone
+    // at once (end of work or an abort raised before the barrier).
+    named_barrier(1, 256);
+    if (!work || *abort_flag) break;
+    const int r = (int)threadIdx.x - 32;
+    if (m.x != m.y && r < BLK) {
+      T sr = 0, si = 0;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      T vr = br[c], vi = bi[c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        vr += __shfl_xor_sync(0xffffffffu, vr, o);
-        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      for (int w = 0; w < 8; ++w) {
+        sr += red[(rp * 8 + w) * BLK + r].x;
+        si += red[(rp * 8 + w) * BLK + r].y;
       }
-      if (lane == c) {
-        T2 v;
-        v.x = vr;
-        v.y = vi;
-        segpart[(int64_t)sg.w * BLK + warp * 16 + c] = v;
-      }
+      T2 v;
+      v.x = sr;
+      v.y = si;
+      tilepart[packed_block(m.x, m.y, nb) * BLK + r] = v;
     }
+    rp ^= 1;
   }
 }
 

@@ -1,6 +1,8 @@
 // libosar C ABI: context management and the per-pulse / per-burst call
 // sequences of Online FISTA (Eqs. 12-13 and Algorithm 1).
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -71,6 +73,12 @@ void free_all(osar_ctx* ctx) {
   if (ctx->adj_buf) cudaFree(ctx->adj_buf);
   for (int i = 0; i < RING; ++i)
     if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);
+  if (ctx->h_iters) cudaFreeHost(ctx->h_iters);
+  for (cudaEvent_t ev : {ctx->ev_free, ctx->ev_synth, ctx->ev_iters})
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : ctx->copy_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   for (auto& pe : ctx->prof_pending) {
     cudaEventDestroy(pe.a);
     cudaEventDestroy(pe.b);
@@ -114,6 +122,9 @@ osar_status validate(const osar_config* c, std::string* why) {
     return *why = "need power_iters_first >= 1 and power_iters >= 0", OSAR_E_INVALID;
   if (!is_finite(c->lipschitz_margin) || c->lipschitz_margin < 0)
     return *why = "lipschitz_margin must be finite and >= 0", OSAR_E_INVALID;
+  if (c->overlap_synthesis != 0 && c->overlap_synthesis != 1)
+    return *why = "overlap_synthesis must be 0 or 1", OSAR_E_INVALID;
+  if (c->synth_ctas < 0) return *why = "synth_ctas must be >= 0", OSAR_E_INVALID;
   return OSAR_OK;
 }
 
@@ -145,11 +156,14 @@ void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
           gram_tiles.push_back(
               make_int4(I, J, (int)packed_block(I, J, nb), 0));
   if (ctx->dict) {
-    // split-K slices only on the tensor-core path; the (atom, frequency)
-    // tiles of one atom block are adjacent so its dictionary rows stay in L2
+    // Split-K slices (tensor-core path only) one after another: the tiles
+    // in flight together share one slice of the phase operand F (6 planes x
+    // Kp x 4096 pixels, 25 MB at K = 512), which stays in L2 however many
+    // SMs the product gets; the frequency tiles of one atom block are
+    // adjacent, so its dictionary rows come from HBM once.
     const int S = ctx->prec == OSAR_SPLIT_BF16 ? ctx->dict_slices : 1;
-    for (int I = 0; I < nb; ++I)
-      for (int sl = 0; sl < S; ++sl)
+    for (int sl = 0; sl < S; ++sl)
+      for (int I = 0; I < nb; ++I)
         for (int J = 0; J < ctx->Kp / BLK; ++J)
           dict_tiles.push_back(make_int4(I, J | (sl << 16), 0, 0));
   }
@@ -258,6 +272,18 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     e = cudaEventCreateWithFlags(&ctx->ring_ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaEventCreate"));
   }
+  for (cudaEvent_t& ev : ctx->copy_ev) {
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaEventCreate"));
+  }
+  if (ctx->dict && cfg->overlap_synthesis) {
+    e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&ctx->ev_free, &ctx->ev_synth, &ctx->ev_iters})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_iters, sizeof(int32_t));
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "side stream"));
+    *ctx->h_iters = 0;
+  }
 
   e = cudaMemcpyAsync(ctx->segs, segs.data(), sizeof(int4) * segs.size(),
                       cudaMemcpyHostToDevice, ctx->stream);
@@ -312,15 +338,101 @@ osar_status read_scalars(osar_ctx* ctx, DevScalars* s) {
   return OSAR_OK;
 }
 
-osar_status push_impl(osar_ctx* ctx, const double gamma[3]) {
-  cudaError_t e;
-  e = launch_pixel_turns(ctx, gamma);
+// The launchers issue on ctx->stream and record their profiling events there;
+// this points ctx->stream at another stream for one scope.
+struct LaunchOn {
+  osar_ctx* ctx;
+  cudaStream_t saved;
+  LaunchOn(osar_ctx* c, cudaStream_t s) : ctx(c), saved(c->stream) { c->stream = s; }
+  ~LaunchOn() { ctx->stream = saved; }
+};
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) != cudaSuccess ||
+         cs != cudaStreamCaptureStatusNone;
+}
+
+// Forward block of a pulse (Eq. 4 with the dictionary of Eq. 5): per-pixel
+// phase terms, phase matrix, then A_s = F_s D for dictionary models.
+cudaError_t synthesize(osar_ctx* ctx, const double gamma[3], int grid_cap) {
+  cudaError_t e = launch_pixel_turns(ctx, gamma);
   if (e == cudaSuccess) e = launch_phase(ctx);
   if (e == cudaSuccess && ctx->dict)
-    e = ctx->prec == OSAR_SPLIT_BF16 ? launch_dict_tc(ctx) : launch_dict_simt(ctx);
+    e = ctx->prec == OSAR_SPLIT_BF16 ? launch_dict_tc(ctx, grid_cap)
+                                     : launch_dict_simt(ctx);
+  return e;
+}
+
+// Take the step count of the last finished burst, if its copy has landed.
+void refresh_iters_estimate(osar_ctx* ctx) {
+  if (cudaEventQuery(ctx->ev_iters) == cudaSuccess && *ctx->h_iters > 0)
+    ctx->iters_est = *ctx->h_iters;
+  else
+    cudaGetLastError();  // cudaErrorNotReady is not an error here
+}
+
+// CTAs for the overlapped dictionary product.  It runs beside the previous
+// pulse's power steps and FISTA burst, which stream the FP32 Gram from HBM
+// while the product keeps the tensor cores busy.  The burst's length is
+// estimated from Gram bytes at HBM3e copy bandwidth, the product's from its
+// tensor flops at the split-BF16 rate one SM sustains beside the streaming
+// burst (about 3/4 of its rate alone, measured on the 128 x 128 workload);
+// the product gets enough SMs to end about when the burst does, but at most
+// 40 % of them: one SM pulls about 73 GB/s from HBM, so the matvec needs
+// some 95 of the 152 to stay at full bandwidth.  0 means the full grid.
+int synth_grid(const osar_ctx* ctx, bool main_idle) {
+  if (ctx->cfg.synth_ctas > 0) return std::min(ctx->cfg.synth_ctas, ctx->sm_count);
+  // nothing in flight on the main stream (the caller waited for the last
+  // burst): the product has the GPU to itself
+  if (main_idle) return 0;
+  constexpr double kTensorFlopsPerSm = 8.0e12;  // f/s, bf16 x 3 products
+  constexpr double kHbmBytesPerS = 6.8e12;
+  const double flops = 24.0 * ctx->Kp * (double)ctx->Np * ctx->Mp;
+  const double sm_seconds = flops / kTensorFlopsPerSm;
+  const double pass = (double)ctx->nblk * BLK * BLK * 8.0 / kHbmBytesPerS;
+  const int power = ctx->n <= 1 ? ctx->cfg.power_iters_first : ctx->cfg.power_iters;
+  const double burst = (power + ctx->iters_est) * pass;
+  const int g = (int)std::ceil(sm_seconds / (0.9 * burst));
+  return std::max(8, std::min(g, (int)(0.4 * ctx->sm_count)));
+}
+
+// True when every launch on the main stream has finished (the caller waited
+// for the last burst before pushing).
+bool main_idle(osar_ctx* ctx) {
+  if (cudaStreamQuery(ctx->stream) == cudaSuccess) return true;
+  cudaGetLastError();  // cudaErrorNotReady: work in flight
+  return false;
+}
+
+// idle: main_idle() taken before the pulse's data copy was queued.
+osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
+  cudaError_t e = cudaSuccess;
+  if (ctx->side && !capturing(ctx->stream)) {
+    refresh_iters_estimate(ctx);
+    // The synthesis buffers are free once the previous pulse's Gram update,
+    // their last reader, is done (ev_free); the burst after it only reads
+    // the Gram, b and the coefficient vectors.
+    if (ctx->free_stale) e = cudaEventRecord(ctx->ev_free, ctx->stream);
+    ctx->free_stale = false;
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_free, 0);
+    if (e == cudaSuccess) {
+      const int grid = synth_grid(ctx, idle);
+      LaunchOn on(ctx, ctx->side);
+      e = synthesize(ctx, gamma, grid);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_synth, ctx->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_synth, 0);
+  } else {
+    // a captured push leaves no usable ev_free behind
+    if (ctx->side) ctx->free_stale = true;
+    e = synthesize(ctx, gamma, 0);
+  }
   if (e == cudaSuccess) e = launch_data_update(ctx);
   if (e == cudaSuccess)
     e = ctx->prec == OSAR_SPLIT_BF16 ? launch_gram_tc(ctx) : launch_gram_simt(ctx);
+  if (e == cudaSuccess && ctx->side && !ctx->free_stale)
+    e = cudaEventRecord(ctx->ev_free, ctx->stream);
   ctx->n += 1;
   if (e == cudaSuccess)
     e = launch_power_steps(ctx, ctx->n == 1 ? ctx->cfg.power_iters_first
@@ -383,6 +495,8 @@ void osar_config_default(osar_config* c) {
   c->restart_momentum = 0;
   c->compensated = 1;
   c->cuda_stream = nullptr;
+  c->overlap_synthesis = 1;
+  c->synth_ctas = 0;
 }
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
@@ -394,6 +508,7 @@ osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
 osar_status osar_destroy(osar_ctx* ctx) {
   if (!ctx) return OSAR_OK;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
   free_all(ctx);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -409,6 +524,7 @@ osar_status osar_push_pulse(osar_ctx* ctx, const double gamma_xyz[3],
   for (int i = 0; i < 3; ++i)
     if (!is_finite(gamma_xyz[i]))
       return fail(ctx, OSAR_E_INVALID, "osar_push_pulse: non-finite gamma");
+  const bool idle = main_idle(ctx);
   const int slot = ctx->ring_pos;
   ctx->ring_pos = (ctx->ring_pos + 1) % RING;
   CK(ctx, cudaEventSynchronize(ctx->ring_ev[slot]));
@@ -417,7 +533,7 @@ osar_status osar_push_pulse(osar_ctx* ctx, const double gamma_xyz[3],
   CK(ctx, cudaMemcpyAsync(ctx->d_dev, h, sizeof(double2) * ctx->K,
                           cudaMemcpyHostToDevice, ctx->stream));
   CK(ctx, cudaEventRecord(ctx->ring_ev[slot], ctx->stream));
-  return push_impl(ctx, gamma_xyz);
+  return push_impl(ctx, gamma_xyz, idle);
 }
 
 osar_status osar_push_pulse_dev(osar_ctx* ctx, const double gamma_xyz[3],
@@ -429,9 +545,10 @@ osar_status osar_push_pulse_dev(osar_ctx* ctx, const double gamma_xyz[3],
   for (int i = 0; i < 3; ++i)
     if (!is_finite(gamma_xyz[i]))
       return fail(ctx, OSAR_E_INVALID, "osar_push_pulse_dev: non-finite gamma");
+  const bool idle = main_idle(ctx);
   CK(ctx, cudaMemcpyAsync(ctx->d_dev, d_dev_c128, sizeof(double2) * ctx->K,
                           cudaMemcpyDeviceToDevice, ctx->stream));
-  return push_impl(ctx, gamma_xyz);
+  return push_impl(ctx, gamma_xyz, idle);
 }
 
 osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
@@ -456,6 +573,14 @@ osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
     st = read_scalars(ctx, &s);
     if (st != OSAR_OK) return st;
     *iters_done = s.iters;
+    if (s.iters > 0) ctx->iters_est = s.iters;
+  } else if (ctx->side && !capturing(ctx->stream)) {
+    // the step count reaches the host without a wait, for synth_grid
+    const char* src = reinterpret_cast<const char*>(ctx->scal) +
+                      offsetof(DevScalars, iters);
+    CK(ctx, cudaMemcpyAsync(ctx->h_iters, src, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaEventRecord(ctx->ev_iters, ctx->stream));
   }
   return OSAR_OK;
 }
@@ -476,6 +601,27 @@ osar_status osar_get_coeffs_dev(osar_ctx* ctx, void* out_dev_c128) {
   if (!out_dev_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_coeffs_dev: NULL");
   CK(ctx, cudaMemcpyAsync(out_dev_c128, ctx->c, sizeof(double2) * ctx->M,
                           cudaMemcpyDeviceToDevice, ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_get_coeffs_async(osar_ctx* ctx, double* out_c128,
+                                  int32_t slot) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!out_c128 || slot < 0 || slot >= OSAR_COPY_SLOTS)
+    return fail(ctx, OSAR_E_INVALID, "osar_get_coeffs_async: bad buffer or slot");
+  CK(ctx, cudaMemcpyAsync(out_c128, ctx->c, sizeof(double2) * ctx->M,
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaEventRecord(ctx->copy_ev[slot], ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_wait_coeffs(osar_ctx* ctx, int32_t slot) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (slot < 0 || slot >= OSAR_COPY_SLOTS)
+    return fail(ctx, OSAR_E_INVALID, "osar_wait_coeffs: slot out of range");
+  CK(ctx, cudaEventSynchronize(ctx->copy_ev[slot]));
   return OSAR_OK;
 }
 
@@ -639,6 +785,7 @@ osar_status osar_synchronize(osar_ctx* ctx) {
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->side) CK(ctx, cudaStreamSynchronize(ctx->side));
   return OSAR_OK;
 }
 
@@ -686,6 +833,20 @@ osar_status osar_profile_reset(osar_ctx* ctx) {
     ctx->prof_launches[k] = 0;
   }
   ctx->launches = 0;
+  CK(ctx, cudaMemsetAsync(reinterpret_cast<char*>(ctx->scal) +
+                              offsetof(DevScalars, passes),
+                          0, sizeof(unsigned long long), ctx->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_profile_passes(osar_ctx* ctx, int64_t* passes) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!passes) return fail(ctx, OSAR_E_INVALID, "osar_profile_passes: NULL");
+  DevScalars s;
+  st = read_scalars(ctx, &s);
+  if (st != OSAR_OK) return st;
+  *passes = (int64_t)s.passes;
   return OSAR_OK;
 }
 
@@ -740,7 +901,7 @@ osar_status osar_save(osar_ctx* ctx, const char* path) {
   if (!f) return fail(ctx, OSAR_E_IO, std::string("cannot open ") + path);
   CkptHeader h = {};
   std::memcpy(h.magic, "OSARCKP", 8);
-  h.version = 3;
+  h.version = 4;
   h.M = ctx->M;
   h.N = ctx->N;
   h.K = ctx->K;
@@ -778,7 +939,7 @@ osar_status osar_load(const char* path, const osar_config* cfg, osar_ctx** out) 
   if (!f) return fail(nullptr, OSAR_E_IO, std::string("cannot open ") + path);
   CkptHeader h;
   if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "OSARCKP", 8) != 0 ||
-      h.version != 3) {
+      h.version != 4) {
     fclose(f);
     return fail(nullptr, OSAR_E_IO, "not an osar checkpoint");
   }

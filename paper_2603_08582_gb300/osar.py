@@ -20,6 +20,7 @@ OSAR_OK, OSAR_E_INVALID, OSAR_E_OOM, OSAR_E_CUDA, OSAR_E_STATE, \
     OSAR_E_TIMEOUT, OSAR_E_NUMERIC, OSAR_E_IO = range(8)
 OSAR_FP64, OSAR_FP32, OSAR_SPLIT_BF16 = 0, 1, 2
 OSAR_DICT_IDENTITY, OSAR_DICT_HOST, OSAR_DICT_GAUSSIAN = 0, 1, 2
+COPY_SLOTS = 4  # OSAR_COPY_SLOTS: osar_get_coeffs_async completion slots
 
 PRECISIONS = {"fp64": OSAR_FP64, "fp32": OSAR_FP32, "split_bf16": OSAR_SPLIT_BF16}
 
@@ -31,12 +32,14 @@ KERNEL_CLASSES = {"phase": 0, "dict_gemm": 1, "gram_gemm": 2, "data_update": 3,
 EXPORTS = [
     "osar_config_default", "osar_create", "osar_destroy", "osar_push_pulse",
     "osar_push_pulse_dev", "osar_iterate", "osar_get_coeffs",
-    "osar_get_coeffs_dev", "osar_get_state", "osar_get_dims", "osar_get_gram",
+    "osar_get_coeffs_dev", "osar_get_coeffs_async", "osar_wait_coeffs",
+    "osar_get_state", "osar_get_dims", "osar_get_gram",
     "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
     "osar_gram_apply_static",
     "osar_simulate_pulse", "osar_unroll_grad", "osar_synchronize",
     "osar_profile_enable",
-    "osar_profile_read", "osar_profile_reset", "osar_launch_count",
+    "osar_profile_read", "osar_profile_reset", "osar_profile_passes",
+    "osar_launch_count",
     "osar_device_bytes", "osar_save", "osar_load", "osar_last_error",
     "osar_version",
     "osar_batch_create", "osar_batch_destroy", "osar_batch_push",
@@ -58,6 +61,7 @@ class OsarConfig(C.Structure):
         ("lipschitz_margin", C.c_double),
         ("restart_momentum", C.c_int32), ("compensated", C.c_int32),
         ("cuda_stream", C.c_void_p),
+        ("overlap_synthesis", C.c_int32), ("synth_ctas", C.c_int32),
     ]
 
 
@@ -92,6 +96,8 @@ def load_library(path: str = LIB_PATH):
         "osar_iterate": (I32, [P, I32, C.c_double, C.POINTER(I32)]),
         "osar_get_coeffs": (I32, [P, D]),
         "osar_get_coeffs_dev": (I32, [P, P]),
+        "osar_get_coeffs_async": (I32, [P, D, I32]),
+        "osar_wait_coeffs": (I32, [P, I32]),
         "osar_get_state": (I32, [P, C.POINTER(I32), D, D, D]),
         "osar_get_dims": (I32, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
         "osar_get_gram": (I32, [P, D]),
@@ -106,6 +112,7 @@ def load_library(path: str = LIB_PATH):
         "osar_profile_enable": (I32, [P, I32]),
         "osar_profile_read": (I32, [P, I32, C.POINTER(C.c_int64), D]),
         "osar_profile_reset": (I32, [P]),
+        "osar_profile_passes": (I32, [P, C.POINTER(C.c_int64)]),
         "osar_launch_count": (I32, [P, C.POINTER(C.c_int64)]),
         "osar_device_bytes": (I32, [P, C.POINTER(C.c_int64)]),
         "osar_save": (I32, [P, C.c_char_p]),
@@ -150,7 +157,8 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
                 precision="fp64", dictionary=None, n_atoms=None, dict_seed=0,
                 lam=0.05, lambda_relative=True, power_iters_first=30,
                 power_iters=4, lipschitz_margin=0.01, restart_momentum=False,
-                compensated=True, stream=None):
+                compensated=True, stream=None, overlap_synthesis=True,
+                synth_ctas=0):
     """Build an osar_config.  dictionary: None (identity), "gaussian"
     (seeded Philox atoms, needs n_atoms) or an N x M complex array."""
     cfg = default_config()
@@ -178,6 +186,8 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
     cfg.restart_momentum = 1 if restart_momentum else 0
     cfg.compensated = 1 if compensated else 0
     cfg.cuda_stream = stream
+    cfg.overlap_synthesis = 1 if overlap_synthesis else 0
+    cfg.synth_ctas = int(synth_ctas)
     cfg._keepalive = keep
     return cfg
 
@@ -253,6 +263,17 @@ class Osar:
 
     def coeffs_dev(self, out_ptr: int):
         self._check(self._lib.osar_get_coeffs_dev(self._h, C.c_void_p(out_ptr)))
+
+    def coeffs_async(self, out: np.ndarray, slot: int = 0):
+        """Queue a copy of c_hat into `out` (complex128, M entries, ideally
+        pinned); it is valid after wait_coeffs(slot)."""
+        if out.dtype != np.complex128 or out.size < self.m_atoms or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous complex128 array of M entries")
+        self._check(self._lib.osar_get_coeffs_async(self._h, _dptr(out.view(np.float64)),
+                                                    int(slot)))
+
+    def wait_coeffs(self, slot: int = 0):
+        self._check(self._lib.osar_wait_coeffs(self._h, int(slot)))
 
     def state(self) -> dict:
         n = C.c_int32()
@@ -334,6 +355,11 @@ class Osar:
 
     def profile_reset(self):
         self._check(self._lib.osar_profile_reset(self._h))
+
+    def profile_passes(self) -> int:
+        n = C.c_int64()
+        self._check(self._lib.osar_profile_passes(self._h, C.byref(n)))
+        return n.value
 
     def profile_read(self, kernel: str):
         n = C.c_int64()
