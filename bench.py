@@ -37,12 +37,15 @@ POWER_ITERS = 4      # power steps per pulse after the first (library default)
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--steps", type=int, default=251,
+                    help="timed pulses (default: the rest of the 256-pulse "
+                         "aperture after the warm-up, less the time-to-tol pulse)")
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-pulses", type=int, default=2)
+    ap.add_argument("--fp32-pulses", type=int, default=4)
     ap.add_argument("--forms", action="store_true",
                     help="also time the other configurations (32x32 FP64, the "
                          "64x64 adjoint, the 96-scene batch, the 256x256 form)")
@@ -203,13 +206,18 @@ def make_ctx(w, precision, stream, overlap=True, synth_ctas=0):
 
 def pulse_data(ctx, w, n_pulses):
     """Noisy pulses d_s = G_s c_true + noise (SNR per pulse), simulated by the
-    library on the device; the noise draws come from the input generator."""
+    library on the device; the noise draws come from the input generator.
+    Past the aperture's last pulse the sequence starts over (same work per
+    pulse)."""
     from paper_2603_08582_gb300 import synth
     track = synth.workload_track(w)
     c_true = synth.workload_scene(w)
+    p = min(n_pulses, w.n_pulses)
     noise = synth.unit_noise(w.n_pulses, w.n_freq, w.seed)
-    clean = np.stack([ctx.simulate_pulse(track[s], c_true) for s in range(n_pulses)])
-    return track[:n_pulses], clean + synth.scale_noise(clean, noise[:n_pulses], w.snr_db)
+    clean = np.stack([ctx.simulate_pulse(track[s], c_true) for s in range(p)])
+    data = clean + synth.scale_noise(clean, noise[:p], w.snr_db)
+    idx = np.arange(n_pulses) % p
+    return track[idx], np.ascontiguousarray(data[idx])
 
 
 # ------------------------------------------------------------------ ours ---
@@ -229,8 +237,6 @@ def run_ours(args):
     ov = dict(overlap=not args.no_overlap, synth_ctas=args.synth_ctas)
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
     total = W + K + 1
-    if total > w.n_pulses:
-        raise SystemExit(f"warmup + steps must be < {w.n_pulses} pulses")
     track, data = pulse_data(ctx, w, total)
     d_dev = torch.from_numpy(data).to(f"cuda:{local_rank}")
     torch.cuda.synchronize()
@@ -360,9 +366,10 @@ def run_ours(args):
         v["frac"] = round(v["achieved"] / v["peak"], 4)
     per_kernel = {k: {"launches": n, "total_ms": round(t, 3)} for k, (n, t) in prof.items()}
 
-    fp64 = None
+    fp64 = fp32 = None
     if not args.no_fp64 and rank == 0 and args.workload == "c2":
-        fp64 = run_fp64_path(w, track, data, stream, args.fp64_pulses)
+        fp64 = run_precision_path(w, "fp64", track, data, stream, args.fp64_pulses)
+        fp32 = run_precision_path(w, "fp32", track, data, stream, args.fp32_pulses)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1 and args.workload == "c2":
         cpu = cpu_baseline(w, pulses=1)
@@ -376,6 +383,8 @@ def run_ours(args):
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny,
                    "n_pixels": w.n_pixels, "n_atoms": w.m_atoms,
                    "n_freq": w.n_freq, "pulses_total": w.n_pulses,
+                   "pulses_timed": f"{W + 1}..{W + K} (after {W} warm-up)"
+                                   + ("; the aperture repeats past 256" if W + K + 1 > w.n_pulses else ""),
                    "inner_steps_max": INNER_STEPS, "tol": TOL,
                    "precision": "split_bf16 (compensated)",
                    "overlap_synthesis": not args.no_overlap,
@@ -388,6 +397,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": w.m_atoms * 16 + 4,
                 "mean_iters_per_pulse": round(fista_steps / K, 2),
                 "pipelined": "image of pulse s read while pulse s+1 is queued"},
+        "mean_iters_per_pulse": round((passes - K * POWER_ITERS) / K, 2),
         "time_to_tol": ttt,
         "gpu_launches": int(launches),
         "roofline": roofline,
@@ -397,6 +407,8 @@ def run_ours(args):
     if fp64 is not None:
         line["fp64_path"] = fp64
         line["speedup_vs_fp64_path"] = round(value / fp64["value"], 2)
+    if fp32 is not None:
+        line["fp32_path"] = fp32
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if args.forms and rank == 0:
@@ -412,11 +424,12 @@ def ctx_blocks(m):
     return nb * (nb + 1) // 2
 
 
-def run_fp64_path(w, track, data, stream, pulses):
-    """The plain FP64 GPU path on the same workload (a few pulses: its Gram
-    update runs on the FP64 pipes)."""
+def run_precision_path(w, precision, track, data, stream, pulses):
+    """Another precision form on the same workload, a few pulses after one
+    untimed pulse: the plain FP64 path (Gram and dictionary products on the
+    FP64 pipes) or FP32 (SIMT FP32 products, FP32 Gram and matvec)."""
     import torch
-    ctx = make_ctx(w, "fp64", stream.cuda_stream)
+    ctx = make_ctx(w, precision, stream.cuda_stream)
     with torch.cuda.stream(stream):
         ctx.push_pulse(track[0], data[0])
         ctx.iterate(INNER_STEPS, TOL)
@@ -433,7 +446,7 @@ def run_fp64_path(w, track, data, stream, pulses):
     ctx.close()
     return {"value": round(pulses / (ms / 1e3), 4), "unit": "pulses/s",
             "pulses_timed": pulses, "ms_per_pulse": round(ms / pulses, 2),
-            "dtype": "f64"}
+            "dtype": {"fp64": "f64", "fp32": "f32"}[precision]}
 
 
 # -------------------------------------------------------- other forms ---

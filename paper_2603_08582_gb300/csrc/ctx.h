@@ -119,8 +119,11 @@ struct osar_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_free = nullptr;   // main: last reader of the synthesis buffers done
   cudaEvent_t ev_synth = nullptr;  // side: synthesis of the pushed pulse done
-  cudaEvent_t ev_iters = nullptr;  // main: burst step count copied to h_iters
-  int32_t* h_iters = nullptr;      // pinned copy of the last burst's step count
+  // step counts of recent bursts, copied to pinned memory without a wait
+  static constexpr int ITERS_RING = 4;
+  cudaEvent_t ev_iters[ITERS_RING] = {};
+  int32_t* h_iters = nullptr;      // ITERS_RING pinned counts
+  int64_t iters_seq = 0;           // counts queued so far
   int iters_est = 20;              // FISTA steps expected in a burst
   bool free_stale = false;         // ev_free predates a captured push
   // osar_get_coeffs_async completion events (OSAR_COPY_SLOTS)

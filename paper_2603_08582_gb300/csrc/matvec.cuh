@@ -51,10 +51,6 @@ __device__ __forceinline__ void load4(const double2* p, double2 (&g)[4]) {
   for (int c = 0; c < 4; ++c) g[c] = __ldcs(p + c);
 }
 
-// Shared-memory pipeline of the matvec.  A stage holds one chunk of CC
-// stored columns of a block (32 KB), the block's x_I (128 entries) and the
-// chunk's x_J entries, all brought in by TMA bulk copies issued by one
-// producer thread; 8 consumer warps work on every chunk.
 // Four consecutive complex entries of one stored column, from shared memory.
 __device__ __forceinline__ void load4_smem(const float2* p, float2 (&g)[4]) {
   const float4* q = reinterpret_cast<const float4*>(p);
@@ -69,30 +65,41 @@ __device__ __forceinline__ void load4_smem(const double2* p, double2 (&g)[4]) {
   for (int c = 0; c < 4; ++c) g[c] = p[c];
 }
 
+// Shared-memory pipeline of the matvec.  A stage holds one chunk of CC
+// stored columns of a block (32 KB), the block's x_I (128 entries) and the
+// chunk's x_J entries, all brought in by TMA bulk copies issued by one
+// producer thread; CW consumer warps work on every chunk, WC columns each.
+#ifndef OSAR_MV_WARPS
+#define OSAR_MV_WARPS 8
+#endif
 template <typename T>
 struct Mv {
   using T2 = typename Vec<T>::T2;
+  static constexpr int CW = OSAR_MV_WARPS;                     // consumer warps
   static constexpr int CC = 32768 / (BLK * (int)sizeof(T2));  // 32 f32 / 16 f64
   static constexpr int CHUNKS = BLK / CC;                      // per block
-  static constexpr int WC = CC / 8;                            // columns per warp and chunk
+  static constexpr int WC = CC / CW;                           // columns per warp and chunk
+  static constexpr int NACC = CHUNKS * WC;                     // y_J columns per thread
   static constexpr int G_BYTES = CC * BLK * (int)sizeof(T2);
   static constexpr int XI_BYTES = BLK * (int)sizeof(T2);
   static constexpr int XJ_BYTES = CC * (int)sizeof(T2);
   static constexpr int STAGE = G_BYTES + XI_BYTES + XJ_BYTES;
-  static constexpr int NST = sizeof(T) == 4 ? 6 : 5;           // ring depth
-  static constexpr int RED_BYTES = 2 * 8 * BLK * (int)sizeof(T2);
+  static constexpr int RED_BYTES = 2 * CW * BLK * (int)sizeof(T2);
+  static constexpr int FIXED = RED_BYTES + 16;
+  static constexpr int PER_STAGE = STAGE + 2 * 8 + 16;         // + barriers, meta
+  static constexpr int NST = (227 * 1024 - FIXED) / PER_STAGE > 6
+                                 ? 6 : (227 * 1024 - FIXED) / PER_STAGE;  // ring depth
   static constexpr int SMEM = NST * STAGE + RED_BYTES + 2 * NST * 8 +
                               NST * 16 + 16;
-  static constexpr int THREADS = 288;  // producer warp + 8 consumer warps
+  static constexpr int THREADS = 32 * (CW + 1);  // producer warp + consumers
 };
-static_assert(Mv<float>::CHUNKS * Mv<float>::WC == 16, "16 columns per thread");
-static_assert(Mv<double>::CHUNKS * Mv<double>::WC == 16, "16 columns per thread");
+static_assert(Mv<float>::WC >= 1 && Mv<double>::WC >= 1, "too many consumer warps");
 static_assert(Mv<float>::SMEM <= 227 * 1024 && Mv<double>::SMEM <= 227 * 1024,
               "matvec ring exceeds shared memory");
 
 constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
 
-// One Gram pass.  Each thread accumulates y_J over 16 of the block's stored
+// One Gram pass.  Each thread accumulates y_J over NACC of the block's stored
 // columns (chunk k, warp w: columns k*CC + w*WC + j) for the whole segment
 // and y_I over its 4 rows for one block; the same sums as the definition at
 // the top, in a fixed order, so the result does not depend on the grid or
@@ -102,7 +109,7 @@ constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
 // product.  Every wait is bounded; on a timeout the CTA records the error,
 // stops at the next per-block barrier and drains its copies in flight.
 template <typename T>
-__global__ void __launch_bounds__(288, 1)
+__global__ void __launch_bounds__(Mv<T>::THREADS, 1)
     k_matvec(const typename Vec<T>::T2* __restrict__ G,
              const typename Vec<T>::T2* __restrict__ x,
              typename Vec<T>::T2* __restrict__ segpart,
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(288, 1)
   using T2 = typename Vec<T>::T2;
   if (gated && sc->converged) return;
   extern __shared__ __align__(128) uint8_t mv_smem[];
-  T2* red = reinterpret_cast<T2*>(mv_smem + C::NST * C::STAGE);  // [2][8][BLK]
+  T2* red = reinterpret_cast<T2*>(mv_smem + C::NST * C::STAGE);  // [2][CW][BLK]
   uint64_t* full = reinterpret_cast<uint64_t*>(mv_smem + C::NST * C::STAGE +
                                                C::RED_BYTES);
   uint64_t* empty = full + C::NST;
@@ -124,7 +131,7 @@ __global__ void __launch_bounds__(288, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::NST; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 8);
+      mbar_init(&empty[i], C::CW);
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -202,9 +209,9 @@ __global__ void __launch_bounds__(288, 1)
   const int cw = warp - 1;
   int stage = 0, rp = 0;
   uint32_t ph = 0;
-  T br[16], bi[16];
+  T br[C::NACC], bi[C::NACC];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) br[c] = bi[c] = T(0);
+  for (int c = 0; c < C::NACC; ++c) br[c] = bi[c] = T(0);
   for (;;) {
     bool ok = !*abort_flag && mbar_wait_bounded(&full[stage], ph, abort_flag,
                                                 &sc->error, MV_WAIT_LIMIT_NS);
@@ -214,7 +221,7 @@ __global__ void __launch_bounds__(288, 1)
       const int I = m.x, J = m.y;
       if (m.w & 1) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) br[c] = bi[c] = T(0);
+        for (int c = 0; c < C::NACC; ++c) br[c] = bi[c] = T(0);
       }
       const T2* xis = reinterpret_cast<const T2*>(mv_smem + stage * C::STAGE +
                                                   C::G_BYTES);
@@ -269,13 +276,13 @@ __global__ void __launch_bounds__(288, 1)
           T2 v;
           v.x = ar[q];
           v.y = ai[q];
-          red[(rp * 8 + cw) * BLK + lane * 4 + q] = v;
+          red[(rp * C::CW + cw) * BLK + lane * 4 + q] = v;
         }
       }
       if (ok && (m.w & 2)) {
         // segment done: y_J over all rows of its blocks, one lane per column
 #pragma unroll
-        for (int a = 0; a < 16; ++a) {
+        for (int a = 0; a < C::NACC; ++a) {
           T vr = br[a], vi = bi[a];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
@@ -295,15 +302,15 @@ __global__ void __launch_bounds__(288, 1)
     // Per-block barrier of the consumer warps: the block partial is summed
     // over the warps in a fixed order, and the loop ends here for everyone
     // at once (end of work or an abort raised before the barrier).
-    named_barrier(1, 256);
+    named_barrier(1, 32 * C::CW);
     if (!work || *abort_flag) break;
     const int r = (int)threadIdx.x - 32;
     if (m.x != m.y && r < BLK) {
       T sr = 0, si = 0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) {
-        sr += red[(rp * 8 + w) * BLK + r].x;
-        si += red[(rp * 8 + w) * BLK + r].y;
+      for (int w = 0; w < C::CW; ++w) {
+        sr += red[(rp * C::CW + w) * BLK + r].x;
+        si += red[(rp * C::CW + w) * BLK + r].y;
       }
       T2 v;
       v.x = sr;

@@ -74,7 +74,9 @@ void free_all(osar_ctx* ctx) {
   for (int i = 0; i < RING; ++i)
     if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);
   if (ctx->h_iters) cudaFreeHost(ctx->h_iters);
-  for (cudaEvent_t ev : {ctx->ev_free, ctx->ev_synth, ctx->ev_iters})
+  for (cudaEvent_t ev : {ctx->ev_free, ctx->ev_synth})
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : ctx->ev_iters)
     if (ev) cudaEventDestroy(ev);
   for (cudaEvent_t ev : ctx->copy_ev)
     if (ev) cudaEventDestroy(ev);
@@ -278,11 +280,13 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   }
   if (ctx->dict && cfg->overlap_synthesis) {
     e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
-    for (cudaEvent_t* ev : {&ctx->ev_free, &ctx->ev_synth, &ctx->ev_iters})
+    for (cudaEvent_t* ev : {&ctx->ev_free, &ctx->ev_synth})
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_iters, sizeof(int32_t));
+    for (cudaEvent_t& ev : ctx->ev_iters)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+      e = cudaMallocHost((void**)&ctx->h_iters, sizeof(int32_t) * osar_ctx::ITERS_RING);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "side stream"));
-    *ctx->h_iters = 0;
   }
 
   e = cudaMemcpyAsync(ctx->segs, segs.data(), sizeof(int4) * segs.size(),
@@ -364,37 +368,65 @@ cudaError_t synthesize(osar_ctx* ctx, const double gamma[3], int grid_cap) {
   return e;
 }
 
-// Take the step count of the last finished burst, if its copy has landed.
+// Step count of a recent burst, for synth_grid.  The host may run ahead of
+// the device; here it waits for the burst before the last one queued, so it
+// stays about two pulses ahead and the estimate at most one burst old, and
+// it takes the last burst's count when that one has finished already.
 void refresh_iters_estimate(osar_ctx* ctx) {
-  if (cudaEventQuery(ctx->ev_iters) == cudaSuccess && *ctx->h_iters > 0)
-    ctx->iters_est = *ctx->h_iters;
-  else
-    cudaGetLastError();  // cudaErrorNotReady is not an error here
+  const int64_t q = ctx->iters_seq;
+  constexpr int R = osar_ctx::ITERS_RING;
+  if (q == 0) return;
+  const int last = (int)((q - 1) % R);
+  if (cudaEventQuery(ctx->ev_iters[last]) == cudaSuccess) {
+    ctx->iters_est = ctx->h_iters[last];
+    return;
+  }
+  cudaGetLastError();  // cudaErrorNotReady is not an error here
+  if (q >= 2) {
+    const int prev = (int)((q - 2) % R);
+    if (cudaEventSynchronize(ctx->ev_iters[prev]) == cudaSuccess)
+      ctx->iters_est = ctx->h_iters[prev];
+  }
 }
 
-// CTAs for the overlapped dictionary product.  It runs beside the previous
-// pulse's power steps and FISTA burst, which stream the FP32 Gram from HBM
-// while the product keeps the tensor cores busy.  The burst's length is
-// estimated from Gram bytes at HBM3e copy bandwidth, the product's from its
-// tensor flops at the split-BF16 rate one SM sustains beside the streaming
-// burst (about 3/4 of its rate alone, measured on the 128 x 128 workload);
-// the product gets enough SMs to end about when the burst does, but at most
-// 40 % of them: one SM pulls about 73 GB/s from HBM, so the matvec needs
-// some 95 of the 152 to stay at full bandwidth.  0 means the full grid.
+// CTAs for the overlapped dictionary product, which runs beside the previous
+// pulse's power steps and FISTA burst: the product keeps the tensor cores
+// busy while the burst streams the FP32 Gram from HBM.  A small model picks
+// the grid.  On g SMs the product takes D / g (D = its tensor flops over
+// the split-BF16 rate one SM sustains beside the burst); meanwhile a Gram
+// pass takes max(bytes / HBM bandwidth, bytes / ((S - g) x per-SM
+// bandwidth)) x contention (one SM pulls at most about 73 GB/s, and the
+// product's own traffic slows the pass by about 8 %), and the rest of the
+// burst runs at full speed.  The g that finishes both soonest is compared
+// with running the product alone on the whole GPU before the burst (0, the
+// full grid).  The constants were measured on GB300 with the 128 x 128
+// workload (one SM: 1.23e13 f/s alone, about 0.9e13 beside the burst).
 int synth_grid(const osar_ctx* ctx, bool main_idle) {
   if (ctx->cfg.synth_ctas > 0) return std::min(ctx->cfg.synth_ctas, ctx->sm_count);
   // nothing in flight on the main stream (the caller waited for the last
   // burst): the product has the GPU to itself
   if (main_idle) return 0;
-  constexpr double kTensorFlopsPerSm = 8.0e12;  // f/s, bf16 x 3 products
-  constexpr double kHbmBytesPerS = 6.8e12;
+  constexpr double kSmRateAlone = 1.23e13, kSmRateBeside = 0.9e13;  // f/s
+  constexpr double kHbm = 6.8e12, kSmBw = 73e9, kContention = 1.08;  // B/s
   const double flops = 24.0 * ctx->Kp * (double)ctx->Np * ctx->Mp;
-  const double sm_seconds = flops / kTensorFlopsPerSm;
-  const double pass = (double)ctx->nblk * BLK * BLK * 8.0 / kHbmBytesPerS;
+  const double bytes = (double)ctx->nblk * BLK * BLK * 8.0;
+  const double pass = bytes / kHbm;
   const int power = ctx->n <= 1 ? ctx->cfg.power_iters_first : ctx->cfg.power_iters;
-  const double burst = (power + ctx->iters_est) * pass;
-  const int g = (int)std::ceil(sm_seconds / (0.9 * burst));
-  return std::max(8, std::min(g, (int)(0.4 * ctx->sm_count)));
+  const double passes = power + ctx->iters_est;
+  const int S = ctx->sm_count;
+  double best = flops / (kSmRateAlone * S) + passes * pass;
+  int best_g = 0;
+  for (int g = 8; g <= S - 16; g += 4) {
+    const double t_dict = flops / (kSmRateBeside * g);
+    const double t_pass = std::max(pass, bytes / ((S - g) * kSmBw)) * kContention;
+    const double beside = t_dict / t_pass;  // passes made while the product runs
+    const double t = passes <= beside ? t_dict : t_dict + (passes - beside) * pass;
+    if (t < best) {
+      best = t;
+      best_g = g;
+    }
+  }
+  return best_g;
 }
 
 // True when every launch on the main stream has finished (the caller waited
@@ -573,14 +605,16 @@ osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
     st = read_scalars(ctx, &s);
     if (st != OSAR_OK) return st;
     *iters_done = s.iters;
-    if (s.iters > 0) ctx->iters_est = s.iters;
+    ctx->iters_est = s.iters;
   } else if (ctx->side && !capturing(ctx->stream)) {
     // the step count reaches the host without a wait, for synth_grid
+    const int slot = (int)(ctx->iters_seq % osar_ctx::ITERS_RING);
     const char* src = reinterpret_cast<const char*>(ctx->scal) +
                       offsetof(DevScalars, iters);
-    CK(ctx, cudaMemcpyAsync(ctx->h_iters, src, sizeof(int32_t),
+    CK(ctx, cudaMemcpyAsync(ctx->h_iters + slot, src, sizeof(int32_t),
                             cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaEventRecord(ctx->ev_iters, ctx->stream));
+    CK(ctx, cudaEventRecord(ctx->ev_iters[slot], ctx->stream));
+    ctx->iters_seq += 1;
   }
   return OSAR_OK;
 }
