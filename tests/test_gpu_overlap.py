@@ -50,7 +50,7 @@ def _same(a, b):
     assert a.state() == b.state()
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fp64"])
 @pytest.mark.parametrize("synth_ctas", [0, 3])
 def test_overlap_is_bitwise_neutral(prec, synth_ctas):
     w = _workload()
