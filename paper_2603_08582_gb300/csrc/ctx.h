@@ -99,6 +99,13 @@ struct osar_ctx {
   float2* d32 = nullptr;       // staged pulse data in FP32 (Kp)
   int nseg = 0;
   int4* gram_tiles = nullptr;  // (I, J, packed block, 0), L2-friendly order
+  // tile pairs for CTA-pair tcgen05 launches: (I0, J | slice << 16, I1,
+  // 1 if the second block is missing (I1 = I0 then))
+  int4* gram_pairs = nullptr;
+  int n_gram_pairs = 0;
+  int4* dict_pairs = nullptr;
+  int n_dict_pairs = 0;
+  int tc_pair_limit = 0;       // co-resident CTA pairs (0 = not queried yet)
   int4* dict_tiles = nullptr;  // (atom block, frequency block | slice << 16, 0, 0)
   int n_dict_tiles = 0;
   int dict_slices = 1;         // split-K slices of the dictionary product
@@ -113,6 +120,7 @@ struct osar_ctx {
   CUtensorMap map_a_rows1;     // Apl, box (KC, 128, 1)
   CUtensorMap map_a_rows2;     // Apl, box (KC, 128, 2)
   CUtensorMap map_d_rows1;     // Dpl, box (KC, 128, 1)
+  CUtensorMap map_f_rows1;     // Fpl, box (KC, 128, 1)
   CUtensorMap map_f_rows2;     // Fpl, box (KC, 128, 2)
   // overlapped synthesis (dictionary models): the next pulse's phase and
   // dictionary product on a side stream while the current burst runs

@@ -31,6 +31,10 @@
 //           current one is processed (~64 KB in flight per SM).
 // The accumulator is double-buffered (2 x 256 TMEM columns) so the epilogue
 // of tile t overlaps the MMAs of tile t+1.
+// CTA-pair variant (clusters of two, cta_group::2): two tiles that share
+// their B rows run as one M = 256 MMA on two SMs, each SM loading its own A
+// rows and one of the two B planes (32 KB per 7-stage ring slot instead of
+// 48 KB); see k_tc_cgemm<true>.
 //
 // Accumulation in the tensor pipe rounds its FP32 partial sums toward zero,
 // which biases long reductions (|A| shrinks by ~(steps) 2^-24).  The
@@ -42,19 +46,29 @@
 // in-flight TMA loads and MMAs, and frees TMEM before the kernel returns.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "ctx.h"
 
 namespace osar {
 namespace {
 
-constexpr int TC_STAGES = 4;
 constexpr int TILE_A_BYTES = BLK * KC * 2;        // 128 rows x 64 B
-constexpr int TILE_B_BYTES = 2 * BLK * KC * 2;    // 256 rows x 64 B
-constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + 2 * TILE_B_BYTES;  // 48 KB
 constexpr int TC_THREADS = 320;
 constexpr int EPI_THREADS = 256;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int TC_SMEM = TC_STAGES * STAGE_BYTES + 1024 + 256;
+
+// Ring geometry: one CTA per tile (B = 256 rows, two planes) or CTA pairs
+// (B = this CTA's 128 rows, one plane).
+template <bool PAIR>
+struct TcCfg {
+  static constexpr int STAGES = PAIR ? 7 : 4;
+  static constexpr int B_BYTES = (PAIR ? 1 : 2) * BLK * KC * 2;
+  static constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + 2 * B_BYTES;  // 32 / 48 KB
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
+static_assert(TcCfg<true>::SMEM <= 227 * 1024 && TcCfg<false>::SMEM <= 227 * 1024,
+              "tcgen05 ring exceeds shared memory");
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 struct TcParams {
@@ -120,29 +134,49 @@ __device__ __forceinline__ void load_piece(const float2* gh,
   }
 }
 
+// PAIR = false: one CTA per tile (the layout described at the top).
+// PAIR = true: clusters of two CTAs on two SMs compute two tiles that share
+// the B rows (blocks (I0, J) and (I1, J)) with one M = 256 tcgen05 MMA: each
+// CTA loads its own 128 A rows and one of the two B planes of the N = 256
+// axis ([Q_re | Q_im] or [Q_im | -Q_re]), i.e. 32 KB per k-chunk instead of
+// 48 KB, and keeps its own 128 x 256 accumulator in its TMEM.  The even CTA
+// issues the MMAs; both CTAs' loads complete on the even CTA's stage
+// barrier, the MMA commits release the stage in both CTAs, and the odd
+// CTA's epilogue warps release the accumulator through the even CTA's
+// barrier.  A tile pair whose second block is missing (odd count) marks it
+// so; the odd CTA then computes a copy and stores nothing.
+template <bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_cgemm(const __grid_constant__ CUtensorMap mapA,
                const __grid_constant__ CUtensorMap mapB, const TcParams p) {
+  using C = TcCfg<PAIR>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE_BYTES);
-  uint64_t* empty = full + TC_STAGES;
-  uint64_t* tfull = empty + TC_STAGES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* tfull = empty + C::STAGES;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  // a failed wait stops the peer CTA too
+  auto stop_peer = [&]() {
+    if (PAIR) st_cluster_u32((const void*)abort_flag, rank ^ 1u, 1u);
+  };
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], EPI_THREADS);
+      mbar_init(&tempty[b], PAIR ? 2 * (EPI_THREADS / 32) : EPI_THREADS);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -152,11 +186,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tma_prefetch_desc(&mapB);
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, TMEM_COLS);
-    tmem_relinquish();
+    if (PAIR) {
+      tmem_alloc_pair(tmem_slot, TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(tmem_slot, TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if (PAIR)
+    cluster_sync();  // both CTAs' barriers exist before any remote arrive
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int total_k = 2 * p.k_slice;
@@ -164,57 +206,84 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ------------------------------------------------------ TMA producer
-      uint32_t issued[TC_STAGES];
-      for (int s = 0; s < TC_STAGES; ++s) issued[s] = 0;
+      uint32_t issued[C::STAGES];
+      for (int s = 0; s < C::STAGES; ++s) issued[s] = 0;
       int stage = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x) {
+      for (int t = unit; ok && t < p.n_tiles; t += units) {
         const int4 tile = p.tiles[t];
-        const int ra = tile.x * BLK, rb = (tile.y & 0xFFFF) * BLK;
+        const int ra = (PAIR && rank ? tile.z : tile.x) * BLK;
+        const int rb = (tile.y & 0xFFFF) * BLK;
         const int k0 = (tile.y >> 16) * p.k_slice;
         for (int kc = 0; kc < total_k; ++kc) {
           if (!mbar_wait_bounded(&empty[stage], ph ^ 1, abort_flag, p.err,
                                  WAIT_LIMIT_NS)) {
             ok = false;
+            stop_peer();
             break;
           }
           const int half = kc >= p.k_slice ? 1 : 0;
           const int k = (k0 + kc - half * p.k_slice) * KC;
-          uint8_t* sb = smem + stage * STAGE_BYTES;
-          mbar_expect_tx(&full[stage], STAGE_BYTES);
-          tma_load_3d(sb, &mapA, &full[stage], k, ra, half);
-          tma_load_3d(sb + TILE_A_BYTES, &mapA, &full[stage], k, ra,
-                      half + p.a_lo);
-          tma_load_3d(sb + 2 * TILE_A_BYTES, &mapB, &full[stage], k, rb, half);
-          tma_load_3d(sb + 2 * TILE_A_BYTES + TILE_B_BYTES, &mapB, &full[stage],
-                      k, rb, half + p.b_lo);
+          uint8_t* sb = smem + stage * C::STAGE_BYTES;
+          // B: both planes of the N axis here, or this CTA's one plane
+          const int bp = half + (PAIR ? (int)rank : 0);
+          if (PAIR && rank) {
+            // the pair's bytes all complete on the even CTA's barrier
+            const uint32_t bar = cluster_addr(&full[stage], 0u);
+            tma_load_3d_peer(sb, &mapA, bar, k, ra, half);
+            tma_load_3d_peer(sb + TILE_A_BYTES, &mapA, bar, k, ra, half + p.a_lo);
+            tma_load_3d_peer(sb + 2 * TILE_A_BYTES, &mapB, bar, k, rb, bp);
+            tma_load_3d_peer(sb + 2 * TILE_A_BYTES + C::B_BYTES, &mapB, bar, k,
+                             rb, bp + p.b_lo);
+          } else {
+            mbar_expect_tx(&full[stage], (PAIR ? 2 : 1) * C::STAGE_BYTES);
+            tma_load_3d(sb, &mapA, &full[stage], k, ra, half);
+            tma_load_3d(sb + TILE_A_BYTES, &mapA, &full[stage], k, ra,
+                        half + p.a_lo);
+            tma_load_3d(sb + 2 * TILE_A_BYTES, &mapB, &full[stage], k, rb, bp);
+            tma_load_3d(sb + 2 * TILE_A_BYTES + C::B_BYTES, &mapB,
+                        &full[stage], k, rb, bp + p.b_lo);
+          }
           issued[stage]++;
-          if (++stage == TC_STAGES) {
+          if (++stage == C::STAGES) {
             stage = 0;
             ph ^= 1;
           }
         }
       }
-      // Drain: every load this thread issued must land before the CTA exits.
+      // Drain: every load this thread issued must land before the CTA exits:
+      // its own barrier says so, or (odd CTA of a pair, whose loads complete
+      // on the even CTA's barrier) the MMA commit that released the stage.
       volatile int no_abort = 0;
-      for (int s = 0; s < TC_STAGES; ++s)
-        if (issued[s])
-          mbar_wait_bounded(&full[s], (issued[s] - 1) & 1, &no_abort, p.err,
-                            WAIT_LIMIT_NS);
+      for (int s = 0; s < C::STAGES; ++s)
+        if (issued[s]) {
+          if (PAIR && rank)
+            mbar_wait_bounded(&empty[s], (issued[s] - 1) & 1, &no_abort, p.err,
+                              WAIT_LIMIT_NS);
+          else
+            mbar_wait_bounded(&full[s], (issued[s] - 1) & 1, &no_abort, p.err,
+                              WAIT_LIMIT_NS);
+        }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && (!PAIR || rank == 0)) {
       // -------------------------------------------------------- MMA issuer
-      const uint32_t id_pos = idesc_bf16_f32(128, 256, false);
-      const uint32_t id_neg = idesc_bf16_f32(128, 256, true);
+      const int m = PAIR ? 2 * BLK : BLK;
+      const uint32_t id_pos = idesc_bf16_f32(m, 256, false);
+      const uint32_t id_neg = idesc_bf16_f32(m, 256, true);
       int stage = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
       bool ok = true;
-      for (int t = blockIdx.x; ok && t < p.n_tiles; t += gridDim.x) {
-        if (!mbar_wait_bounded(&tempty[acc], aph ^ 1, abort_flag, p.err,
-                               WAIT_LIMIT_NS)) {
+      for (int t = unit; ok && t < p.n_tiles; t += units) {
+        const bool got =
+            PAIR ? mbar_wait_bounded_cluster(&tempty[acc], aph ^ 1, abort_flag,
+                                             p.err, WAIT_LIMIT_NS)
+                 : mbar_wait_bounded(&tempty[acc], aph ^ 1, abort_flag, p.err,
+                                     WAIT_LIMIT_NS);
+        if (!got) {
           ok = false;
+          stop_peer();
           break;
         }
         tc_fence_after();
@@ -223,15 +292,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (!mbar_wait_bounded(&full[stage], ph, abort_flag, p.err,
                                  WAIT_LIMIT_NS)) {
             ok = false;
+            stop_peer();
             break;
           }
           tc_fence_after();
           const int half = kc >= p.k_slice ? 1 : 0;
           const uint32_t id = (half && p.neg_second) ? id_neg : id_pos;
-          const uint32_t a_hi = smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t a_hi = smem_u32(smem + stage * C::STAGE_BYTES);
           const uint32_t a_lo = a_hi + TILE_A_BYTES;
           const uint32_t b_hi = a_hi + 2 * TILE_A_BYTES;
-          const uint32_t b_lo = b_hi + TILE_B_BYTES;
+          const uint32_t b_lo = b_hi + C::B_BYTES;
 #pragma unroll
           for (int k16 = 0; k16 < KC / 16; ++k16) {
             const uint32_t o = (uint32_t)k16 * 32u;
@@ -239,23 +309,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint64_t dal = smem_desc_sw64(a_lo + o);
             const uint64_t dbh = smem_desc_sw64(b_hi + o);
             const uint64_t dbl = smem_desc_sw64(b_lo + o);
-            tc_mma_f16(d, dah, dbh, id, (kc | k16) != 0 ? 1u : 0u);
-            tc_mma_f16(d, dah, dbl, id, 1u);
-            tc_mma_f16(d, dal, dbh, id, 1u);
+            const uint32_t first = (kc | k16) != 0 ? 1u : 0u;
+            if (PAIR) {
+              tc_mma_f16_pair(d, dah, dbh, id, first);
+              tc_mma_f16_pair(d, dah, dbl, id, 1u);
+              tc_mma_f16_pair(d, dal, dbh, id, 1u);
+            } else {
+              tc_mma_f16(d, dah, dbh, id, first);
+              tc_mma_f16(d, dah, dbl, id, 1u);
+              tc_mma_f16(d, dal, dbh, id, 1u);
+            }
           }
-          tc_commit(&empty[stage]);
-          if (++stage == TC_STAGES) {
+          if (PAIR)
+            tc_commit_pair(&empty[stage], 0x3);
+          else
+            tc_commit(&empty[stage]);
+          if (++stage == C::STAGES) {
             stage = 0;
             ph ^= 1;
           }
         }
         if (!ok) break;
-        tc_commit(&tfull[acc]);
+        if (PAIR)
+          tc_commit_pair(&tfull[acc], 0x3);
+        else
+          tc_commit(&tfull[acc]);
         acc ^= 1;
         if (acc == 0) aph ^= 1;
       }
       // Drain: all MMAs issued by this thread complete before TMEM is freed.
-      tc_commit(drain);
+      if (PAIR)
+        tc_commit_pair(drain, 0x1);
+      else
+        tc_commit(drain);
       volatile int no_abort = 0;
       mbar_wait_bounded(drain, 0, &no_abort, p.err, WAIT_LIMIT_NS);
     }
@@ -267,23 +353,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const bool comp = p.g_lo != nullptr;
     int acc = 0;
     uint32_t aph = 0;
-    for (int t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
+    for (int t = unit; t < p.n_tiles; t += units) {
       const int4 tile = p.tiles[t];
       const int tj = tile.y & 0xFFFF, slice = tile.y >> 16;
+      const int ti = PAIR && rank ? tile.z : tile.x;    // this CTA's A rows
+      const bool store = !(PAIR && rank && (tile.w & 1));
       float2 h0[16], h1[16];
       __nv_bfloat162 l0[16], l1[16];
       float2* gh = nullptr;
       __nv_bfloat162* gl = nullptr;
-      if (p.mode == 1) {
-        const int64_t off = (int64_t)tile.z * (BLK * BLK) +
-                            (int64_t)(colh * 64) * BLK + row;
+      if (p.mode == 1 && store) {
+        const int64_t blk = PAIR ? packed_block(ti, tj, p.nb) : (int64_t)tile.z;
+        const int64_t off = blk * (BLK * BLK) + (int64_t)(colh * 64) * BLK + row;
         gh = p.g_hi + off;
         gl = comp ? p.g_lo + off : nullptr;
         load_piece(gh, gl, h0, l0, comp);  // prefetch before the MMAs finish
       }
       if (!mbar_wait_bounded(&tfull[acc], aph, abort_flag, p.err,
-                             WAIT_LIMIT_NS))
+                             WAIT_LIMIT_NS)) {
+        stop_peer();
         break;
+      }
       __syncwarp();
       tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) +
@@ -293,7 +383,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float re[16], im[16];
         tmem_ld16(base + (uint32_t)(pc * 16), re);
         tmem_ld16(base + 128u + (uint32_t)(pc * 16), im);
-        if (p.mode == 1 && pc < 3) {
+        if (p.mode == 1 && store && pc < 3) {
           const int64_t nxt = (int64_t)(16 * (pc + 1)) * BLK;
           if (pc & 1)
             load_piece(gh + nxt, comp ? gl + nxt : nullptr, h0, l0, comp);
@@ -301,6 +391,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             load_piece(gh + nxt, comp ? gl + nxt : nullptr, h1, l1, comp);
         }
         tmem_wait_ld();
+        if (!store) continue;
         if (p.mode == 1) {
           const int64_t cur = (int64_t)(16 * pc) * BLK;
           if (pc & 1)
@@ -310,7 +401,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         } else {
           float4* dst = reinterpret_cast<float4*>(
               p.part + slice * p.part_slice +
-              (int64_t)(tile.x * BLK + row) * p.part_ld + tj * BLK + colh * 64 +
+              (int64_t)(ti * BLK + row) * p.part_ld + tj * BLK + colh * 64 +
               pc * 16);
 #pragma unroll
           for (int c = 0; c < 8; ++c)
@@ -318,17 +409,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       tc_fence_before();
-      mbar_arrive(&tempty[acc]);
+      if (PAIR) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(&tempty[acc], 0u);
+      } else {
+        mbar_arrive(&tempty[acc]);
+      }
       acc ^= 1;
       if (acc == 0) aph ^= 1;
     }
   }
   tc_fence_before();
-  __syncthreads();
+  if (PAIR)
+    cluster_sync();  // no CTA leaves while its peer may still touch it
+  else
+    __syncthreads();
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    if (PAIR)
+      tmem_dealloc_pair(tmem, TMEM_COLS);
+    else
+      tmem_dealloc(tmem, TMEM_COLS);
   }
 }
 
@@ -405,26 +507,81 @@ bool encode_planes(CUtensorMap* m, void* base, int cols, int rows, int planes,
   return true;
 }
 
-// grid_cap > 0 limits the persistent grid to that many CTAs (one per SM).
+// Launch one persistent tcgen05 grid over p.n_tiles work items (tiles, or
+// tile pairs on CTA pairs) with at most grid_cap CTAs (0: one per SM).
+template <bool PAIR>
+cudaError_t launch_tc_grid(cudaStream_t st, int sm_count, int pair_limit,
+                           const CUtensorMap& ma, const CUtensorMap& mb,
+                           const TcParams& p, int grid_cap) {
+  cudaError_t e = cudaFuncSetAttribute(
+      k_tc_cgemm<PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      TcCfg<PAIR>::SMEM);
+  if (e != cudaSuccess) return e;
+  const int cap = grid_cap > 0 && grid_cap < sm_count ? grid_cap : sm_count;
+  if (p.n_tiles <= 0) return cudaSuccess;
+  if (!PAIR) {
+    const int grid = p.n_tiles < cap ? p.n_tiles : cap;
+    k_tc_cgemm<PAIR><<<grid, TC_THREADS, TcCfg<PAIR>::SMEM, st>>>(ma, mb, p);
+    return cudaGetLastError();
+  }
+  int pairs = std::min(p.n_tiles, std::max(1, cap / 2));
+  if (pair_limit > 0) pairs = std::min(pairs, pair_limit);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = TcCfg<PAIR>::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_tc_cgemm<PAIR>, ma, mb, p);
+}
+
+// Clusters of two of k_tc_cgemm<true> that fit on the device at once.
+int pair_limit(osar_ctx* ctx) {
+  if (ctx->tc_pair_limit == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ctx->sm_count & ~1));
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = TcCfg<true>::SMEM;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaFuncSetAttribute(k_tc_cgemm<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcCfg<true>::SMEM) == cudaSuccess &&
+        cudaOccupancyMaxActiveClusters(&n, k_tc_cgemm<true>, &cfg) == cudaSuccess &&
+        n > 0)
+      ctx->tc_pair_limit = n;
+    else
+      ctx->tc_pair_limit = -1;  // unknown: one pair per two SMs
+    cudaGetLastError();
+  }
+  return ctx->tc_pair_limit > 0 ? ctx->tc_pair_limit : 0;
+}
+
 cudaError_t launch_tc(osar_ctx* ctx, const CUtensorMap& ma,
                       const CUtensorMap& mb, const TcParams& p, int kind,
-                      int grid_cap = 0) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(
-        k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  int grid = p.n_tiles < ctx->sm_count ? p.n_tiles : ctx->sm_count;
-  if (grid_cap > 0 && grid > grid_cap) grid = grid_cap;
-  if (grid <= 0) return cudaSuccess;
+                      bool pairs, int grid_cap) {
   ProfEvent ev;
   prof_begin(ctx, kind, &ev);
-  k_tc_cgemm<<<grid, TC_THREADS, TC_SMEM, ctx->stream>>>(ma, mb, p);
+  const cudaError_t e =
+      pairs ? launch_tc_grid<true>(ctx->stream, ctx->sm_count, pair_limit(ctx),
+                                   ma, mb, p, grid_cap)
+            : launch_tc_grid<false>(ctx->stream, ctx->sm_count, 0, ma, mb, p,
+                                    grid_cap);
   prof_end(ctx, &ev);
   ctx->launches++;
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
@@ -436,6 +593,8 @@ bool make_tensor_maps(osar_ctx* ctx, std::string* err) {
     return false;
   if (ctx->dict) {
     if (!encode_planes(&ctx->map_d_rows1, ctx->Dpl, ctx->Np, ctx->Mp, 4, 1, err))
+      return false;
+    if (!encode_planes(&ctx->map_f_rows1, ctx->Fpl, ctx->Np, ctx->Kp, 6, 1, err))
       return false;
     if (!encode_planes(&ctx->map_f_rows2, ctx->Fpl, ctx->Np, ctx->Kp, 6, 2, err))
       return false;
@@ -451,9 +610,10 @@ int dict_slices(int np) {
 }
 
 cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap) {
+  const bool pairs = (ctx->cfg.tc_pairs & 1) != 0;
   TcParams p = {};
-  p.tiles = ctx->dict_tiles;
-  p.n_tiles = ctx->n_dict_tiles;
+  p.tiles = pairs ? ctx->dict_pairs : ctx->dict_tiles;
+  p.n_tiles = pairs ? ctx->n_dict_pairs : ctx->n_dict_tiles;
   p.k_chunks = ctx->Np / KC;
   p.k_slice = p.k_chunks / ctx->dict_slices;
   p.a_lo = 2;
@@ -465,8 +625,9 @@ cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap) {
   p.part_slice = (int64_t)ctx->Mp * ctx->Kp;
   p.nb = ctx->nb;
   p.err = &ctx->scal->error;
-  cudaError_t e =
-      launch_tc(ctx, ctx->map_d_rows1, ctx->map_f_rows2, p, KCL_DICT, grid_cap);
+  cudaError_t e = launch_tc(ctx, ctx->map_d_rows1,
+                            pairs ? ctx->map_f_rows1 : ctx->map_f_rows2, p,
+                            KCL_DICT, pairs, grid_cap);
   if (e != cudaSuccess) return e;
   const int64_t groups = (int64_t)ctx->Mp * ctx->Kp / 8;
   ProfEvent ev;
@@ -480,9 +641,10 @@ cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap) {
 }
 
 cudaError_t launch_gram_tc(osar_ctx* ctx) {
+  const bool pairs = (ctx->cfg.tc_pairs & 2) != 0;
   TcParams p = {};
-  p.tiles = ctx->gram_tiles;
-  p.n_tiles = (int)ctx->nblk;
+  p.tiles = pairs ? ctx->gram_pairs : ctx->gram_tiles;
+  p.n_tiles = pairs ? ctx->n_gram_pairs : (int)ctx->nblk;
   p.k_chunks = ctx->Kp / KC;
   p.k_slice = p.k_chunks;
   p.a_lo = 3;
@@ -493,7 +655,9 @@ cudaError_t launch_gram_tc(osar_ctx* ctx) {
   p.g_lo = ctx->g_lo;
   p.nb = ctx->nb;
   p.err = &ctx->scal->error;
-  return launch_tc(ctx, ctx->map_a_rows1, ctx->map_a_rows2, p, KCL_GRAM);
+  return launch_tc(ctx, ctx->map_a_rows1,
+                   pairs ? ctx->map_a_rows1 : ctx->map_a_rows2, p, KCL_GRAM,
+                   pairs, 0);
 }
 
 bool encode_plane_map(CUtensorMap* m, void* base, int cols, int rows,
@@ -507,13 +671,6 @@ cudaError_t launch_gram_tc_tiles(cudaStream_t st, int sm_count,
                                  const CUtensorMap& m1, const CUtensorMap& m2,
                                  const int4* tiles, int n_tiles, float2* g_hi,
                                  __nv_bfloat162* g_lo, int kp, int* err) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(
-        k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   TcParams p = {};
   p.tiles = tiles;
   p.n_tiles = n_tiles;
@@ -526,10 +683,7 @@ cudaError_t launch_gram_tc_tiles(cudaStream_t st, int sm_count,
   p.g_hi = g_hi;
   p.g_lo = g_lo;
   p.err = err;
-  const int grid = n_tiles < sm_count ? n_tiles : sm_count;
-  if (grid <= 0) return cudaSuccess;
-  k_tc_cgemm<<<grid, TC_THREADS, TC_SMEM, st>>>(m1, m2, p);
-  return cudaGetLastError();
+  return launch_tc_grid<false>(st, sm_count, 0, m1, m2, p, 0);
 }
 
 }  // namespace osar

@@ -66,7 +66,8 @@ void free_all(osar_ctx* ctx) {
                   ctx->zt, ctx->vt, ctx->xt, ctx->bmax, ctx->d32,
                   ctx->gram_tiles, ctx->dict_tiles, ctx->A, ctx->F, ctx->D,
                   ctx->Apl, ctx->Fpl, ctx->Dpl, ctx->sim_rho, ctx->sim_nz,
-                  ctx->sim_idx, ctx->sim_d, ctx->dict_part};
+                  ctx->sim_idx, ctx->sim_d, ctx->dict_part, ctx->gram_pairs,
+                  ctx->dict_pairs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
@@ -127,12 +128,15 @@ osar_status validate(const osar_config* c, std::string* why) {
   if (c->overlap_synthesis != 0 && c->overlap_synthesis != 1)
     return *why = "overlap_synthesis must be 0 or 1", OSAR_E_INVALID;
   if (c->synth_ctas < 0) return *why = "synth_ctas must be >= 0", OSAR_E_INVALID;
+  if (c->tc_pairs < 0 || c->tc_pairs > 3)
+    return *why = "tc_pairs must be in [0, 3]", OSAR_E_INVALID;
   return OSAR_OK;
 }
 
 void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
                   std::vector<int>& seg_begin, std::vector<int4>& gram_tiles,
-                  std::vector<int4>& dict_tiles) {
+                  std::vector<int4>& dict_tiles, std::vector<int4>& gram_pairs,
+                  std::vector<int4>& dict_pairs) {
   const int nb = ctx->nb;
   // matvec segments: runs of S blocks of one block column
   int64_t target = (int64_t)ctx->sm_count * 2 * 12;
@@ -157,6 +161,16 @@ void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
         for (int J = (bj > I ? bj : I); J < bj + SB && J < nb; ++J)
           gram_tiles.push_back(
               make_int4(I, J, (int)packed_block(I, J, nb), 0));
+  // The same super-blocks for CTA pairs: rows I0 and I0 + 1 of one block
+  // column J share B; on the diagonal an even I0 == J has no partner.
+  for (int bi = 0; bi < nb; bi += SB)
+    for (int bj = bi; bj < nb; bj += SB)
+      for (int J = bj; J < bj + SB && J < nb; ++J)
+        for (int I0 = bi; I0 < bi + SB && I0 <= J; I0 += 2) {
+          const bool single = I0 + 1 > J;
+          gram_pairs.push_back(
+              make_int4(I0, J, single ? I0 : I0 + 1, single ? 1 : 0));
+        }
   if (ctx->dict) {
     // Split-K slices (tensor-core path only) one after another: the tiles
     // in flight together share one slice of the phase operand F (6 planes x
@@ -168,6 +182,13 @@ void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
       for (int I = 0; I < nb; ++I)
         for (int J = 0; J < ctx->Kp / BLK; ++J)
           dict_tiles.push_back(make_int4(I, J | (sl << 16), 0, 0));
+    for (int sl = 0; sl < S; ++sl)
+      for (int I0 = 0; I0 < nb; I0 += 2)
+        for (int J = 0; J < ctx->Kp / BLK; ++J) {
+          const bool single = I0 + 1 >= nb;
+          dict_pairs.push_back(make_int4(I0, J | (sl << 16),
+                                         single ? I0 : I0 + 1, single ? 1 : 0));
+        }
   }
 }
 
@@ -212,10 +233,12 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
 
   std::vector<int4> segs;
   std::vector<int> seg_begin;
-  std::vector<int4> gtiles, dtiles;
-  build_tables(ctx, segs, seg_begin, gtiles, dtiles);
+  std::vector<int4> gtiles, dtiles, gpairs, dpairs;
+  build_tables(ctx, segs, seg_begin, gtiles, dtiles, gpairs, dpairs);
   ctx->nseg = (int)segs.size();
   ctx->n_dict_tiles = (int)dtiles.size();
+  ctx->n_gram_pairs = (int)gpairs.size();
+  ctx->n_dict_pairs = (int)dpairs.size();
 
   const size_t cplx = ctx->prec == OSAR_FP64 ? 16 : 8;
   const int64_t Mp = ctx->Mp, Np = ctx->Np, Kp = ctx->Kp;
@@ -249,6 +272,8 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   AL(ctx->seg_begin, sizeof(int) * seg_begin.size());
   AL(ctx->gram_tiles, sizeof(int4) * gtiles.size());
   if (ctx->dict) AL(ctx->dict_tiles, sizeof(int4) * (dtiles.size() ? dtiles.size() : 1));
+  AL(ctx->gram_pairs, sizeof(int4) * gpairs.size());
+  if (ctx->dict) AL(ctx->dict_pairs, sizeof(int4) * (dpairs.size() ? dpairs.size() : 1));
   if (ctx->prec == OSAR_SPLIT_BF16) {
     AL(ctx->Apl, 2 * 6 * Mp * Kp);
     if (ctx->dict) {
@@ -302,6 +327,14 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   if (e == cudaSuccess && ctx->dict && !dtiles.empty())
     e = cudaMemcpyAsync(ctx->dict_tiles, dtiles.data(),
                         sizeof(int4) * dtiles.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->gram_pairs, gpairs.data(),
+                        sizeof(int4) * gpairs.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess && ctx->dict && !dpairs.empty())
+    e = cudaMemcpyAsync(ctx->dict_pairs, dpairs.data(),
+                        sizeof(int4) * dpairs.size(), cudaMemcpyHostToDevice,
                         ctx->stream);
   // initial scalars and power vector v = 1/sqrt(M) on the M real atoms
   DevScalars s0 = {};
@@ -529,6 +562,7 @@ void osar_config_default(osar_config* c) {
   c->cuda_stream = nullptr;
   c->overlap_synthesis = 1;
   c->synth_ctas = 0;
+  c->tc_pairs = 1;
 }
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
