@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--no-overlap", action="store_true",
                     help="run each pulse's dictionary product on the main "
                          "stream instead of beside the previous burst")
-    ap.add_argument("--no-tc-pairs", action="store_true",
-                    help="one SM per tensor-core tile instead of CTA pairs")
+    ap.add_argument("--tc-pairs", type=int, default=3,
+                    help="tensor-core products on SM pairs: bit 0 dictionary "
+                         "product, bit 1 Gram update (0: one SM per tile)")
     ap.add_argument("--synth-ctas", type=int, default=0,
                     help="SMs for the overlapped dictionary product (0: auto)")
     ap.add_argument("--workload", choices=["c2", "probe8k"], default="c2",
@@ -193,7 +194,7 @@ def workload(name="c2"):
     return synth.workloads()[WORKLOAD]
 
 
-def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=1):
+def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3):
     from paper_2603_08582_gb300 import osar
     gauss = w.dictionary == "gaussian"
     cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
@@ -237,7 +238,7 @@ def run_ours(args):
     W, K = args.warmup, args.steps
     stream = torch.cuda.Stream()
     ov = dict(overlap=not args.no_overlap, synth_ctas=args.synth_ctas,
-              tc_pairs=0 if args.no_tc_pairs else 1)
+              tc_pairs=args.tc_pairs)
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
     total = W + K + 1
     track, data = pulse_data(ctx, w, total)
@@ -406,7 +407,8 @@ def run_ours(args):
                    "precision": "split_bf16 (compensated)",
                    "overlap_synthesis": not args.no_overlap,
                    "synth_ctas": args.synth_ctas or "auto",
-                   "tc_pairs": "off" if args.no_tc_pairs else "dictionary product",
+                   "tc_pairs": {0: "off", 1: "dictionary product", 2: "Gram update",
+                                3: "dictionary product and Gram update"}[args.tc_pairs & 3],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (packed Gram 4.3 GB streamed per step)"},
         "clocks": clocks,

@@ -121,18 +121,17 @@ typedef struct {
   /* SPLIT_BF16: tensor-core products on pairs of SMs (one M = 256 tcgen05
      MMA per two 128 x 128 blocks that share their B rows, each SM loading
      half of B) instead of one SM per block.  Bit 0: the dictionary product;
-     bit 1: the Gram update.  Bitwise the same results either way.  Default
-     1: the pairs cut the product's operand traffic, which matters beside
-     the burst; the Gram update is bound by its read-modify-write epilogue
-     and runs slightly faster on single SMs. */
+     bit 1: the Gram update (whose read-modify-write of the Gram then goes
+     through shared memory by bulk copies, in the room the smaller operand
+     ring leaves).  Bitwise the same results either way.  Default 3. */
   int32_t tc_pairs;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
    9.9-10.1 GHz, identity dictionary, FP64, lambda = 0.05 relative,
    30 / 4 power steps, margin 0.01, carried momentum, compensated = 1,
-   overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 1
-   (dictionary product on SM pairs). */
+   overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
+   (both tensor-core products on SM pairs). */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128

@@ -33,8 +33,10 @@
 // of tile t overlaps the MMAs of tile t+1.
 // CTA-pair variant (clusters of two, cta_group::2): two tiles that share
 // their B rows run as one M = 256 MMA on two SMs, each SM loading its own A
-// rows and one of the two B planes (32 KB per 7-stage ring slot instead of
-// 48 KB); see k_tc_cgemm<true>.
+// rows and one of the two B planes (32 KB per ring slot instead of 48 KB);
+// in Gram mode the ring keeps 4 slots and the Gram read-modify-write is
+// staged through the freed shared memory by bulk copies; see
+// k_tc_cgemm<true>.
 //
 // Accumulation in the tensor pipe rounds its FP32 partial sums toward zero,
 // which biases long reductions (|A| shrinks by ~(steps) 2^-24).  The
@@ -60,6 +62,14 @@ constexpr uint32_t TMEM_COLS = 512;
 
 // Ring geometry: one CTA per tile (B = 256 rows, two planes) or CTA pairs
 // (B = this CTA's 128 rows, one plane).
+// Gram epilogue of the pair kernel: per 64-column half of the tile, a
+// 16-column piece of the block (hi 16 KB + lo 8 KB, contiguous in the
+// column-major block) is staged by a bulk copy; two slots per half.
+constexpr int G_PIECE_HI = 16 * BLK * 8;
+constexpr int G_PIECE_LO = 16 * BLK * 4;
+constexpr int G_SLOT = G_PIECE_HI + G_PIECE_LO;  // 24 KB
+constexpr int PAIR_GRAM_STAGES = 4;              // operand ring beside the slots
+
 template <bool PAIR>
 struct TcCfg {
   static constexpr int STAGES = PAIR ? 7 : 4;
@@ -69,6 +79,9 @@ struct TcCfg {
 };
 static_assert(TcCfg<true>::SMEM <= 227 * 1024 && TcCfg<false>::SMEM <= 227 * 1024,
               "tcgen05 ring exceeds shared memory");
+static_assert(PAIR_GRAM_STAGES * TcCfg<true>::STAGE_BYTES + 4 * G_SLOT <=
+                  TcCfg<true>::STAGES * TcCfg<true>::STAGE_BYTES,
+              "staged Gram epilogue does not fit beside the operand ring");
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 struct TcParams {
@@ -158,11 +171,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* tfull = empty + C::STAGES;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* gfull = drain + 1;    // staged Gram pieces: slot landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gfull + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  // pair kernel, Gram mode: shorter operand ring, Gram pieces staged after it
+  const bool staged = PAIR && p.mode == 1;
+  const int nst = staged ? PAIR_GRAM_STAGES : C::STAGES;
   const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   // a failed wait stops the peer CTA too
@@ -178,6 +195,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], PAIR ? 2 * (EPI_THREADS / 32) : EPI_THREADS);
     }
+    for (int b = 0; b < 4; ++b) mbar_init(&gfull[b], 1);
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -246,7 +264,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         &full[stage], k, rb, bp + p.b_lo);
           }
           issued[stage]++;
-          if (++stage == C::STAGES) {
+          if (++stage == nst) {
             stage = 0;
             ph ^= 1;
           }
@@ -256,7 +274,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // its own barrier says so, or (odd CTA of a pair, whose loads complete
       // on the even CTA's barrier) the MMA commit that released the stage.
       volatile int no_abort = 0;
-      for (int s = 0; s < C::STAGES; ++s)
+      for (int s = 0; s < nst; ++s)
         if (issued[s]) {
           if (PAIR && rank)
             mbar_wait_bounded(&empty[s], (issued[s] - 1) & 1, &no_abort, p.err,
@@ -324,7 +342,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_commit_pair(&empty[stage], 0x3);
           else
             tc_commit(&empty[stage]);
-          if (++stage == C::STAGES) {
+          if (++stage == nst) {
             stage = 0;
             ph ^= 1;
           }
@@ -344,6 +362,128 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_commit(drain);
       volatile int no_abort = 0;
       mbar_wait_bounded(drain, 0, &no_abort, p.err, WAIT_LIMIT_NS);
+    }
+  } else if (staged) {
+    // ------------------------------------- epilogue, Gram, staged pieces
+    // Each 64-column half (4 warps) walks its 16-column pieces of every
+    // tile in order; piece n sits in slot n & 1 of its half.  One thread per
+    // half bulk-loads a piece into its slot, the 4 warps update it there
+    // (TwoSum, in place), and the same thread bulk-stores it back and then
+    // loads piece n + 2 into the slot.  Two pieces (48 KB per CTA) are in
+    // flight each way without holding registers, and the next tile's first
+    // pieces load while this tile's MMAs run.
+    const int q = warp & 3;
+    const int colh = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    const bool comp = p.g_lo != nullptr;
+    const bool loader = lane == 0 && (warp - 2) % 4 == 0;
+    uint8_t* slots = smem + PAIR_GRAM_STAGES * C::STAGE_BYTES + colh * 2 * G_SLOT;
+    uint64_t* gf = gfull + colh * 2;
+    const uint32_t bytes = G_PIECE_HI + (comp ? G_PIECE_LO : 0);
+    // offset of piece pc (16 columns) of the block this CTA updates for tile t
+    auto piece_off = [&](int t, int pc) {
+      const int4 tile = p.tiles[t];
+      const int ti = rank ? tile.z : tile.x;
+      return packed_block(ti, tile.y & 0xFFFF, p.nb) * (BLK * BLK) +
+             (int64_t)(colh * 64 + pc * 16) * BLK;
+    };
+    auto issue = [&](int t, int pc, int b) {
+      const int64_t off = piece_off(t, pc);
+      uint8_t* dst = slots + b * G_SLOT;
+      mbar_expect_tx(&gf[b], bytes);
+      bulk_load(dst, p.g_hi + off, G_PIECE_HI, &gf[b]);
+      if (comp) bulk_load(dst + G_PIECE_HI, p.g_lo + off, G_PIECE_LO, &gf[b]);
+    };
+    uint32_t issued[2] = {0, 0};
+    if (loader && unit < p.n_tiles) {
+      issue(unit, 0, 0);
+      issue(unit, 1, 1);
+      issued[0] = issued[1] = 1;
+    }
+    int acc = 0;
+    uint32_t aph = 0;
+    bool fail = false;
+    int n = 0;  // pieces of this half processed so far
+    // The 4 warps of a half pass the same barriers: every tile they enter
+    // has 4 barriers, and whether to stop is the OR over the half, taken at
+    // a barrier, so all of them leave together.
+    for (int t = unit; t < p.n_tiles; t += units) {
+      const bool store = !(rank && (p.tiles[t].w & 1));
+      if (!mbar_wait_bounded(&tfull[acc], aph, abort_flag, p.err,
+                             WAIT_LIMIT_NS))
+        fail = true;
+      fail = __any_sync(0xffffffffu, fail);
+      if (fail) stop_peer();
+      tc_fence_after();
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) +
+                            (uint32_t)acc * 256u + (uint32_t)colh * 64u;
+      for (int pc = 0; pc < 4; ++pc, ++n) {
+        const int b = n & 1;
+        const uint32_t gph = (uint32_t)(n >> 1) & 1u;
+        float re[16], im[16];
+        if (!fail) {
+          tmem_ld16(base + (uint32_t)(pc * 16), re);
+          tmem_ld16(base + 128u + (uint32_t)(pc * 16), im);
+          tmem_wait_ld();
+          if (!mbar_wait_bounded(&gf[b], gph, abort_flag, p.err, WAIT_LIMIT_NS))
+            fail = true;
+          fail = __any_sync(0xffffffffu, fail);
+          if (fail) stop_peer();
+        }
+        uint8_t* sl = slots + b * G_SLOT;
+        if (!fail && store) {
+          float2* hs = reinterpret_cast<float2*>(sl) + row;
+          __nv_bfloat162* ls =
+              reinterpret_cast<__nv_bfloat162*>(sl + G_PIECE_HI) + row;
+          float2 h[16];
+          __nv_bfloat162 l[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) h[c] = hs[c * BLK];
+          if (comp) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) l[c] = ls[c * BLK];
+          }
+          gram_piece(hs, comp ? ls : nullptr, h, l, re, im, comp);
+          fence_proxy_async();  // the bulk store reads what was written here
+        }
+        // all 4 warps of the half have updated the piece (or given up)
+        if (named_barrier_or(1 + colh, EPI_THREADS / 2, fail || *abort_flag)) {
+          fail = true;
+          break;
+        }
+        if (loader) {
+          if (store) {
+            const int64_t off = piece_off(t, pc);
+            bulk_store(p.g_hi + off, sl, G_PIECE_HI);
+            if (comp) bulk_store(p.g_lo + off, sl + G_PIECE_HI, G_PIECE_LO);
+            bulk_commit();
+          }
+          // next piece for this slot: n + 2 (this tile, or the next one's)
+          const int m = pc + 2;
+          const int tn = m < 4 ? t : t + units;
+          if (tn < p.n_tiles) {
+            bulk_wait_read();
+            issue(tn, m & 3, b);
+            issued[b]++;
+          }
+        }
+        __syncwarp();
+      }
+      if (fail) break;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(&tempty[acc], 0u);
+      acc ^= 1;
+      if (acc == 0) aph ^= 1;
+    }
+    // every piece this thread loaded or stored completes before the CTA exits
+    if (loader) {
+      volatile int no_abort = 0;
+      for (int b = 0; b < 2; ++b)
+        if (issued[b])
+          mbar_wait_bounded(&gf[b], (issued[b] - 1) & 1, &no_abort, p.err,
+                            WAIT_LIMIT_NS);
+      bulk_wait_all();
     }
   } else {
     // ---------------------------------------------------------- epilogue

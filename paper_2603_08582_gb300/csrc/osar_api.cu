@@ -562,7 +562,7 @@ void osar_config_default(osar_config* c) {
   c->cuda_stream = nullptr;
   c->overlap_synthesis = 1;
   c->synth_ctas = 0;
-  c->tc_pairs = 1;
+  c->tc_pairs = 3;
 }
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {

@@ -47,7 +47,7 @@ def test_config_defaults_and_layout(lib):
     assert cfg.restart_momentum == 0 and cfg.compensated == 1
     assert cfg.cuda_stream is None
     assert cfg.overlap_synthesis == 1 and cfg.synth_ctas == 0
-    assert cfg.tc_pairs == 1
+    assert cfg.tc_pairs == 3
 
 
 @pytest.mark.parametrize("field,value", [
