@@ -57,10 +57,13 @@ def parse():
                          "product, bit 1 Gram update (0: one SM per tile)")
     ap.add_argument("--synth-ctas", type=int, default=0,
                     help="SMs for the overlapped dictionary product (0: auto)")
-    ap.add_argument("--workload", choices=["c2", "probe8k"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "probe8k", "probe_dict"],
+                    default="c2",
                     help="c2: the 128x128 headline workload; probe8k: a "
                          "64x128 pixel-basis scene (M = 8192, 272 MB packed "
-                         "Gram) for profiler captures")
+                         "Gram) for profiler captures; probe_dict: a 64x64 "
+                         "scene with 8192 Gaussian atoms (dictionary product "
+                         "of 0.4 TFLOP) for profiler captures")
     return ap.parse_args()
 
 
@@ -191,6 +194,12 @@ def workload(name="c2"):
             name="probe8k_64x128", nx=128, ny=64, n_freq=512, f_lo_hz=9.75e9,
             f_hi_hz=10.25e9, n_pulses=64, span_deg=45.0, sparsity=0.03,
             snr_db=25.0, seed=8)
+    if name == "probe_dict":
+        return synth.Workload(
+            name="probe_dict_64x64_M8192", nx=64, ny=64, n_freq=512,
+            f_lo_hz=9.75e9, f_hi_hz=10.25e9, n_pulses=64, span_deg=45.0,
+            dictionary="gaussian", n_atoms=8192, dict_seed=2, sparsity=0.03,
+            snr_db=25.0, seed=9)
     return synth.workloads()[WORKLOAD]
 
 
