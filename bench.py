@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-overlap", action="store_true",
                     help="run each pulse's dictionary product on the main "
                          "stream instead of beside the previous burst")
+    ap.add_argument("--no-fuse", action="store_true",
+                    help="separate Gram passes for the last power step and "
+                         "the first FISTA step of a pulse")
     ap.add_argument("--tc-pairs", type=int, default=3,
                     help="tensor-core products on SM pairs: bit 0 dictionary "
                          "product, bit 1 Gram update (0: one SM per tile)")
@@ -203,7 +206,8 @@ def workload(name="c2"):
     return synth.workloads()[WORKLOAD]
 
 
-def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3):
+def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
+             fuse=True):
     from paper_2603_08582_gb300 import osar
     gauss = w.dictionary == "gaussian"
     cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
@@ -212,7 +216,8 @@ def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3):
                            n_atoms=w.m_atoms if gauss else None,
                            dict_seed=w.dict_seed, lam=w.lambda_rel,
                            stream=stream, overlap_synthesis=overlap,
-                           synth_ctas=synth_ctas, tc_pairs=tc_pairs)
+                           synth_ctas=synth_ctas, tc_pairs=tc_pairs,
+                           fuse_first_step=fuse)
     return osar.Osar(cfg)
 
 
@@ -247,7 +252,7 @@ def run_ours(args):
     W, K = args.warmup, args.steps
     stream = torch.cuda.Stream()
     ov = dict(overlap=not args.no_overlap, synth_ctas=args.synth_ctas,
-              tc_pairs=args.tc_pairs)
+              tc_pairs=args.tc_pairs, fuse=not args.no_fuse)
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
     total = W + K + 1
     track, data = pulse_data(ctx, w, total)
@@ -334,7 +339,8 @@ def run_ours(args):
                 ctx_e.wait_coeffs((q - 1) % 2)
         ctx_e.wait_coeffs((K - 1) % 2)
         e2e_s = time.perf_counter() - t0
-        fista_steps = ctx_e.profile_passes() - K * POWER_ITERS
+        fista_steps = (ctx_e.profile_passes() - K * POWER_ITERS
+                       + (0 if args.no_fuse else K))
         ctx_e.close()
 
     ms = max_over_ranks(ms, f"cuda:{local_rank}")
@@ -418,6 +424,7 @@ def run_ours(args):
                    "synth_ctas": args.synth_ctas or "auto",
                    "tc_pairs": {0: "off", 1: "dictionary product", 2: "Gram update",
                                 3: "dictionary product and Gram update"}[args.tc_pairs & 3],
+                   "fused_first_step": not args.no_fuse,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (packed Gram 4.3 GB streamed per step)"},
         "clocks": clocks,
@@ -426,7 +433,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": w.m_atoms * 16 + 4,
                 "mean_iters_per_pulse": round(fista_steps / K, 2),
                 "pipelined": "image of pulse s read while pulse s+1 is queued"},
-        "mean_iters_per_pulse": round((passes - K * POWER_ITERS) / K, 2),
+        # Gram passes per pulse: the power steps, plus the FISTA steps less
+        # the first one when it shares the last power step's pass
+        "mean_iters_per_pulse": round((passes - K * POWER_ITERS) / K
+                                      + (0 if args.no_fuse else 1), 2),
         "time_to_tol": ttt,
         "gpu_launches": int(launches),
         "roofline": roofline,

@@ -125,13 +125,18 @@ typedef struct {
      through shared memory by bulk copies, in the room the smaller operand
      ring leaves).  Bitwise the same results either way.  Default 3. */
   int32_t tc_pairs;
+  /* 1: the last power step of a push also applies the Gram to the next
+     burst's first iterate z = c_hat (both vectors in one pass over the
+     Gram), and that burst's first FISTA step uses the result; one Gram
+     pass fewer per pulse, bitwise the same results.  0: separate passes. */
+  int32_t fuse_first_step;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
    9.9-10.1 GHz, identity dictionary, FP64, lambda = 0.05 relative,
    30 / 4 power steps, margin 0.01, carried momentum, compensated = 1,
    overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
-   (both tensor-core products on SM pairs). */
+   (both tensor-core products on SM pairs), fuse_first_step = 1. */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128

@@ -93,6 +93,9 @@ struct osar_ctx {
                                    // bf16 (re, im) per entry
   void* segpart = nullptr;     // matvec segment partials (nseg x BLK)
   void* tilepart = nullptr;    // matvec per-block partials (nblk x BLK)
+  void* segpart2 = nullptr;    // fuse_first_step: G z_1 partials of the
+  void* tilepart2 = nullptr;   // next burst's first step
+  bool first_ready = false;    // segpart2 / tilepart2 hold G z_1 for the burst
   int4* segs = nullptr;        // matvec work items (J, I0, I1, slot)
   int* seg_begin = nullptr;    // first segment of block column J (nb + 1)
   double* bmax = nullptr;      // per-block max |b_j|^2 (data update)
@@ -191,7 +194,9 @@ cudaError_t launch_gram_tc(osar_ctx* ctx);
 
 // ---- k_fista.cu ------------------------------------------------------------
 cudaError_t launch_data_update(osar_ctx* ctx);
-cudaError_t launch_power_steps(osar_ctx* ctx, int steps);
+// fuse: the last step also applies the Gram to the next burst's z_1 = c_hat
+// (burst started here; its first FISTA step reuses that pass)
+cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse);
 cudaError_t launch_set_working(osar_ctx* ctx);
 cudaError_t launch_burst_begin(osar_ctx* ctx);
 cudaError_t launch_iter_begin(osar_ctx* ctx, double tol);

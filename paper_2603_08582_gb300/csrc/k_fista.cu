@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(FIN_THREADS)
                      const int* __restrict__ seg_begin, int nb,
                      const double2* __restrict__ b, double2* __restrict__ c,
                      double2* __restrict__ z, T2* __restrict__ zt,
-                     double2* __restrict__ part, DevScalars* sc) {
+                     double2* __restrict__ part, DevScalars* sc,
+                     int count_pass) {
   if (sc->converged) return;
   __shared__ double sh[3];  // tau, alpha, beta
   if (threadIdx.x == 0) {
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
     const double t = sc->t;
     sc->t = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
     sc->iters += 1;
-    sc->passes += 1;
+    sc->passes += count_pass;
     if (sc->tol > 0.0 && sqrt(tot.x) <= sc->tol * sqrt(tot.y)) sc->converged = 1;
     sc->done = 0;
   }
@@ -413,19 +414,29 @@ __global__ void __launch_bounds__(FIN_THREADS)
   if (i < BLK && K * BLK + i < m_valid) y[K * BLK + i] = v;
 }
 
-// One matvec launch: one CTA per SM (the shared-memory ring fills an SM),
-// at most one per segment.
+// One matvec launch over R vectors: one CTA per SM (the shared-memory ring
+// fills an SM), at most one per segment.
+template <typename T, int R>
+void launch_mv(osar_ctx* ctx, const MvArgs<T, R>& a, int gated) {
+  using C = Mv<T, R>;
+  cudaFuncSetAttribute(k_matvec<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       C::SMEM);
+  const unsigned grid =
+      (unsigned)(ctx->nseg < ctx->sm_count ? ctx->nseg : ctx->sm_count);
+  k_matvec<T, R><<<grid, C::THREADS, C::SMEM, ctx->stream>>>(
+      (const typename Vec<T>::T2*)ctx->g_hi, a, ctx->segs, ctx->nseg, ctx->nb,
+      ctx->scal, gated, matvec_queue(ctx->scal));
+}
+
 template <typename T>
 void launch_mv(osar_ctx* ctx, const void* xt, void* segp, void* tilep,
                int gated) {
   using T2 = typename Vec<T>::T2;
-  cudaFuncSetAttribute(k_matvec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       Mv<T>::SMEM);
-  const unsigned grid =
-      (unsigned)(ctx->nseg < ctx->sm_count ? ctx->nseg : ctx->sm_count);
-  k_matvec<T><<<grid, Mv<T>::THREADS, Mv<T>::SMEM, ctx->stream>>>(
-      (const T2*)ctx->g_hi, (const T2*)xt, (T2*)segp, (T2*)tilep, ctx->segs,
-      ctx->nseg, ctx->nb, ctx->scal, gated, matvec_queue(ctx->scal));
+  MvArgs<T, 1> a;
+  a.x[0] = (const T2*)xt;
+  a.segpart[0] = (T2*)segp;
+  a.tilepart[0] = (T2*)tilep;
+  launch_mv<T, 1>(ctx, a, gated);
 }
 
 // Launch the matvec on the working-precision copy of a vector.
@@ -469,13 +480,43 @@ cudaError_t launch_data_update(osar_ctx* ctx) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_power_steps(osar_ctx* ctx, int steps) {
+cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
   const unsigned nb = (unsigned)ctx->nb;
   for (int s = 0; s < steps; ++s) {
-    matvec(ctx, ctx->vt, 0);
+    const int last = s == steps - 1 ? 1 : 0;
+    if (last && fuse) {
+      // the burst that follows starts from z = c_hat: apply the Gram to it
+      // in the same pass as the last power step
+      cudaError_t e = launch_burst_begin(ctx);
+      if (e != cudaSuccess) return e;
+      ProfEvent ev;
+      prof_begin(ctx, KCL_MATVEC, &ev);
+      if (ctx->prec == OSAR_FP64) {
+        MvArgs<double, 2> a;
+        a.x[0] = (const double2*)ctx->vt;
+        a.x[1] = (const double2*)ctx->zt;
+        a.segpart[0] = (double2*)ctx->segpart;
+        a.segpart[1] = (double2*)ctx->segpart2;
+        a.tilepart[0] = (double2*)ctx->tilepart;
+        a.tilepart[1] = (double2*)ctx->tilepart2;
+        launch_mv<double, 2>(ctx, a, 0);
+      } else {
+        MvArgs<float, 2> a;
+        a.x[0] = (const float2*)ctx->vt;
+        a.x[1] = (const float2*)ctx->zt;
+        a.segpart[0] = (float2*)ctx->segpart;
+        a.segpart[1] = (float2*)ctx->segpart2;
+        a.tilepart[0] = (float2*)ctx->tilepart;
+        a.tilepart[1] = (float2*)ctx->tilepart2;
+        launch_mv<float, 2>(ctx, a, 0);
+      }
+      prof_end(ctx, &ev);
+      ctx->launches++;
+    } else {
+      matvec(ctx, ctx->vt, 0);
+    }
     ProfEvent ev;
     prof_begin(ctx, KCL_POWFIN, &ev);
-    const int last = s == steps - 1 ? 1 : 0;
     if (ctx->prec == OSAR_FP64) {
       k_power_finalize<double2, double><<<nb, FIN_THREADS, 0, ctx->stream>>>(
           (const double2*)ctx->segpart, (const double2*)ctx->tilepart,
@@ -493,6 +534,10 @@ cudaError_t launch_power_steps(osar_ctx* ctx, int steps) {
     }
     prof_end(ctx, &ev);
     ctx->launches += 2;
+  }
+  if (fuse && steps > 0) {
+    ctx->first_ready = true;
+    ctx->fresh = false;
   }
   return cudaGetLastError();
 }
@@ -516,19 +561,25 @@ cudaError_t launch_iter_begin(osar_ctx* ctx, double tol) {
 }
 
 cudaError_t launch_fista_step(osar_ctx* ctx) {
-  matvec(ctx, ctx->zt, 1);
+  // the first step after a fused push reuses the pass made with the last
+  // power step (already counted as a Gram pass)
+  const bool pre = ctx->first_ready;
+  ctx->first_ready = false;
+  if (!pre) matvec(ctx, ctx->zt, 1);
+  void* segp = pre ? ctx->segpart2 : ctx->segpart;
+  void* tilep = pre ? ctx->tilepart2 : ctx->tilepart;
   ProfEvent ev;
   prof_begin(ctx, KCL_FIN, &ev);
   if (ctx->prec == OSAR_FP64)
     k_fista_finalize<double2, double><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
-        (const double2*)ctx->segpart, (const double2*)ctx->tilepart,
-        ctx->seg_begin, ctx->nb, ctx->b, ctx->c, ctx->z, (double2*)ctx->zt,
-        ctx->part, ctx->scal);
+        (const double2*)segp, (const double2*)tilep, ctx->seg_begin, ctx->nb,
+        ctx->b, ctx->c, ctx->z, (double2*)ctx->zt, ctx->part, ctx->scal,
+        pre ? 0 : 1);
   else
     k_fista_finalize<float2, float><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
-        (const float2*)ctx->segpart, (const float2*)ctx->tilepart,
-        ctx->seg_begin, ctx->nb, ctx->b, ctx->c, ctx->z, (float2*)ctx->zt,
-        ctx->part, ctx->scal);
+        (const float2*)segp, (const float2*)tilep, ctx->seg_begin, ctx->nb,
+        ctx->b, ctx->c, ctx->z, (float2*)ctx->zt, ctx->part, ctx->scal,
+        pre ? 0 : 1);
   prof_end(ctx, &ev);
   ctx->launches++;
   return cudaGetLastError();

@@ -66,16 +66,15 @@ __device__ __forceinline__ void load4_smem(const double2* p, double2 (&g)[4]) {
 }
 
 // Shared-memory pipeline of the matvec.  A stage holds one chunk of CC
-// stored columns of a block (32 KB), the block's x_I (128 entries) and the
-// chunk's x_J entries, all brought in by TMA bulk copies issued by one
-// producer thread; CW consumer warps work on every chunk, WC columns each.
-#ifndef OSAR_MV_WARPS
-#define OSAR_MV_WARPS 8
-#endif
-template <typename T>
+// stored columns of a block (32 KB) and, for each of the R right-hand sides,
+// the block's x_I (128 entries) and the chunk's x_J entries, all brought in
+// by TMA bulk copies issued by one producer thread; CW consumer warps work
+// on every chunk, WC columns each.  R = 2 applies the Gram to two vectors
+// in one pass (the last power step of a pulse and the first FISTA step).
+template <typename T, int R>
 struct Mv {
   using T2 = typename Vec<T>::T2;
-  static constexpr int CW = OSAR_MV_WARPS;                     // consumer warps
+  static constexpr int CW = 8;                                 // consumer warps
   static constexpr int CC = 32768 / (BLK * (int)sizeof(T2));  // 32 f32 / 16 f64
   static constexpr int CHUNKS = BLK / CC;                      // per block
   static constexpr int WC = CC / CW;                           // columns per warp and chunk
@@ -83,8 +82,8 @@ struct Mv {
   static constexpr int G_BYTES = CC * BLK * (int)sizeof(T2);
   static constexpr int XI_BYTES = BLK * (int)sizeof(T2);
   static constexpr int XJ_BYTES = CC * (int)sizeof(T2);
-  static constexpr int STAGE = G_BYTES + XI_BYTES + XJ_BYTES;
-  static constexpr int RED_BYTES = 2 * CW * BLK * (int)sizeof(T2);
+  static constexpr int STAGE = G_BYTES + R * (XI_BYTES + XJ_BYTES);
+  static constexpr int RED_BYTES = 2 * R * CW * BLK * (int)sizeof(T2);
   static constexpr int FIXED = RED_BYTES + 16;
   static constexpr int PER_STAGE = STAGE + 2 * 8 + 16;         // + barriers, meta
   static constexpr int NST = (227 * 1024 - FIXED) / PER_STAGE > 6
@@ -93,35 +92,41 @@ struct Mv {
                               NST * 16 + 16;
   static constexpr int THREADS = 32 * (CW + 1);  // producer warp + consumers
 };
-static_assert(Mv<float>::WC >= 1 && Mv<double>::WC >= 1, "too many consumer warps");
-static_assert(Mv<float>::SMEM <= 227 * 1024 && Mv<double>::SMEM <= 227 * 1024,
+static_assert(Mv<float, 2>::NST >= 4 && Mv<double, 2>::NST >= 4,
+              "matvec ring too shallow");
+static_assert(Mv<float, 2>::SMEM <= 227 * 1024 && Mv<double, 2>::SMEM <= 227 * 1024,
               "matvec ring exceeds shared memory");
+
+// The R right-hand sides of one pass and their partial-sum outputs.
+template <typename T, int R>
+struct MvArgs {
+  const typename Vec<T>::T2* x[R];
+  typename Vec<T>::T2* segpart[R];
+  typename Vec<T>::T2* tilepart[R];
+};
 
 constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
 
 // One Gram pass.  Each thread accumulates y_J over NACC of the block's stored
 // columns (chunk k, warp w: columns k*CC + w*WC + j) for the whole segment
 // and y_I over its 4 rows for one block; the same sums as the definition at
-// the top, in a fixed order, so the result does not depend on the grid or
-// on which CTA takes which segment.  Segments are handed out dynamically
-// (first by block index, then from an atomic ticket), so the kernel spreads
-// over whatever SMs are free, e.g. beside the next pulse's dictionary
-// product.  Every wait is bounded; on a timeout the CTA records the error,
-// stops at the next per-block barrier and drains its copies in flight.
-template <typename T>
-__global__ void __launch_bounds__(Mv<T>::THREADS, 1)
-    k_matvec(const typename Vec<T>::T2* __restrict__ G,
-             const typename Vec<T>::T2* __restrict__ x,
-             typename Vec<T>::T2* __restrict__ segpart,
-             typename Vec<T>::T2* __restrict__ tilepart,
+// the top, in a fixed order, so the result does not depend on the grid, on
+// which CTA takes which segment, or on R.  Segments are handed out
+// dynamically (first by block index, then from an atomic ticket), so the
+// kernel spreads over whatever SMs are free, e.g. beside the next pulse's
+// dictionary product.  Every wait is bounded; on a timeout the CTA records
+// the error, stops at the next per-block barrier and drains its copies.
+template <typename T, int R>
+__global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
+    k_matvec(const typename Vec<T>::T2* __restrict__ G, const MvArgs<T, R> a,
              const int4* __restrict__ segs, int nseg, int nb,
              DevScalars* __restrict__ sc, int gated,
              unsigned* __restrict__ queue) {
-  using C = Mv<T>;
+  using C = Mv<T, R>;
   using T2 = typename Vec<T>::T2;
   if (gated && sc->converged) return;
   extern __shared__ __align__(128) uint8_t mv_smem[];
-  T2* red = reinterpret_cast<T2*>(mv_smem + C::NST * C::STAGE);  // [2][CW][BLK]
+  T2* red = reinterpret_cast<T2*>(mv_smem + C::NST * C::STAGE);  // [2][R][CW][BLK]
   uint64_t* full = reinterpret_cast<uint64_t*>(mv_smem + C::NST * C::STAGE +
                                                C::RED_BYTES);
   uint64_t* empty = full + C::NST;
@@ -167,9 +172,14 @@ __global__ void __launch_bounds__(Mv<T>::THREADS, 1)
           mbar_expect_tx(&full[stage], C::STAGE);
           bulk_load_hint(st, blk + (int64_t)k * C::CC * BLK, C::G_BYTES,
                          &full[stage], stream_policy);
-          bulk_load(st + C::G_BYTES, x + (int64_t)I * BLK, C::XI_BYTES, &full[stage]);
-          bulk_load(st + C::G_BYTES + C::XI_BYTES,
-                    x + (int64_t)sg.x * BLK + k * C::CC, C::XJ_BYTES, &full[stage]);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            bulk_load(st + C::G_BYTES + r * C::XI_BYTES, a.x[r] + (int64_t)I * BLK,
+                      C::XI_BYTES, &full[stage]);
+            bulk_load(st + C::G_BYTES + R * C::XI_BYTES + r * C::XJ_BYTES,
+                      a.x[r] + (int64_t)sg.x * BLK + k * C::CC, C::XJ_BYTES,
+                      &full[stage]);
+          }
           issued[stage]++;
           if (++stage == C::NST) {
             stage = 0;
@@ -209,9 +219,11 @@ __global__ void __launch_bounds__(Mv<T>::THREADS, 1)
   const int cw = warp - 1;
   int stage = 0, rp = 0;
   uint32_t ph = 0;
-  T br[C::NACC], bi[C::NACC];
+  T br[R][C::NACC], bi[R][C::NACC];
 #pragma unroll
-  for (int c = 0; c < C::NACC; ++c) br[c] = bi[c] = T(0);
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < C::NACC; ++c) br[r][c] = bi[r][c] = T(0);
   for (;;) {
     bool ok = !*abort_flag && mbar_wait_bounded(&full[stage], ph, abort_flag,
                                                 &sc->error, MV_WAIT_LIMIT_NS);
@@ -221,16 +233,23 @@ __global__ void __launch_bounds__(Mv<T>::THREADS, 1)
       const int I = m.x, J = m.y;
       if (m.w & 1) {
 #pragma unroll
-        for (int c = 0; c < C::NACC; ++c) br[c] = bi[c] = T(0);
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int c = 0; c < C::NACC; ++c) br[r][c] = bi[r][c] = T(0);
       }
-      const T2* xis = reinterpret_cast<const T2*>(mv_smem + stage * C::STAGE +
-                                                  C::G_BYTES);
-      T2 xi[4];
+      T2 xi[R][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) xi[q] = xis[lane * 4 + q];
-      T ar[4], ai[4];
+      for (int r = 0; r < R; ++r) {
+        const T2* xis = reinterpret_cast<const T2*>(
+            mv_smem + stage * C::STAGE + C::G_BYTES + r * C::XI_BYTES);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) ar[q] = ai[q] = T(0);
+        for (int q = 0; q < 4; ++q) xi[r][q] = xis[lane * 4 + q];
+      }
+      T ar[R][4], ai[R][4];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ar[r][q] = ai[r][q] = T(0);
 #pragma unroll
       for (int k = 0; k < C::CHUNKS; ++k) {
         if (k > 0 && ok)
@@ -239,27 +258,30 @@ __global__ void __launch_bounds__(Mv<T>::THREADS, 1)
         if (ok) {
           const uint8_t* st = mv_smem + stage * C::STAGE;
           const T2* gs = reinterpret_cast<const T2*>(st);
-          const T2* xjs = reinterpret_cast<const T2*>(st + C::G_BYTES + C::XI_BYTES);
 #pragma unroll
           for (int j = 0; j < C::WC; ++j) {
             const int col = cw * C::WC + j;
-            const T2 xj = xjs[col];
             T2 g[4];
             load4_smem(gs + col * BLK + lane * 4, g);
-            const int a = k * C::WC + j;
+            const int aa = k * C::WC + j;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const T2 e = g[q];
-              // y_J[c] += conj(e) x_I[r]
-              br[a] = fma(e.x, xi[q].x, br[a]);
-              br[a] = fma(e.y, xi[q].y, br[a]);
-              bi[a] = fma(e.x, xi[q].y, bi[a]);
-              bi[a] = fma(-e.y, xi[q].x, bi[a]);
-              // y_I[r] += e x_J[c]
-              ar[q] = fma(e.x, xj.x, ar[q]);
-              ar[q] = fma(-e.y, xj.y, ar[q]);
-              ai[q] = fma(e.x, xj.y, ai[q]);
-              ai[q] = fma(e.y, xj.x, ai[q]);
+            for (int r = 0; r < R; ++r) {
+              const T2 xj = reinterpret_cast<const T2*>(
+                  st + C::G_BYTES + R * C::XI_BYTES + r * C::XJ_BYTES)[col];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const T2 e = g[q];
+                // y_J[c] += conj(e) x_I[r]
+                br[r][aa] = fma(e.x, xi[r][q].x, br[r][aa]);
+                br[r][aa] = fma(e.y, xi[r][q].y, br[r][aa]);
+                bi[r][aa] = fma(e.x, xi[r][q].y, bi[r][aa]);
+                bi[r][aa] = fma(-e.y, xi[r][q].x, bi[r][aa]);
+                // y_I[r] += e x_J[c]
+                ar[r][q] = fma(e.x, xj.x, ar[r][q]);
+                ar[r][q] = fma(-e.y, xj.y, ar[r][q]);
+                ai[r][q] = fma(e.x, xj.y, ai[r][q]);
+                ai[r][q] = fma(e.y, xj.x, ai[r][q]);
+              }
             }
           }
           __syncwarp();
@@ -272,31 +294,35 @@ __global__ void __launch_bounds__(Mv<T>::THREADS, 1)
       }
       if (ok && I != J) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          T2 v;
-          v.x = ar[q];
-          v.y = ai[q];
-          red[(rp * C::CW + cw) * BLK + lane * 4 + q] = v;
-        }
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            T2 v;
+            v.x = ar[r][q];
+            v.y = ai[r][q];
+            red[((rp * R + r) * C::CW + cw) * BLK + lane * 4 + q] = v;
+          }
       }
       if (ok && (m.w & 2)) {
         // segment done: y_J over all rows of its blocks, one lane per column
 #pragma unroll
-        for (int a = 0; a < C::NACC; ++a) {
-          T vr = br[a], vi = bi[a];
+        for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            vr += __shfl_xor_sync(0xffffffffu, vr, o);
-            vi += __shfl_xor_sync(0xffffffffu, vi, o);
+          for (int aa = 0; aa < C::NACC; ++aa) {
+            T vr = br[r][aa], vi = bi[r][aa];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              vr += __shfl_xor_sync(0xffffffffu, vr, o);
+              vi += __shfl_xor_sync(0xffffffffu, vi, o);
+            }
+            if (lane == aa) {
+              T2 v;
+              v.x = vr;
+              v.y = vi;
+              const int col = (aa / C::WC) * C::CC + cw * C::WC + (aa % C::WC);
+              a.segpart[r][(int64_t)m.z * BLK + col] = v;
+            }
           }
-          if (lane == a) {
-            T2 v;
-            v.x = vr;
-            v.y = vi;
-            const int col = (a / C::WC) * C::CC + cw * C::WC + (a % C::WC);
-            segpart[(int64_t)m.z * BLK + col] = v;
-          }
-        }
       }
     }
     // Per-block barrier of the consumer warps: the block partial is summed
@@ -304,18 +330,19 @@ __global__ void __launch_bounds__(Mv<T>::THREADS, 1)
     // at once (end of work or an abort raised before the barrier).
     named_barrier(1, 32 * C::CW);
     if (!work || *abort_flag) break;
-    const int r = (int)threadIdx.x - 32;
-    if (m.x != m.y && r < BLK) {
+    const int rr = (int)threadIdx.x - 32;
+    if (m.x != m.y && rr < R * BLK) {
+      const int r = rr / BLK, row = rr % BLK;
       T sr = 0, si = 0;
 #pragma unroll
       for (int w = 0; w < C::CW; ++w) {
-        sr += red[(rp * C::CW + w) * BLK + r].x;
-        si += red[(rp * C::CW + w) * BLK + r].y;
+        sr += red[((rp * R + r) * C::CW + w) * BLK + row].x;
+        si += red[((rp * R + r) * C::CW + w) * BLK + row].y;
       }
       T2 v;
       v.x = sr;
       v.y = si;
-      tilepart[packed_block(m.x, m.y, nb) * BLK + r] = v;
+      a.tilepart[r][packed_block(m.x, m.y, nb) * BLK + row] = v;
     }
     rp ^= 1;
   }

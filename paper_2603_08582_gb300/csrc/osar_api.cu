@@ -67,7 +67,7 @@ void free_all(osar_ctx* ctx) {
                   ctx->gram_tiles, ctx->dict_tiles, ctx->A, ctx->F, ctx->D,
                   ctx->Apl, ctx->Fpl, ctx->Dpl, ctx->sim_rho, ctx->sim_nz,
                   ctx->sim_idx, ctx->sim_d, ctx->dict_part, ctx->gram_pairs,
-                  ctx->dict_pairs};
+                  ctx->dict_pairs, ctx->segpart2, ctx->tilepart2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
@@ -130,6 +130,8 @@ osar_status validate(const osar_config* c, std::string* why) {
   if (c->synth_ctas < 0) return *why = "synth_ctas must be >= 0", OSAR_E_INVALID;
   if (c->tc_pairs < 0 || c->tc_pairs > 3)
     return *why = "tc_pairs must be in [0, 3]", OSAR_E_INVALID;
+  if (c->fuse_first_step != 0 && c->fuse_first_step != 1)
+    return *why = "fuse_first_step must be 0 or 1", OSAR_E_INVALID;
   return OSAR_OK;
 }
 
@@ -263,6 +265,10 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     AL(ctx->g_lo, 4 * bb * ctx->nblk);
   AL(ctx->segpart, cplx * BLK * (int64_t)ctx->nseg);
   AL(ctx->tilepart, cplx * BLK * ctx->nblk);
+  if (cfg->fuse_first_step) {
+    AL(ctx->segpart2, cplx * BLK * (int64_t)ctx->nseg);
+    AL(ctx->tilepart2, cplx * BLK * ctx->nblk);
+  }
   AL(ctx->zt, cplx * Mp);
   AL(ctx->vt, cplx * Mp);
   AL(ctx->xt, cplx * Mp);
@@ -499,11 +505,14 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
   if (e == cudaSuccess && ctx->side && !ctx->free_stale)
     e = cudaEventRecord(ctx->ev_free, ctx->stream);
   ctx->n += 1;
-  if (e == cudaSuccess)
-    e = launch_power_steps(ctx, ctx->n == 1 ? ctx->cfg.power_iters_first
-                                            : ctx->cfg.power_iters);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_push_pulse");
   ctx->fresh = true;
+  ctx->first_ready = false;
+  if (e == cudaSuccess)
+    e = launch_power_steps(ctx,
+                           ctx->n == 1 ? ctx->cfg.power_iters_first
+                                       : ctx->cfg.power_iters,
+                           ctx->cfg.fuse_first_step != 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_push_pulse");
   return OSAR_OK;
 }
 
@@ -563,6 +572,7 @@ void osar_config_default(osar_config* c) {
   c->overlap_synthesis = 1;
   c->synth_ctas = 0;
   c->tc_pairs = 3;
+  c->fuse_first_step = 1;
 }
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {

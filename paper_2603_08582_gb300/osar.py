@@ -62,7 +62,7 @@ class OsarConfig(C.Structure):
         ("restart_momentum", C.c_int32), ("compensated", C.c_int32),
         ("cuda_stream", C.c_void_p),
         ("overlap_synthesis", C.c_int32), ("synth_ctas", C.c_int32),
-        ("tc_pairs", C.c_int32),
+        ("tc_pairs", C.c_int32), ("fuse_first_step", C.c_int32),
     ]
 
 
@@ -159,7 +159,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
                 lam=0.05, lambda_relative=True, power_iters_first=30,
                 power_iters=4, lipschitz_margin=0.01, restart_momentum=False,
                 compensated=True, stream=None, overlap_synthesis=True,
-                synth_ctas=0, tc_pairs=3):
+                synth_ctas=0, tc_pairs=3, fuse_first_step=True):
     """Build an osar_config.  dictionary: None (identity), "gaussian"
     (seeded Philox atoms, needs n_atoms) or an N x M complex array."""
     cfg = default_config()
@@ -190,6 +190,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
     cfg.overlap_synthesis = 1 if overlap_synthesis else 0
     cfg.synth_ctas = int(synth_ctas)
     cfg.tc_pairs = int(tc_pairs)  # bit 0 dictionary product, bit 1 Gram update
+    cfg.fuse_first_step = 1 if fuse_first_step else 0
     cfg._keepalive = keep
     return cfg
 
