@@ -176,7 +176,8 @@ void prof_end(osar_ctx* ctx, ProfEvent* ev);
 
 // ---- k_phase.cu -------------------------------------------------------------
 cudaError_t launch_pixel_turns(osar_ctx* ctx, const double gamma[3]);
-cudaError_t launch_phase(osar_ctx* ctx);
+// grid_cap > 0: grid-stride over at most 4 x grid_cap CTAs (split-BF16)
+cudaError_t launch_phase(osar_ctx* ctx, int grid_cap);
 cudaError_t launch_dictionary_build(osar_ctx* ctx, const double* host_dict);
 cudaError_t launch_simulate(osar_ctx* ctx, int nnz, double2* d_out);
 

@@ -580,34 +580,36 @@ __global__ void k_dict_reduce(const float2* __restrict__ part, int slices,
                               int64_t slice_stride, int64_t groups,
                               __nv_bfloat16* __restrict__ planes,
                               int64_t plane) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= groups) return;
-  const int64_t off = g * 8;
-  float re[8], im[8];
+  // grid-stride: a capped grid leaves SMs to the burst running beside it
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t off = g * 8;
+    float re[8], im[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) re[q] = im[q] = 0.f;
-  for (int s = 0; s < slices; ++s) {
-    const float4* src = reinterpret_cast<const float4*>(part + s * slice_stride + off);
+    for (int q = 0; q < 8; ++q) re[q] = im[q] = 0.f;
+    for (int s = 0; s < slices; ++s) {
+      const float4* src = reinterpret_cast<const float4*>(part + s * slice_stride + off);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const float4 v = __ldcs(src + c);
-      re[2 * c] += v.x;
-      im[2 * c] += v.y;
-      re[2 * c + 1] += v.z;
-      im[2 * c + 1] += v.w;
+      for (int c = 0; c < 4; ++c) {
+        const float4 v = __ldcs(src + c);
+        re[2 * c] += v.x;
+        im[2 * c] += v.y;
+        re[2 * c + 1] += v.z;
+        im[2 * c + 1] += v.w;
+      }
     }
-  }
-  __align__(16) __nv_bfloat16 v[6][8];
+    __align__(16) __nv_bfloat16 v[6][8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    split_bf16(re[q], v[0][q], v[3][q]);
-    split_bf16(im[q], v[1][q], v[4][q]);
-    split_bf16(-re[q], v[2][q], v[5][q]);
-  }
+    for (int q = 0; q < 8; ++q) {
+      split_bf16(re[q], v[0][q], v[3][q]);
+      split_bf16(im[q], v[1][q], v[4][q]);
+      split_bf16(-re[q], v[2][q], v[5][q]);
+    }
 #pragma unroll
-  for (int pl = 0; pl < 6; ++pl)
-    *reinterpret_cast<uint4*>(planes + pl * plane + off) =
-        *reinterpret_cast<const uint4*>(v[pl]);
+    for (int pl = 0; pl < 6; ++pl)
+      *reinterpret_cast<uint4*>(planes + pl * plane + off) =
+          *reinterpret_cast<const uint4*>(v[pl]);
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -770,9 +772,11 @@ cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap) {
                             KCL_DICT, pairs, grid_cap);
   if (e != cudaSuccess) return e;
   const int64_t groups = (int64_t)ctx->Mp * ctx->Kp / 8;
+  int64_t rg = (groups + 255) / 256;
+  if (grid_cap > 0 && rg > 4 * grid_cap) rg = 4 * grid_cap;  // beside a burst
   ProfEvent ev;
   prof_begin(ctx, KCL_DICT, &ev);
-  k_dict_reduce<<<(unsigned)((groups + 255) / 256), 256, 0, ctx->stream>>>(
+  k_dict_reduce<<<(unsigned)rg, 256, 0, ctx->stream>>>(
       ctx->dict_part, ctx->dict_slices, p.part_slice, groups, ctx->Apl,
       p.part_slice);
   prof_end(ctx, &ev);

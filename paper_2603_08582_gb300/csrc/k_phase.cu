@@ -122,32 +122,34 @@ __global__ void k_phase_planes(const ulonglong2* __restrict__ turns, int N,
                                int K, int rows, int ld,
                                __nv_bfloat16* __restrict__ planes) {
   const int groups = ld / 8;
-  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (int64_t)rows * groups) return;
-  int row = (int)(gid / groups);
-  int col0 = (int)(gid - (int64_t)row * groups) * 8;
   const int64_t plane = (int64_t)rows * ld;
-  __align__(16) __nv_bfloat16 v[6][8];
-  ulonglong2 tp_row = make_ulonglong2(0, 0);
-  if (PIXEL_MAJOR && row < N) tp_row = turns[row];
+  // grid-stride: a capped grid leaves SMs to the burst running beside it
+  for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+       gid < (int64_t)rows * groups; gid += (int64_t)gridDim.x * blockDim.x) {
+    int row = (int)(gid / groups);
+    int col0 = (int)(gid - (int64_t)row * groups) * 8;
+    __align__(16) __nv_bfloat16 v[6][8];
+    ulonglong2 tp_row = make_ulonglong2(0, 0);
+    if (PIXEL_MAJOR && row < N) tp_row = turns[row];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    int p = PIXEL_MAJOR ? row : col0 + q;
-    int m = PIXEL_MAJOR ? col0 + q : row;
-    float2 e = make_float2(0.f, 0.f);
-    if (p < N && m < K) {
-      ulonglong2 tp = PIXEL_MAJOR ? tp_row : turns[p];
-      e = unit_phase_f32(tp.x + (uint64_t)m * tp.y);
+    for (int q = 0; q < 8; ++q) {
+      int p = PIXEL_MAJOR ? row : col0 + q;
+      int m = PIXEL_MAJOR ? col0 + q : row;
+      float2 e = make_float2(0.f, 0.f);
+      if (p < N && m < K) {
+        ulonglong2 tp = PIXEL_MAJOR ? tp_row : turns[p];
+        e = unit_phase_f32(tp.x + (uint64_t)m * tp.y);
+      }
+      split_bf16(e.x, v[0][q], v[3][q]);
+      split_bf16(e.y, v[1][q], v[4][q]);
+      split_bf16(-e.x, v[2][q], v[5][q]);
     }
-    split_bf16(e.x, v[0][q], v[3][q]);
-    split_bf16(e.y, v[1][q], v[4][q]);
-    split_bf16(-e.x, v[2][q], v[5][q]);
-  }
-  const int64_t off = (int64_t)row * ld + col0;
+    const int64_t off = (int64_t)row * ld + col0;
 #pragma unroll
-  for (int pl = 0; pl < 6; ++pl)
-    *reinterpret_cast<uint4*>(planes + pl * plane + off) =
-        *reinterpret_cast<const uint4*>(v[pl]);
+    for (int pl = 0; pl < 6; ++pl)
+      *reinterpret_cast<uint4*>(planes + pl * plane + off) =
+          *reinterpret_cast<const uint4*>(v[pl]);
+  }
 }
 
 // ---------------------------------------------------------------- dictionary
@@ -342,14 +344,18 @@ cudaError_t launch_pixel_turns(osar_ctx* ctx, const double gamma[3]) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_phase(osar_ctx* ctx) {
+cudaError_t launch_phase(osar_ctx* ctx, int grid_cap) {
   ProfEvent ev;
   prof_begin(ctx, KCL_PHASE, &ev);
   const bool pix = !ctx->dict;
   const int rows = pix ? ctx->Mp : ctx->Kp;
   const int ld = pix ? ctx->Kp : ctx->Np;
   const int64_t work = (int64_t)rows * (ld / 8);
-  const unsigned g = blocks_for(work, 256);
+  unsigned g = blocks_for(work, 256);
+  // beside a burst: at most 4 CTAs per SM the side work was given (the
+  // split-BF16 kernel strides over its rows)
+  if (grid_cap > 0 && ctx->prec == OSAR_SPLIT_BF16 && g > (unsigned)(4 * grid_cap))
+    g = (unsigned)(4 * grid_cap);
   if (ctx->prec == OSAR_SPLIT_BF16) {
     __nv_bfloat16* out = pix ? ctx->Apl : ctx->Fpl;
     if (pix)

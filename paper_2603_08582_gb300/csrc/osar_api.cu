@@ -400,7 +400,7 @@ bool capturing(cudaStream_t s) {
 // phase terms, phase matrix, then A_s = F_s D for dictionary models.
 cudaError_t synthesize(osar_ctx* ctx, const double gamma[3], int grid_cap) {
   cudaError_t e = launch_pixel_turns(ctx, gamma);
-  if (e == cudaSuccess) e = launch_phase(ctx);
+  if (e == cudaSuccess) e = launch_phase(ctx, grid_cap);
   if (e == cudaSuccess && ctx->dict)
     e = ctx->prec == OSAR_SPLIT_BF16 ? launch_dict_tc(ctx, grid_cap)
                                      : launch_dict_simt(ctx);
