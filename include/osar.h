@@ -128,7 +128,9 @@ typedef struct {
   /* 1: the last power step of a push also applies the Gram to the next
      burst's first iterate z = c_hat (both vectors in one pass over the
      Gram), and that burst's first FISTA step uses the result; one Gram
-     pass fewer per pulse, bitwise the same results.  0: separate passes. */
+     pass fewer per pulse, bitwise the same results.  0: separate passes.
+     (FP32 and split-BF16 matvecs; the FP64 path always uses separate
+     passes.) */
   int32_t fuse_first_step;
 } osar_config;
 

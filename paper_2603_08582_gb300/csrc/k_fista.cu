@@ -482,6 +482,9 @@ cudaError_t launch_data_update(osar_ctx* ctx) {
 
 cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
   const unsigned nb = (unsigned)ctx->nb;
+  // the FP64 path keeps separate passes: two FP64 vectors' partial sums do
+  // not fit the matvec's registers
+  fuse = fuse && ctx->prec != OSAR_FP64;
   for (int s = 0; s < steps; ++s) {
     const int last = s == steps - 1 ? 1 : 0;
     if (last && fuse) {
@@ -491,25 +494,14 @@ cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
       if (e != cudaSuccess) return e;
       ProfEvent ev;
       prof_begin(ctx, KCL_MATVEC, &ev);
-      if (ctx->prec == OSAR_FP64) {
-        MvArgs<double, 2> a;
-        a.x[0] = (const double2*)ctx->vt;
-        a.x[1] = (const double2*)ctx->zt;
-        a.segpart[0] = (double2*)ctx->segpart;
-        a.segpart[1] = (double2*)ctx->segpart2;
-        a.tilepart[0] = (double2*)ctx->tilepart;
-        a.tilepart[1] = (double2*)ctx->tilepart2;
-        launch_mv<double, 2>(ctx, a, 0);
-      } else {
-        MvArgs<float, 2> a;
-        a.x[0] = (const float2*)ctx->vt;
-        a.x[1] = (const float2*)ctx->zt;
-        a.segpart[0] = (float2*)ctx->segpart;
-        a.segpart[1] = (float2*)ctx->segpart2;
-        a.tilepart[0] = (float2*)ctx->tilepart;
-        a.tilepart[1] = (float2*)ctx->tilepart2;
-        launch_mv<float, 2>(ctx, a, 0);
-      }
+      MvArgs<float, 2> a;
+      a.x[0] = (const float2*)ctx->vt;
+      a.x[1] = (const float2*)ctx->zt;
+      a.segpart[0] = (float2*)ctx->segpart;
+      a.segpart[1] = (float2*)ctx->segpart2;
+      a.tilepart[0] = (float2*)ctx->tilepart;
+      a.tilepart[1] = (float2*)ctx->tilepart2;
+      launch_mv<float, 2>(ctx, a, 0);
       prof_end(ctx, &ev);
       ctx->launches++;
     } else {

@@ -65,6 +65,16 @@ __device__ __forceinline__ void load4_smem(const double2* p, double2 (&g)[4]) {
   for (int c = 0; c < 4; ++c) g[c] = p[c];
 }
 
+// acc += a * b on both components, with the rounding of two scalar FMAs:
+// one packed FP32x2 FMA (FFMA2) on sm_100 and later, two FP64 FMAs.
+__device__ __forceinline__ void mac2(float2& acc, float a, float2 b) {
+  acc = __ffma2_rn(make_float2(a, a), b, acc);
+}
+__device__ __forceinline__ void mac2(double2& acc, double a, double2 b) {
+  acc.x = fma(a, b.x, acc.x);
+  acc.y = fma(a, b.y, acc.y);
+}
+
 // Shared-memory pipeline of the matvec.  A stage holds one chunk of CC
 // stored columns of a block (32 KB) and, for each of the R right-hand sides,
 // the block's x_I (128 entries) and the chunk's x_J entries, all brought in
@@ -92,9 +102,9 @@ struct Mv {
                               NST * 16 + 16;
   static constexpr int THREADS = 32 * (CW + 1);  // producer warp + consumers
 };
-static_assert(Mv<float, 2>::NST >= 4 && Mv<double, 2>::NST >= 4,
+static_assert(Mv<float, 2>::NST >= 4 && Mv<double, 1>::NST >= 4,
               "matvec ring too shallow");
-static_assert(Mv<float, 2>::SMEM <= 227 * 1024 && Mv<double, 2>::SMEM <= 227 * 1024,
+static_assert(Mv<float, 2>::SMEM <= 227 * 1024 && Mv<double, 1>::SMEM <= 227 * 1024,
               "matvec ring exceeds shared memory");
 
 // The R right-hand sides of one pass and their partial-sum outputs.
@@ -219,11 +229,11 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
   const int cw = warp - 1;
   int stage = 0, rp = 0;
   uint32_t ph = 0;
-  T br[R][C::NACC], bi[R][C::NACC];
+  T2 yj[R][C::NACC];  // y_J partials (re, im) of this thread's columns
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int c = 0; c < C::NACC; ++c) br[r][c] = bi[r][c] = T(0);
+    for (int c = 0; c < C::NACC; ++c) yj[r][c].x = yj[r][c].y = T(0);
   for (;;) {
     bool ok = !*abort_flag && mbar_wait_bounded(&full[stage], ph, abort_flag,
                                                 &sc->error, MV_WAIT_LIMIT_NS);
@@ -235,21 +245,26 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int c = 0; c < C::NACC; ++c) br[r][c] = bi[r][c] = T(0);
+          for (int c = 0; c < C::NACC; ++c) yj[r][c].x = yj[r][c].y = T(0);
       }
-      T2 xi[R][4];
+      // x_I of this lane's 4 rows as (re, im) and (im, -re)
+      T2 xa[R][4], xb[R][4];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const T2* xis = reinterpret_cast<const T2*>(
             mv_smem + stage * C::STAGE + C::G_BYTES + r * C::XI_BYTES);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) xi[r][q] = xis[lane * 4 + q];
+        for (int q = 0; q < 4; ++q) {
+          xa[r][q] = xis[lane * 4 + q];
+          xb[r][q].x = xa[r][q].y;
+          xb[r][q].y = -xa[r][q].x;
+        }
       }
-      T ar[R][4], ai[R][4];
+      T2 yi[R][4];  // y_I partials of this lane's 4 rows
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ar[r][q] = ai[r][q] = T(0);
+        for (int q = 0; q < 4; ++q) yi[r][q].x = yi[r][q].y = T(0);
 #pragma unroll
       for (int k = 0; k < C::CHUNKS; ++k) {
         if (k > 0 && ok)
@@ -266,21 +281,20 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
             const int aa = k * C::WC + j;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-              const T2 xj = reinterpret_cast<const T2*>(
+              const T2 ja = reinterpret_cast<const T2*>(
                   st + C::G_BYTES + R * C::XI_BYTES + r * C::XJ_BYTES)[col];
+              T2 jb;  // (-im, re) of x_J[c]
+              jb.x = -ja.y;
+              jb.y = ja.x;
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
                 const T2 e = g[q];
-                // y_J[c] += conj(e) x_I[r]
-                br[r][aa] = fma(e.x, xi[r][q].x, br[r][aa]);
-                br[r][aa] = fma(e.y, xi[r][q].y, br[r][aa]);
-                bi[r][aa] = fma(e.x, xi[r][q].y, bi[r][aa]);
-                bi[r][aa] = fma(-e.y, xi[r][q].x, bi[r][aa]);
-                // y_I[r] += e x_J[c]
-                ar[r][q] = fma(e.x, xj.x, ar[r][q]);
-                ar[r][q] = fma(-e.y, xj.y, ar[r][q]);
-                ai[r][q] = fma(e.x, xj.y, ai[r][q]);
-                ai[r][q] = fma(e.y, xj.x, ai[r][q]);
+                // y_J[c] += conj(e) x_I[r] = e.re (x.re, x.im) + e.im (x.im, -x.re)
+                mac2(yj[r][aa], e.x, xa[r][q]);
+                mac2(yj[r][aa], e.y, xb[r][q]);
+                // y_I[r] += e x_J[c] = e.re (x.re, x.im) + e.im (-x.im, x.re)
+                mac2(yi[r][q], e.x, ja);
+                mac2(yi[r][q], e.y, jb);
               }
             }
           }
@@ -296,12 +310,8 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            T2 v;
-            v.x = ar[r][q];
-            v.y = ai[r][q];
-            red[((rp * R + r) * C::CW + cw) * BLK + lane * 4 + q] = v;
-          }
+          for (int q = 0; q < 4; ++q)
+            red[((rp * R + r) * C::CW + cw) * BLK + lane * 4 + q] = yi[r][q];
       }
       if (ok && (m.w & 2)) {
         // segment done: y_J over all rows of its blocks, one lane per column
@@ -309,7 +319,7 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
         for (int r = 0; r < R; ++r)
 #pragma unroll
           for (int aa = 0; aa < C::NACC; ++aa) {
-            T vr = br[r][aa], vi = bi[r][aa];
+            T vr = yj[r][aa].x, vi = yj[r][aa].y;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
               vr += __shfl_xor_sync(0xffffffffu, vr, o);
