@@ -416,9 +416,14 @@ __global__ void __launch_bounds__(FIN_THREADS)
 
 // One matvec launch over R vectors: one CTA per SM (the shared-memory ring
 // fills an SM), at most one per segment.
+// Packed Grams up to this size stay in L2 (129 MB on GB300) across passes.
+constexpr int64_t KEEP_L2_BYTES = 80ll << 20;
+
 template <typename T, int R>
-void launch_mv(osar_ctx* ctx, const MvArgs<T, R>& a, int gated) {
+void launch_mv(osar_ctx* ctx, MvArgs<T, R> a, int gated) {
   using C = Mv<T, R>;
+  a.keep_l2 = ctx->nblk * BLK * BLK * (int64_t)sizeof(typename Vec<T>::T2) <=
+              KEEP_L2_BYTES;
   cudaFuncSetAttribute(k_matvec<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        C::SMEM);
   const unsigned grid =

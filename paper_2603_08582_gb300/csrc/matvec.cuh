@@ -113,6 +113,7 @@ struct MvArgs {
   const typename Vec<T>::T2* x[R];
   typename Vec<T>::T2* segpart[R];
   typename Vec<T>::T2* tilepart[R];
+  int keep_l2;  // the Gram fits in L2: keep it there between passes
 };
 
 constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
@@ -156,7 +157,10 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
   if (warp == 0) {
     if (lane != 0) return;
     // ------------------------------------------------------------ producer
-    const uint64_t stream_policy = l2_policy_evict_first();
+    // a Gram larger than L2 streams through it once per pass; a small one
+    // stays resident for the next pass
+    const uint64_t stream_policy =
+        a.keep_l2 ? l2_policy_evict_last() : l2_policy_evict_first();
     uint32_t issued[C::NST];
     for (int i = 0; i < C::NST; ++i) issued[i] = 0;
     int stage = 0;
