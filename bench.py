@@ -601,6 +601,35 @@ def run_forms(stream):
                                         "pulses_per_s": round(4 / (ms / 1e3), 2),
                                         "device_gb": round(ctx.device_bytes() / 1e9, 1)}
         ctx.close()
+        # lambda path on the 128 x 128 workload: 4 lambdas on one Gram (each
+        # pass serves two solutions) against one lambda, 20 steps per pulse
+        w = wl["c2_128x128_split_bf16"]
+        lams = [0.02, 0.05, 0.08, 0.12]
+        res = {}
+        for n in (1, len(lams)):
+            cfg = osar.make_config(
+                w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz, pixel_m=w.pixel_m,
+                precision="split_bf16", dictionary="gaussian", n_atoms=w.m_atoms,
+                dict_seed=w.dict_seed, lam=lams[0], stream=stream.cuda_stream,
+                lambdas=lams[:n])
+            ctx = osar.Osar(cfg)
+            track, data, _ = _sim_pulses(ctx, w, 7)
+            for s in range(3):
+                ctx.push_pulse(track[s], data[s])
+                ctx.iterate(INNER_STEPS, 0.0, want_count=False)
+
+            def runp(c=ctx, tr=track, dd=data):
+                for s in range(3, 7):
+                    c.push_pulse(tr[s], dd[s])
+                    c.iterate(INNER_STEPS, 0.0, want_count=False)
+            res[n] = _time(runp, stream) / 4
+            ctx.close()
+        out["c2_lambda_path"] = {
+            "lambdas": len(lams), "pulses": 4, "steps": INNER_STEPS,
+            "ms_per_pulse": round(res[len(lams)], 2),
+            "ms_per_pulse_one_lambda": round(res[1], 2),
+            "solution_pulses_per_s": round(len(lams) / (res[len(lams)] / 1e3), 1),
+            "speedup_vs_separate": round(len(lams) * res[1] / res[len(lams)], 2)}
     return out
 
 

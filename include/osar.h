@@ -132,13 +132,24 @@ typedef struct {
      (FP32 and split-BF16 matvecs; the FP64 path always uses separate
      passes.) */
   int32_t fuse_first_step;
+  /* lambda path: 1..8 solutions of the same pulses that differ only in
+     lambda.  n_lambdas > 1 takes lambda_list[l] (relative or absolute per
+     lambda_relative) for solution l and ignores `lambda`; the Gram, b, L_n
+     and the power iteration are shared, and each Gram pass applies the Gram
+     to two solutions' iterates at once.  Solution l is bitwise the one a
+     context with lambda = lambda_list[l] computes.  osar_get_coeffs and
+     osar_get_state report solution 0; osar_get_lambda_state any.  The list
+     is copied at create. */
+  int32_t n_lambdas;
+  const double* lambda_list;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
    9.9-10.1 GHz, identity dictionary, FP64, lambda = 0.05 relative,
    30 / 4 power steps, margin 0.01, carried momentum, compensated = 1,
    overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
-   (both tensor-core products on SM pairs), fuse_first_step = 1. */
+   (both tensor-core products on SM pairs), fuse_first_step = 1,
+   n_lambdas = 1. */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128
@@ -197,6 +208,14 @@ osar_status osar_get_coeffs_async(osar_ctx* ctx, double* out_c128,
    at once when none was queued).  Errors: OSAR_E_INVALID (slot out of
    range), OSAR_E_TIMEOUT (a bounded device wait gave up). */
 osar_status osar_wait_coeffs(osar_ctx* ctx, int32_t slot);
+
+/* Solution l of a lambda path (0 <= l < n_lambdas): c_hat (M complex, may
+   be NULL), lambda_n, momentum t and the FISTA steps of the last
+   osar_iterate call (may be NULL); synchronises.  No paper counterpart:
+   the path shares one Gram (Eqs. 12-13) between several lambdas.
+   Errors: OSAR_E_INVALID (l out of range). */
+osar_status osar_get_lambda_state(osar_ctx* ctx, int32_t l, double* out_c128,
+                                  double* lambda, double* t, int32_t* iters);
 
 /* Pulse count n, L_n, lambda_n, momentum t; synchronises.  Any pointer may
    be NULL. */

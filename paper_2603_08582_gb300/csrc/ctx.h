@@ -18,9 +18,19 @@
 namespace osar {
 
 constexpr double C_LIGHT = 299792458.0;
+constexpr int MAX_LAMBDAS = 8;  // solutions of a lambda path
+
+// lambda settings of the path's solutions (relative factors or absolute)
+struct LamSet {
+  double v[MAX_LAMBDAS];
+  int n;
+};
 
 // Scalars of the online state that live on the device so that no step of a
-// pulse or a FISTA burst needs a host round trip.
+// pulse or a FISTA burst needs a host round trip.  A lambda path keeps one
+// per solution: entry 0 holds the shared fields (L_n, tau, mu, tol, error,
+// queue, pass count) and solution 0's; entry l > 0 only solution l's (t,
+// lambda, converged, iters, done).
 struct DevScalars {
   double t;         // momentum scalar t_k of Algorithm 1
   double t_next;    // t_{k+1} of the step in flight
@@ -75,14 +85,16 @@ struct osar_ctx {
   std::string last_error;
 
   // device state
-  osar::DevScalars* scal = nullptr;
+  osar::DevScalars* scal = nullptr;  // n_lam entries (lambda path)
+  int n_lam = 1;                     // solutions of the lambda path
+  osar::LamSet lam;                  // their lambda settings
   double2* b = nullptr;        // data vector b_n (Mp)
-  double2* c = nullptr;        // c^(k) == c_hat after a burst (Mp)
-  double2* z = nullptr;        // z^(k) (Mp)
+  double2* c = nullptr;        // c^(k) == c_hat after a burst (n_lam x Mp)
+  double2* z = nullptr;        // z^(k) (n_lam x Mp)
   double2* v = nullptr;        // power-iteration vector, unit norm (Mp)
   double2* w = nullptr;        // G v scratch (Mp)
   double2* xtmp = nullptr;     // scratch vector for osar_gram_apply (Mp)
-  void* zt = nullptr;          // z in the matvec's precision (Mp)
+  void* zt = nullptr;          // z in the matvec's precision (n_lam x Mp)
   void* vt = nullptr;          // v in the matvec's precision (Mp)
   void* xt = nullptr;          // osar_gram_apply input, matvec precision (Mp)
   double2* part = nullptr;     // per-block partial sums (nb)
@@ -93,8 +105,10 @@ struct osar_ctx {
                                    // bf16 (re, im) per entry
   void* segpart = nullptr;     // matvec segment partials (nseg x BLK)
   void* tilepart = nullptr;    // matvec per-block partials (nblk x BLK)
-  void* segpart2 = nullptr;    // fuse_first_step: G z_1 partials of the
-  void* tilepart2 = nullptr;   // next burst's first step
+  void* segpart2 = nullptr;    // partials of a second vector: the fused
+  void* tilepart2 = nullptr;   // first step's G z_1, or solution 1's G z
+  void* segpart_x = nullptr;   // lambda path: partials of solutions 2..
+  void* tilepart_x = nullptr;
   bool first_ready = false;    // segpart2 / tilepart2 hold G z_1 for the burst
   int4* segs = nullptr;        // matvec work items (J, I0, I1, slot)
   int* seg_begin = nullptr;    // first segment of block column J (nb + 1)

@@ -65,11 +65,12 @@ __global__ void __launch_bounds__(FIN_THREADS)
                      const double2* __restrict__ b, double2* __restrict__ c,
                      double2* __restrict__ z, T2* __restrict__ zt,
                      double2* __restrict__ part, DevScalars* sc,
-                     int count_pass) {
+                     DevScalars* gs, int count_pass) {
+  // sc: this solution's scalars; gs: the shared ones (tau, tol, passes)
   if (sc->converged) return;
   __shared__ double sh[3];  // tau, alpha, beta
   if (threadIdx.x == 0) {
-    const double t = sc->t, tau = sc->tau;
+    const double t = sc->t, tau = gs->tau;
     const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
     sh[0] = tau;
     sh[1] = sc->lambda * tau;
@@ -105,8 +106,8 @@ __global__ void __launch_bounds__(FIN_THREADS)
     const double t = sc->t;
     sc->t = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
     sc->iters += 1;
-    sc->passes += count_pass;
-    if (sc->tol > 0.0 && sqrt(tot.x) <= sc->tol * sqrt(tot.y)) sc->converged = 1;
+    gs->passes += count_pass;
+    if (gs->tol > 0.0 && sqrt(tot.x) <= gs->tol * sqrt(tot.y)) sc->converged = 1;
     sc->done = 0;
   }
 }
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
 // The last CTA of a data-update grid sets lambda_n = rel * max_j |b_j| (or
 // the absolute value) and counts the pulse.
 __device__ __forceinline__ void lambda_tail(double local_max2, double* bmax,
-                                            DevScalars* sc, double lam,
+                                            DevScalars* sc, const LamSet& lam,
                                             int relative) {
   __shared__ double red[32];
   double m = local_max2;
@@ -208,7 +209,10 @@ __device__ __forceinline__ void lambda_tail(double local_max2, double* bmax,
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t = fmax(t, red[w2]);
-    sc->lambda = relative ? lam * sqrt(t) : lam;
+    // every solution of the lambda path: lambda_n = factor x ||b_n||_inf
+    // (Eq. 11's lambda, relative) or the absolute value
+    for (int l = 0; l < lam.n; ++l)
+      sc[l].lambda = relative ? lam.v[l] * sqrt(t) : lam.v[l];
     sc->n += 1;
     sc->done = 0;
   }
@@ -219,7 +223,7 @@ template <typename T2>
 __global__ void __launch_bounds__(256)
     k_data_update_complex(const T2* __restrict__ A, int Mp, int Kp,
                           const double2* __restrict__ d, double2* __restrict__ b,
-                          double* bmax, DevScalars* sc, double lam,
+                          double* bmax, DevScalars* sc, LamSet lam,
                           int relative) {
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_data_update_planes(const __nv_bfloat16* __restrict__ Ap, int Mp, int Kp,
                          const float2* __restrict__ d, double2* __restrict__ b,
-                         double* bmax, DevScalars* sc, double lam,
+                         double* bmax, DevScalars* sc, LamSet lam,
                          int relative) {
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -322,8 +326,8 @@ __global__ void k_burst_begin(double2* __restrict__ z, T2* __restrict__ zt,
   }
 }
 
-__global__ void k_iter_begin(DevScalars* sc, double tol) {
-  sc->iters = 0;
+__global__ void k_iter_begin(DevScalars* sc, int n_lam, double tol) {
+  for (int l = 0; l < n_lam; ++l) sc[l].iters = 0;
   sc->tol = tol;
 }
 
@@ -433,6 +437,30 @@ void launch_mv(osar_ctx* ctx, MvArgs<T, R> a, int gated) {
       ctx->scal, gated, matvec_queue(ctx->scal));
 }
 
+// Device address of solution l's stop flag (pointer arithmetic only).
+const int32_t* stop_flag(const osar_ctx* ctx, int l) {
+  return reinterpret_cast<const int32_t*>(
+      reinterpret_cast<const char*>(ctx->scal + l) +
+      offsetof(DevScalars, converged));
+}
+
+// Partial-sum buffers for vector slot l of a pass: 0 the main ones, 1 the
+// second vector's, 2.. the lambda path's further solutions.
+void* seg_set(const osar_ctx* ctx, int l) {
+  if (l == 0) return ctx->segpart;
+  if (l == 1) return ctx->segpart2;
+  const size_t cplx = ctx->prec == OSAR_FP64 ? 16 : 8;
+  return static_cast<char*>(ctx->segpart_x) +
+         (size_t)(l - 2) * cplx * BLK * (size_t)ctx->nseg;
+}
+void* tile_set(const osar_ctx* ctx, int l) {
+  if (l == 0) return ctx->tilepart;
+  if (l == 1) return ctx->tilepart2;
+  const size_t cplx = ctx->prec == OSAR_FP64 ? 16 : 8;
+  return static_cast<char*>(ctx->tilepart_x) +
+         (size_t)(l - 2) * cplx * BLK * (size_t)ctx->nblk;
+}
+
 template <typename T>
 void launch_mv(osar_ctx* ctx, const void* xt, void* segp, void* tilep,
                int gated) {
@@ -441,6 +469,7 @@ void launch_mv(osar_ctx* ctx, const void* xt, void* segp, void* tilep,
   a.x[0] = (const T2*)xt;
   a.segpart[0] = (T2*)segp;
   a.tilepart[0] = (T2*)tilep;
+  a.gate[0] = stop_flag(ctx, 0);
   launch_mv<T, 1>(ctx, a, gated);
 }
 
@@ -456,13 +485,39 @@ void matvec(osar_ctx* ctx, const void* xt, int gated) {
   ctx->launches++;
 }
 
+// Gated pass applying the Gram to the iterates of solutions l and l + 1
+// (both when l + 1 < n_lam) into their partial-sum sets.
+template <typename T>
+void matvec_solutions(osar_ctx* ctx, int l) {
+  using T2 = typename Vec<T>::T2;
+  const size_t wv = sizeof(T2) * (size_t)ctx->Mp;
+  const char* zt = static_cast<const char*>(ctx->zt);
+  if (l + 1 < ctx->n_lam) {
+    MvArgs<T, 2> a;
+    for (int r = 0; r < 2; ++r) {
+      a.x[r] = reinterpret_cast<const T2*>(zt + (l + r) * wv);
+      a.segpart[r] = (T2*)seg_set(ctx, l + r);
+      a.tilepart[r] = (T2*)tile_set(ctx, l + r);
+      a.gate[r] = stop_flag(ctx, l + r);
+    }
+    launch_mv<T, 2>(ctx, a, 1);
+  } else {
+    MvArgs<T, 1> a;
+    a.x[0] = reinterpret_cast<const T2*>(zt + l * wv);
+    a.segpart[0] = (T2*)seg_set(ctx, l);
+    a.tilepart[0] = (T2*)tile_set(ctx, l);
+    a.gate[0] = stop_flag(ctx, l);
+    launch_mv<T, 1>(ctx, a, 1);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_data_update(osar_ctx* ctx) {
   ProfEvent ev;
   prof_begin(ctx, KCL_BUPD, &ev);
   const unsigned g = (unsigned)((ctx->Mp + 7) / 8);
-  const double lam = ctx->cfg.lambda;
+  const LamSet lam = ctx->lam;
   const int rel = ctx->cfg.lambda_relative;
   if (ctx->prec == OSAR_SPLIT_BF16) {
     k_stage_data<<<(unsigned)((ctx->Kp + 255) / 256), 256, 0, ctx->stream>>>(
@@ -488,8 +543,8 @@ cudaError_t launch_data_update(osar_ctx* ctx) {
 cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
   const unsigned nb = (unsigned)ctx->nb;
   // the FP64 path keeps separate passes: two FP64 vectors' partial sums do
-  // not fit the matvec's registers
-  fuse = fuse && ctx->prec != OSAR_FP64;
+  // not fit the matvec's registers; a lambda path pairs its own solutions
+  fuse = fuse && ctx->prec != OSAR_FP64 && ctx->n_lam == 1;
   for (int s = 0; s < steps; ++s) {
     const int last = s == steps - 1 ? 1 : 0;
     if (last && fuse) {
@@ -506,6 +561,7 @@ cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
       a.segpart[1] = (float2*)ctx->segpart2;
       a.tilepart[0] = (float2*)ctx->tilepart;
       a.tilepart[1] = (float2*)ctx->tilepart2;
+      a.gate[0] = a.gate[1] = stop_flag(ctx, 0);  // ungated pass
       launch_mv<float, 2>(ctx, a, 0);
       prof_end(ctx, &ev);
       ctx->launches++;
@@ -541,42 +597,82 @@ cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
 
 cudaError_t launch_burst_begin(osar_ctx* ctx) {
   const bool reset = ctx->n == 1 || ctx->cfg.restart_momentum;
-  if (ctx->prec == OSAR_FP64)
-    k_burst_begin<double2><<<(unsigned)ctx->nb, 128, 0, ctx->stream>>>(
-        ctx->z, (double2*)ctx->zt, ctx->c, ctx->Mp, ctx->scal, reset ? 1 : 0);
-  else
-    k_burst_begin<float2><<<(unsigned)ctx->nb, 128, 0, ctx->stream>>>(
-        ctx->z, (float2*)ctx->zt, ctx->c, ctx->Mp, ctx->scal, reset ? 1 : 0);
-  ctx->launches++;
+  const int64_t Mp = ctx->Mp;
+  for (int l = 0; l < ctx->n_lam; ++l) {
+    if (ctx->prec == OSAR_FP64)
+      k_burst_begin<double2><<<(unsigned)ctx->nb, 128, 0, ctx->stream>>>(
+          ctx->z + l * Mp, (double2*)ctx->zt + l * Mp, ctx->c + l * Mp, ctx->Mp,
+          ctx->scal + l, reset ? 1 : 0);
+    else
+      k_burst_begin<float2><<<(unsigned)ctx->nb, 128, 0, ctx->stream>>>(
+          ctx->z + l * Mp, (float2*)ctx->zt + l * Mp, ctx->c + l * Mp, ctx->Mp,
+          ctx->scal + l, reset ? 1 : 0);
+    ctx->launches++;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_iter_begin(osar_ctx* ctx, double tol) {
-  k_iter_begin<<<1, 1, 0, ctx->stream>>>(ctx->scal, tol);
+  k_iter_begin<<<1, 1, 0, ctx->stream>>>(ctx->scal, ctx->n_lam, tol);
   ctx->launches++;
   return cudaGetLastError();
 }
 
+namespace {
+
+// Algorithm 1's step (after the Gram pass) for solution l from partial set s.
+template <typename T2, typename Acc>
+void fista_finalize(osar_ctx* ctx, int l, int s, int count_pass) {
+  const int64_t Mp = ctx->Mp;
+  k_fista_finalize<T2, Acc><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
+      (const T2*)seg_set(ctx, s), (const T2*)tile_set(ctx, s), ctx->seg_begin,
+      ctx->nb, ctx->b, ctx->c + l * Mp, ctx->z + l * Mp, (T2*)ctx->zt + l * Mp,
+      ctx->part, ctx->scal + l, ctx->scal, count_pass);
+}
+
+}  // namespace
+
 cudaError_t launch_fista_step(osar_ctx* ctx) {
+  const bool fp64 = ctx->prec == OSAR_FP64;
+  if (ctx->n_lam > 1) {
+    // lambda path: one pass per two solutions, then each solution's step
+    // (a solution past the stop rule skips both; a pass of two runs while
+    // either still steps, and counts once)
+    for (int l = 0; l < ctx->n_lam; l += 2) {
+      ProfEvent ev;
+      prof_begin(ctx, KCL_MATVEC, &ev);
+      if (fp64)
+        matvec_solutions<double>(ctx, l);
+      else
+        matvec_solutions<float>(ctx, l);
+      prof_end(ctx, &ev);
+      ctx->launches++;
+    }
+    ProfEvent ev;
+    prof_begin(ctx, KCL_FIN, &ev);
+    for (int l = 0; l < ctx->n_lam; ++l) {
+      // the pair's pass is counted with its first solution's step
+      const int count = l % 2 == 0 ? 1 : 0;
+      if (fp64)
+        fista_finalize<double2, double>(ctx, l, l, count);
+      else
+        fista_finalize<float2, float>(ctx, l, l, count);
+      ctx->launches++;
+    }
+    prof_end(ctx, &ev);
+    return cudaGetLastError();
+  }
   // the first step after a fused push reuses the pass made with the last
   // power step (already counted as a Gram pass)
   const bool pre = ctx->first_ready;
   ctx->first_ready = false;
   if (!pre) matvec(ctx, ctx->zt, 1);
-  void* segp = pre ? ctx->segpart2 : ctx->segpart;
-  void* tilep = pre ? ctx->tilepart2 : ctx->tilepart;
   ProfEvent ev;
   prof_begin(ctx, KCL_FIN, &ev);
-  if (ctx->prec == OSAR_FP64)
-    k_fista_finalize<double2, double><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
-        (const double2*)segp, (const double2*)tilep, ctx->seg_begin, ctx->nb,
-        ctx->b, ctx->c, ctx->z, (double2*)ctx->zt, ctx->part, ctx->scal,
-        pre ? 0 : 1);
+  if (fp64)
+    fista_finalize<double2, double>(ctx, 0, pre ? 1 : 0, pre ? 0 : 1);
   else
-    k_fista_finalize<float2, float><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
-        (const float2*)segp, (const float2*)tilep, ctx->seg_begin, ctx->nb,
-        ctx->b, ctx->c, ctx->z, (float2*)ctx->zt, ctx->part, ctx->scal,
-        pre ? 0 : 1);
+    fista_finalize<float2, float>(ctx, 0, pre ? 1 : 0, pre ? 0 : 1);
   prof_end(ctx, &ev);
   ctx->launches++;
   return cudaGetLastError();
@@ -602,13 +698,16 @@ cudaError_t launch_gram_apply(osar_ctx* ctx, const double2* x, double2* y) {
 }
 
 cudaError_t launch_set_working(osar_ctx* ctx) {
-  // working-precision copies of z and v (after a checkpoint load)
+  // working-precision copies of every solution's z and of v (after a
+  // checkpoint load)
+  const int nz = ctx->n_lam * ctx->Mp;
+  const unsigned gz = (unsigned)((nz + 255) / 256);
   const unsigned g = (unsigned)((ctx->Mp + 255) / 256);
   if (ctx->prec == OSAR_FP64) {
-    k_to_working<double2><<<g, 256, 0, ctx->stream>>>(ctx->z, (double2*)ctx->zt, ctx->Mp);
+    k_to_working<double2><<<gz, 256, 0, ctx->stream>>>(ctx->z, (double2*)ctx->zt, nz);
     k_to_working<double2><<<g, 256, 0, ctx->stream>>>(ctx->v, (double2*)ctx->vt, ctx->Mp);
   } else {
-    k_to_working<float2><<<g, 256, 0, ctx->stream>>>(ctx->z, (float2*)ctx->zt, ctx->Mp);
+    k_to_working<float2><<<gz, 256, 0, ctx->stream>>>(ctx->z, (float2*)ctx->zt, nz);
     k_to_working<float2><<<g, 256, 0, ctx->stream>>>(ctx->v, (float2*)ctx->vt, ctx->Mp);
   }
   ctx->launches += 2;

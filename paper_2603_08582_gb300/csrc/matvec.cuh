@@ -113,6 +113,7 @@ struct MvArgs {
   const typename Vec<T>::T2* x[R];
   typename Vec<T>::T2* segpart[R];
   typename Vec<T>::T2* tilepart[R];
+  const int32_t* gate[R];  // gated passes: skipped when every flag is set
   int keep_l2;  // the Gram fits in L2: keep it there between passes
 };
 
@@ -135,7 +136,12 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
              unsigned* __restrict__ queue) {
   using C = Mv<T, R>;
   using T2 = typename Vec<T>::T2;
-  if (gated && sc->converged) return;
+  if (gated) {
+    bool all = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r) all = all && *a.gate[r] != 0;
+    if (all) return;  // every vector's solution has met the stop rule
+  }
   extern __shared__ __align__(128) uint8_t mv_smem[];
   T2* red = reinterpret_cast<T2*>(mv_smem + C::NST * C::STAGE);  // [2][R][CW][BLK]
   uint64_t* full = reinterpret_cast<uint64_t*>(mv_smem + C::NST * C::STAGE +

@@ -67,7 +67,8 @@ void free_all(osar_ctx* ctx) {
                   ctx->gram_tiles, ctx->dict_tiles, ctx->A, ctx->F, ctx->D,
                   ctx->Apl, ctx->Fpl, ctx->Dpl, ctx->sim_rho, ctx->sim_nz,
                   ctx->sim_idx, ctx->sim_d, ctx->dict_part, ctx->gram_pairs,
-                  ctx->dict_pairs, ctx->segpart2, ctx->tilepart2};
+                  ctx->dict_pairs, ctx->segpart2, ctx->tilepart2,
+                  ctx->segpart_x, ctx->tilepart_x};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
@@ -132,6 +133,14 @@ osar_status validate(const osar_config* c, std::string* why) {
     return *why = "tc_pairs must be in [0, 3]", OSAR_E_INVALID;
   if (c->fuse_first_step != 0 && c->fuse_first_step != 1)
     return *why = "fuse_first_step must be 0 or 1", OSAR_E_INVALID;
+  if (c->n_lambdas < 1 || c->n_lambdas > MAX_LAMBDAS)
+    return *why = "n_lambdas must be in [1, 8]", OSAR_E_INVALID;
+  if (c->n_lambdas > 1) {
+    if (!c->lambda_list) return *why = "lambda_list is NULL", OSAR_E_INVALID;
+    for (int l = 0; l < c->n_lambdas; ++l)
+      if (!is_finite(c->lambda_list[l]) || c->lambda_list[l] < 0)
+        return *why = "lambda_list values must be finite and >= 0", OSAR_E_INVALID;
+  }
   return OSAR_OK;
 }
 
@@ -201,6 +210,12 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   osar_ctx* ctx = new osar_ctx();
   ctx->cfg = *cfg;
   ctx->cfg.dict_c128 = nullptr;
+  ctx->cfg.lambda_list = nullptr;  // copied below
+  ctx->n_lam = cfg->n_lambdas;
+  ctx->lam.n = ctx->n_lam;
+  for (int l = 0; l < MAX_LAMBDAS; ++l)
+    ctx->lam.v[l] = l < ctx->n_lam && ctx->n_lam > 1 ? cfg->lambda_list[l]
+                                                     : cfg->lambda;
   ctx->prec = cfg->precision;
   ctx->dict = cfg->dict_kind != OSAR_DICT_IDENTITY;
   ctx->N = cfg->nx * cfg->ny;
@@ -250,10 +265,11 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     osar_status _s = dev_alloc(ctx, &(p), (bytes));  \
     if (_s != OSAR_OK) return bail(_s);              \
   } while (0)
-  AL(ctx->scal, sizeof(DevScalars));
+  const int L = ctx->n_lam;
+  AL(ctx->scal, sizeof(DevScalars) * L);
   AL(ctx->b, 16 * Mp);
-  AL(ctx->c, 16 * Mp);
-  AL(ctx->z, 16 * Mp);
+  AL(ctx->c, 16 * Mp * L);
+  AL(ctx->z, 16 * Mp * L);
   AL(ctx->v, 16 * Mp);
   AL(ctx->w, 16 * Mp);
   AL(ctx->xtmp, 16 * Mp);
@@ -265,11 +281,15 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     AL(ctx->g_lo, 4 * bb * ctx->nblk);
   AL(ctx->segpart, cplx * BLK * (int64_t)ctx->nseg);
   AL(ctx->tilepart, cplx * BLK * ctx->nblk);
-  if (cfg->fuse_first_step) {
+  if (cfg->fuse_first_step || L > 1) {
     AL(ctx->segpart2, cplx * BLK * (int64_t)ctx->nseg);
     AL(ctx->tilepart2, cplx * BLK * ctx->nblk);
   }
-  AL(ctx->zt, cplx * Mp);
+  if (L > 2) {
+    AL(ctx->segpart_x, cplx * BLK * (int64_t)ctx->nseg * (L - 2));
+    AL(ctx->tilepart_x, cplx * BLK * ctx->nblk * (L - 2));
+  }
+  AL(ctx->zt, cplx * Mp * L);
   AL(ctx->vt, cplx * Mp);
   AL(ctx->xt, cplx * Mp);
   AL(ctx->bmax, 8 * ((Mp + 7) / 8));
@@ -343,11 +363,12 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
                         sizeof(int4) * dpairs.size(), cudaMemcpyHostToDevice,
                         ctx->stream);
   // initial scalars and power vector v = 1/sqrt(M) on the M real atoms
-  DevScalars s0 = {};
-  s0.t = 1.0;
+  std::vector<DevScalars> s0(L);
+  std::memset(s0.data(), 0, sizeof(DevScalars) * L);
+  for (auto& s : s0) s.t = 1.0;
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ctx->scal, &s0, sizeof(s0), cudaMemcpyHostToDevice,
-                        ctx->stream);
+    e = cudaMemcpyAsync(ctx->scal, s0.data(), sizeof(DevScalars) * L,
+                        cudaMemcpyHostToDevice, ctx->stream);
   std::vector<double2> v0((size_t)Mp, make_double2(0.0, 0.0));
   for (int i = 0; i < ctx->M; ++i) v0[i].x = 1.0 / std::sqrt((double)ctx->M);
   if (e == cudaSuccess)
@@ -573,6 +594,8 @@ void osar_config_default(osar_config* c) {
   c->synth_ctas = 0;
   c->tc_pairs = 3;
   c->fuse_first_step = 1;
+  c->n_lambdas = 1;
+  c->lambda_list = nullptr;
 }
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
@@ -714,6 +737,26 @@ osar_status osar_get_state(osar_ctx* ctx, int32_t* n, double* lipschitz,
   if (lipschitz) *lipschitz = s.lip;
   if (lambda) *lambda = s.lambda;
   if (t) *t = s.t;
+  return OSAR_OK;
+}
+
+osar_status osar_get_lambda_state(osar_ctx* ctx, int32_t l, double* out_c128,
+                                  double* lambda, double* t, int32_t* iters) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (l < 0 || l >= ctx->n_lam)
+    return fail(ctx, OSAR_E_INVALID, "osar_get_lambda_state: no such solution");
+  DevScalars s;
+  CK(ctx, cudaMemcpyAsync(&s, ctx->scal + l, sizeof(s), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  if (out_c128)
+    CK(ctx, cudaMemcpyAsync(out_c128, ctx->c + (int64_t)l * ctx->Mp,
+                            sizeof(double2) * ctx->M, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (lambda) *lambda = s.lambda;
+  if (t) *t = s.t;
+  if (iters) *iters = s.iters;
   return OSAR_OK;
 }
 
@@ -948,6 +991,7 @@ struct CkptHeader {
   int32_t M, N, K, prec, dict_kind, compensated, n, fresh;
   int64_t nblk;
   int32_t entry_bytes, has_lo;
+  int32_t n_lambdas, pad;
 };
 
 osar_status write_dev(osar_ctx* ctx, FILE* f, const void* dev, size_t bytes) {
@@ -979,7 +1023,7 @@ osar_status osar_save(osar_ctx* ctx, const char* path) {
   if (!f) return fail(ctx, OSAR_E_IO, std::string("cannot open ") + path);
   CkptHeader h = {};
   std::memcpy(h.magic, "OSARCKP", 8);
-  h.version = 4;
+  h.version = 5;
   h.M = ctx->M;
   h.N = ctx->N;
   h.K = ctx->K;
@@ -991,17 +1035,19 @@ osar_status osar_save(osar_ctx* ctx, const char* path) {
   h.nblk = ctx->nblk;
   h.entry_bytes = ctx->prec == OSAR_FP64 ? 16 : 8;
   h.has_lo = ctx->g_lo ? 1 : 0;
+  h.n_lambdas = ctx->n_lam;
   const size_t vec = sizeof(double2) * ctx->Mp;
+  const size_t lvec = vec * ctx->n_lam;
   const size_t gb = (size_t)h.entry_bytes * BLK * BLK * ctx->nblk;
   bool ok = fwrite(&h, sizeof(h), 1, f) == 1;
   if (!ok) {
     fclose(f);
     return fail(ctx, OSAR_E_IO, "checkpoint write failed");
   }
-  st = write_dev(ctx, f, ctx->scal, sizeof(DevScalars));
+  st = write_dev(ctx, f, ctx->scal, sizeof(DevScalars) * ctx->n_lam);
   if (st == OSAR_OK) st = write_dev(ctx, f, ctx->b, vec);
-  if (st == OSAR_OK) st = write_dev(ctx, f, ctx->c, vec);
-  if (st == OSAR_OK) st = write_dev(ctx, f, ctx->z, vec);
+  if (st == OSAR_OK) st = write_dev(ctx, f, ctx->c, lvec);
+  if (st == OSAR_OK) st = write_dev(ctx, f, ctx->z, lvec);
   if (st == OSAR_OK) st = write_dev(ctx, f, ctx->v, vec);
   if (st == OSAR_OK) st = write_dev(ctx, f, ctx->g_hi, gb);
   if (st == OSAR_OK && ctx->g_lo) st = write_dev(ctx, f, ctx->g_lo, (size_t)4 * BLK * BLK * ctx->nblk);
@@ -1017,7 +1063,7 @@ osar_status osar_load(const char* path, const osar_config* cfg, osar_ctx** out) 
   if (!f) return fail(nullptr, OSAR_E_IO, std::string("cannot open ") + path);
   CkptHeader h;
   if (fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "OSARCKP", 8) != 0 ||
-      h.version != 4) {
+      h.version != 5) {
     fclose(f);
     return fail(nullptr, OSAR_E_IO, "not an osar checkpoint");
   }
@@ -1029,17 +1075,18 @@ osar_status osar_load(const char* path, const osar_config* cfg, osar_ctx** out) 
   }
   if (h.M != ctx->M || h.N != ctx->N || h.K != ctx->K || h.prec != ctx->prec ||
       h.dict_kind != ctx->cfg.dict_kind || h.nblk != ctx->nblk ||
-      h.has_lo != (ctx->g_lo ? 1 : 0)) {
+      h.has_lo != (ctx->g_lo ? 1 : 0) || h.n_lambdas != ctx->n_lam) {
     fclose(f);
     osar_destroy(ctx);
     return fail(nullptr, OSAR_E_INVALID, "checkpoint does not match the config");
   }
   const size_t vec = sizeof(double2) * ctx->Mp;
+  const size_t lvec = vec * ctx->n_lam;
   const size_t gb = (size_t)h.entry_bytes * BLK * BLK * ctx->nblk;
-  st = read_dev(ctx, f, ctx->scal, sizeof(DevScalars));
+  st = read_dev(ctx, f, ctx->scal, sizeof(DevScalars) * ctx->n_lam);
   if (st == OSAR_OK) st = read_dev(ctx, f, ctx->b, vec);
-  if (st == OSAR_OK) st = read_dev(ctx, f, ctx->c, vec);
-  if (st == OSAR_OK) st = read_dev(ctx, f, ctx->z, vec);
+  if (st == OSAR_OK) st = read_dev(ctx, f, ctx->c, lvec);
+  if (st == OSAR_OK) st = read_dev(ctx, f, ctx->z, lvec);
   if (st == OSAR_OK) st = read_dev(ctx, f, ctx->v, vec);
   if (st == OSAR_OK) st = read_dev(ctx, f, ctx->g_hi, gb);
   if (st == OSAR_OK && ctx->g_lo)

@@ -178,6 +178,10 @@ osar_status osar_batch_create(const osar_config* cfgs, int32_t n_scenes,
       return bfail(nullptr, OSAR_E_INVALID, "batched scenes use the pixel basis");
     if (c.precision != prec)
       return bfail(nullptr, OSAR_E_INVALID, "all scenes share one precision");
+    if (c.n_lambdas > 1)
+      return bfail(nullptr, OSAR_E_INVALID,
+                   "batched scenes have one lambda each (a lambda path is a "
+                   "single-context feature)");
     if (c.nx < 1 || c.ny < 1 || (int64_t)c.nx * c.ny > 131072 || c.n_freq < 1 ||
         c.n_freq > 16384 || !(c.pixel_m > 0) || !(c.f_lo_hz > 0) ||
         !(c.f_hi_hz >= c.f_lo_hz) || !(c.lambda >= 0) ||

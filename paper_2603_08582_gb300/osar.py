@@ -33,6 +33,7 @@ EXPORTS = [
     "osar_config_default", "osar_create", "osar_destroy", "osar_push_pulse",
     "osar_push_pulse_dev", "osar_iterate", "osar_get_coeffs",
     "osar_get_coeffs_dev", "osar_get_coeffs_async", "osar_wait_coeffs",
+    "osar_get_lambda_state",
     "osar_get_state", "osar_get_dims", "osar_get_gram",
     "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
     "osar_gram_apply_static",
@@ -63,6 +64,7 @@ class OsarConfig(C.Structure):
         ("cuda_stream", C.c_void_p),
         ("overlap_synthesis", C.c_int32), ("synth_ctas", C.c_int32),
         ("tc_pairs", C.c_int32), ("fuse_first_step", C.c_int32),
+        ("n_lambdas", C.c_int32), ("lambda_list", C.c_void_p),
     ]
 
 
@@ -99,6 +101,7 @@ def load_library(path: str = LIB_PATH):
         "osar_get_coeffs_dev": (I32, [P, P]),
         "osar_get_coeffs_async": (I32, [P, D, I32]),
         "osar_wait_coeffs": (I32, [P, I32]),
+        "osar_get_lambda_state": (I32, [P, I32, D, D, D, C.POINTER(I32)]),
         "osar_get_state": (I32, [P, C.POINTER(I32), D, D, D]),
         "osar_get_dims": (I32, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
         "osar_get_gram": (I32, [P, D]),
@@ -159,7 +162,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
                 lam=0.05, lambda_relative=True, power_iters_first=30,
                 power_iters=4, lipschitz_margin=0.01, restart_momentum=False,
                 compensated=True, stream=None, overlap_synthesis=True,
-                synth_ctas=0, tc_pairs=3, fuse_first_step=True):
+                synth_ctas=0, tc_pairs=3, fuse_first_step=True, lambdas=None):
     """Build an osar_config.  dictionary: None (identity), "gaussian"
     (seeded Philox atoms, needs n_atoms) or an N x M complex array."""
     cfg = default_config()
@@ -191,6 +194,14 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
     cfg.synth_ctas = int(synth_ctas)
     cfg.tc_pairs = int(tc_pairs)  # bit 0 dictionary product, bit 1 Gram update
     cfg.fuse_first_step = 1 if fuse_first_step else 0
+    if lambdas is not None and len(lambdas) > 1:
+        # lambda path: one solution per value (relative or absolute like lam)
+        lv = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+        cfg.n_lambdas = int(lv.size)
+        cfg.lambda_list = lv.ctypes.data
+        keep = (keep, lv)
+    elif lambdas is not None:
+        cfg.lam = float(lambdas[0])
     cfg._keepalive = keep
     return cfg
 
@@ -284,6 +295,17 @@ class Osar:
         self._check(self._lib.osar_get_state(self._h, C.byref(n), C.byref(lip),
                                              C.byref(lam), C.byref(t)))
         return {"n": n.value, "lipschitz": lip.value, "lambda": lam.value, "t": t.value}
+
+    def lambda_state(self, l: int) -> dict:
+        """Solution l of a lambda path: coefficients, lambda_n, t and the FISTA
+        steps of the last iterate call."""
+        out = np.empty(self.m_atoms, dtype=np.complex128)
+        lam, t = C.c_double(), C.c_double()
+        it = C.c_int32()
+        self._check(self._lib.osar_get_lambda_state(
+            self._h, int(l), _dptr(out.view(np.float64)), C.byref(lam), C.byref(t),
+            C.byref(it)))
+        return {"coeffs": out, "lambda": lam.value, "t": t.value, "iters": it.value}
 
     def gram(self) -> np.ndarray:
         out = np.empty((self.m_atoms, self.m_atoms), dtype=np.complex128)

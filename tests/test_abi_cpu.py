@@ -48,6 +48,7 @@ def test_config_defaults_and_layout(lib):
     assert cfg.cuda_stream is None
     assert cfg.overlap_synthesis == 1 and cfg.synth_ctas == 0
     assert cfg.tc_pairs == 3 and cfg.fuse_first_step == 1
+    assert cfg.n_lambdas == 1 and cfg.lambda_list is None
 
 
 @pytest.mark.parametrize("field,value", [
@@ -55,7 +56,8 @@ def test_config_defaults_and_layout(lib):
     ("precision", 7), ("dict_kind", 9), ("power_iters_first", 0),
     ("lam", float("nan")), ("lipschitz_margin", -0.5),
     ("overlap_synthesis", 2), ("synth_ctas", -1), ("tc_pairs", 4),
-    ("fuse_first_step", 2),
+    ("fuse_first_step", 2), ("n_lambdas", 0), ("n_lambdas", 9),
+    ("n_lambdas", 2),  # > 1 without a lambda_list
 ])
 def test_create_rejects_invalid_config_before_any_device_work(lib, field, value):
     cfg = osar.default_config()
