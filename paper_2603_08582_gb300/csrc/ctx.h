@@ -212,6 +212,7 @@ cudaError_t launch_data_update(osar_ctx* ctx);
 // fuse: the last step also applies the Gram to the next burst's z_1 = c_hat
 // (burst started here; its first FISTA step reuses that pass)
 cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse);
+cudaError_t prepare_burst_kernels();  // shared-memory carve-out of the burst kernels
 cudaError_t launch_set_working(osar_ctx* ctx);
 cudaError_t launch_burst_begin(osar_ctx* ctx);
 cudaError_t launch_iter_begin(osar_ctx* ctx, double tol);

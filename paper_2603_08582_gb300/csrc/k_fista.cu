@@ -612,6 +612,28 @@ cudaError_t launch_burst_begin(osar_ctx* ctx) {
   return cudaGetLastError();
 }
 
+// The matvec runs with the largest shared-memory carve-out; the small
+// kernels between its passes ask for the same one, so that the SMs need not
+// switch their L1 / shared-memory split at every launch of a burst.
+cudaError_t prepare_burst_kernels() {
+  const int v = cudaSharedmemCarveoutMaxShared;
+  const cudaFuncAttribute a = cudaFuncAttributePreferredSharedMemoryCarveout;
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, a, v);
+  };
+  set((const void*)k_fista_finalize<float2, float>);
+  set((const void*)k_fista_finalize<double2, double>);
+  set((const void*)k_power_finalize<float2, float>);
+  set((const void*)k_power_finalize<double2, double>);
+  set((const void*)k_power_normalize<float2>);
+  set((const void*)k_power_normalize<double2>);
+  set((const void*)k_burst_begin<float2>);
+  set((const void*)k_burst_begin<double2>);
+  set((const void*)k_iter_begin);
+  return e;
+}
+
 cudaError_t launch_iter_begin(osar_ctx* ctx, double tol) {
   k_iter_begin<<<1, 1, 0, ctx->stream>>>(ctx->scal, ctx->n_lam, tol);
   ctx->launches++;
