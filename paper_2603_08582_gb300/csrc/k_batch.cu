@@ -219,123 +219,6 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 2)
-    k_b_matvec(const typename Vec<T>::T2* __restrict__ G,
-               const typename Vec<T>::T2* __restrict__ x,
-               typename Vec<T>::T2* __restrict__ segpart,
-               typename Vec<T>::T2* __restrict__ tilepart,
-               const int4* __restrict__ segs, const int* __restrict__ seg_scene,
-               int nseg, const SceneDesc* __restrict__ desc,
-               const DevScalars* __restrict__ sc, int gated, int pstep,
-               unsigned* __restrict__ queue) {
-  using T2 = typename Vec<T>::T2;
-  constexpr int RB = sizeof(T) == 4 ? 8 : 4;
-  __shared__ T2 xs[BLK];
-  __shared__ T2 red[8][BLK];
-  __shared__ int s_next;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int s = blockIdx.x; s < nseg; s = s_next) {
-    const int scene = seg_scene[s];
-    const SceneDesc& d = desc[scene];
-    const bool skip = !d.active || (gated && sc[scene].converged) ||
-                      (pstep >= 0 && pstep >= d.psteps);
-    if (!skip) {
-      const int4 sg = segs[s];
-      const int J = sg.x, nb = d.nb;
-      const T2* xsc = x + d.row;
-      __syncthreads();
-      if (threadIdx.x < BLK) xs[threadIdx.x] = xsc[J * BLK + threadIdx.x];
-      __syncthreads();
-      T br[16], bi[16];
-  #pragma unroll
-      for (int c = 0; c < 16; ++c) br[c] = bi[c] = T(0);
-      for (int I = sg.y; I < sg.z; ++I) {
-        const int64_t bidx = d.gblk + packed_block(I, J, nb);
-        const T2* blk = G + bidx * (int64_t)(BLK * BLK) +
-                        (int64_t)(warp * 16) * BLK + lane * 4;
-        T2 xi[4];
-  #pragma unroll
-        for (int q = 0; q < 4; ++q) xi[q] = xsc[I * BLK + lane * 4 + q];
-        T ar[4], ai[4];
-  #pragma unroll
-        for (int q = 0; q < 4; ++q) ar[q] = ai[q] = T(0);
-  #pragma unroll
-        for (int c0 = 0; c0 < 16; c0 += RB) {
-          T2 g[RB][4];
-  #pragma unroll
-          for (int c = 0; c < RB; ++c) load4(blk + (int64_t)(c0 + c) * BLK, g[c]);
-  #pragma unroll
-          for (int c = 0; c < RB; ++c) {
-            const T2 xj = xs[warp * 16 + c0 + c];
-  #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const T2 e = g[c][q];
-              br[c0 + c] = fma(e.x, xi[q].x, br[c0 + c]);
-              br[c0 + c] = fma(e.y, xi[q].y, br[c0 + c]);
-              bi[c0 + c] = fma(e.x, xi[q].y, bi[c0 + c]);
-              bi[c0 + c] = fma(-e.y, xi[q].x, bi[c0 + c]);
-              ar[q] = fma(e.x, xj.x, ar[q]);
-              ar[q] = fma(-e.y, xj.y, ar[q]);
-              ai[q] = fma(e.x, xj.y, ai[q]);
-              ai[q] = fma(e.y, xj.x, ai[q]);
-            }
-          }
-        }
-        if (I != J) {
-  #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            T2 v;
-            v.x = ar[q];
-            v.y = ai[q];
-            red[warp][lane * 4 + q] = v;
-          }
-          __syncthreads();
-          if (threadIdx.x < BLK) {
-            T sr = 0, si = 0;
-  #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-              sr += red[w][threadIdx.x].x;
-              si += red[w][threadIdx.x].y;
-            }
-            T2 v;
-            v.x = sr;
-            v.y = si;
-            tilepart[bidx * BLK + threadIdx.x] = v;
-          }
-          __syncthreads();
-        }
-      }
-  #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        T vr = br[c], vi = bi[c];
-  #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          vr += __shfl_xor_sync(0xffffffffu, vr, o);
-          vi += __shfl_xor_sync(0xffffffffu, vi, o);
-        }
-        if (lane == c) {
-          T2 v;
-          v.x = vr;
-          v.y = vi;
-          segpart[(int64_t)sg.w * BLK + warp * 16 + c] = v;
-        }
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s_next = (int)gridDim.x + (int)atomicAdd(&queue[0], 1u);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&queue[1], 1u) == gridDim.x - 1) {
-      queue[0] = 0;
-      queue[1] = 0;
-      __threadfence();
-    }
-  }
-}
-
 // Gather for item (scene, K): the scene's column-K segment partials and its
 // block partials (K, J), J > K.
 template <typename T2, typename Acc>
@@ -576,18 +459,27 @@ cudaError_t batch_launch_data_update(osar_batch* B) {
 
 cudaError_t batch_launch_matvec(osar_batch* B, const void* xt, int gated,
                                 int pstep) {
-  const int grid = std::min(B->nseg, 2 * B->sm_count);
+  const int grid = std::min(B->nseg, B->sm_count);
   if (grid <= 0) return cudaSuccess;
+  const MvBatch mb{B->seg_scene, B->desc, B->sc, gated, pstep};
+  auto go = [&](auto zero) {
+    using T = decltype(zero);
+    using T2 = typename Vec<T>::T2;
+    using C = Mv<T, 1>;
+    MvArgs<T, 1> a = {};
+    a.x[0] = (const T2*)xt;
+    a.segpart[0] = (T2*)B->segpart;
+    a.tilepart[0] = (T2*)B->tilepart;
+    cudaFuncSetAttribute(k_matvec<T, 1, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    k_matvec<T, 1, true><<<grid, C::THREADS, C::SMEM, B->stream>>>(
+        (const T2*)B->g_hi, a, B->segs, B->nseg, 0, B->sc, 0,
+        matvec_queue(B->sc), mb);
+  };
   if (B->prec == OSAR_FP64)
-    k_b_matvec<double><<<grid, 256, 0, B->stream>>>(
-        (const double2*)B->g_hi, (const double2*)xt, (double2*)B->segpart,
-        (double2*)B->tilepart, B->segs, B->seg_scene, B->nseg, B->desc, B->sc,
-        gated, pstep, matvec_queue(B->sc));
+    go(0.0);
   else
-    k_b_matvec<float><<<grid, 256, 0, B->stream>>>(
-        (const float2*)B->g_hi, (const float2*)xt, (float2*)B->segpart,
-        (float2*)B->tilepart, B->segs, B->seg_scene, B->nseg, B->desc, B->sc,
-        gated, pstep, matvec_queue(B->sc));
+    go(0.0f);
   B->launches++;
   return cudaGetLastError();
 }

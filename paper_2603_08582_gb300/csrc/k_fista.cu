@@ -428,13 +428,13 @@ void launch_mv(osar_ctx* ctx, MvArgs<T, R> a, int gated) {
   using C = Mv<T, R>;
   a.keep_l2 = ctx->nblk * BLK * BLK * (int64_t)sizeof(typename Vec<T>::T2) <=
               KEEP_L2_BYTES;
-  cudaFuncSetAttribute(k_matvec<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       C::SMEM);
+  cudaFuncSetAttribute(k_matvec<T, R, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   const unsigned grid =
       (unsigned)(ctx->nseg < ctx->sm_count ? ctx->nseg : ctx->sm_count);
-  k_matvec<T, R><<<grid, C::THREADS, C::SMEM, ctx->stream>>>(
+  k_matvec<T, R, false><<<grid, C::THREADS, C::SMEM, ctx->stream>>>(
       (const typename Vec<T>::T2*)ctx->g_hi, a, ctx->segs, ctx->nseg, ctx->nb,
-      ctx->scal, gated, matvec_queue(ctx->scal));
+      ctx->scal, gated, matvec_queue(ctx->scal), MvBatch{});
 }
 
 // Device address of solution l's stop flag (pointer arithmetic only).

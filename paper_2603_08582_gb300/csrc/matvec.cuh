@@ -7,9 +7,11 @@
 //
 // Matvec: y = A x needs, for every stored block,
 //     y_I += T_IJ x_J      and, when I < J,      y_J += T_IJ^H x_I.
-// Work items ("segments") are runs of blocks I0..I1-1 of one block column J.
-// A CTA streams each block once from HBM; each warp owns 16 stored columns c,
-// each lane 4 consecutive rows r (one 32-byte sector per column):
+// Work items ("segments") are runs of blocks I0..I1-1 of one block column J
+// (of one scene, in the batching form).  A CTA's producer thread streams each
+// block once from HBM into a shared-memory ring, in 32 KB chunks of stored
+// columns; each consumer warp owns WC columns of every chunk (16 of each
+// block), each lane 4 consecutive rows r:
 //   * y_J[c] = sum_r conj(T[r][c]) x_I[r] accumulates over the whole segment
 //     in registers and is reduced across lanes once at the end (segment
 //     partial); on a diagonal block (T Hermitian, stored in full) this alone
@@ -21,7 +23,7 @@
 // in the packed order.  No floating-point atomics: results are deterministic.
 #pragma once
 
-#include "ctx.h"
+#include "batch.h"
 
 namespace osar {
 namespace {
@@ -36,20 +38,6 @@ template <>
 struct Vec<double> {
   using T2 = double2;
 };
-
-// Four consecutive complex entries of one stored column (streamed once).
-__device__ __forceinline__ void load4(const float2* p, float2 (&g)[4]) {
-  const float4* q = reinterpret_cast<const float4*>(p);
-  float4 a = __ldcs(q), b = __ldcs(q + 1);
-  g[0] = make_float2(a.x, a.y);
-  g[1] = make_float2(a.z, a.w);
-  g[2] = make_float2(b.x, b.y);
-  g[3] = make_float2(b.z, b.w);
-}
-__device__ __forceinline__ void load4(const double2* p, double2 (&g)[4]) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) g[c] = __ldcs(p + c);
-}
 
 // Four consecutive complex entries of one stored column, from shared memory.
 __device__ __forceinline__ void load4_smem(const float2* p, float2 (&g)[4]) {
@@ -117,6 +105,17 @@ struct MvArgs {
   int keep_l2;  // the Gram fits in L2: keep it there between passes
 };
 
+// Batching form: a segment's scene gives its Gram's first packed block, its
+// block count per side and its first stacked row, and whether it takes part
+// in this pass (active scene, stop rule not met, power steps left).
+struct MvBatch {
+  const int* seg_scene;
+  const SceneDesc* desc;
+  const DevScalars* sc;
+  int gated;
+  int pstep;  // power step of the pass, or -1 for a FISTA pass
+};
+
 constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
 
 // One Gram pass.  Each thread accumulates y_J over NACC of the block's stored
@@ -128,15 +127,15 @@ constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
 // kernel spreads over whatever SMs are free, e.g. beside the next pulse's
 // dictionary product.  Every wait is bounded; on a timeout the CTA records
 // the error, stops at the next per-block barrier and drains its copies.
-template <typename T, int R>
+template <typename T, int R, bool BATCH>
 __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
     k_matvec(const typename Vec<T>::T2* __restrict__ G, const MvArgs<T, R> a,
              const int4* __restrict__ segs, int nseg, int nb,
              DevScalars* __restrict__ sc, int gated,
-             unsigned* __restrict__ queue) {
+             unsigned* __restrict__ queue, const MvBatch mb) {
   using C = Mv<T, R>;
   using T2 = typename Vec<T>::T2;
-  if (gated) {
+  if (!BATCH && gated) {
     bool all = true;
 #pragma unroll
     for (int r = 0; r < R; ++r) all = all && *a.gate[r] != 0;
@@ -147,7 +146,8 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(mv_smem + C::NST * C::STAGE +
                                                C::RED_BYTES);
   uint64_t* empty = full + C::NST;
-  int4* meta = reinterpret_cast<int4*>(empty + C::NST);  // (I, J, slot, flags)
+  // per stage: (packed block of the Gram, diagonal?, segment slot, flags)
+  int4* meta = reinterpret_cast<int4*>(empty + C::NST);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(meta + C::NST);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -177,8 +177,21 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
     if (s < nseg) s_next = (int)gridDim.x + (int)atomicAdd(&queue[0], 1u);
     while (ok && s < nseg) {
       const int4 sg = segs[s];
-      for (int I = sg.y; ok && I < sg.z; ++I) {
-        const T2* blk = G + packed_block(I, sg.x, nb) * (int64_t)(BLK * BLK);
+      int64_t gbase = 0, xrow = 0;
+      int nbs = nb;
+      bool take = true;
+      if (BATCH) {
+        const int scene = mb.seg_scene[s];
+        const SceneDesc& d = mb.desc[scene];
+        take = d.active && !(mb.gated && mb.sc[scene].converged) &&
+               !(mb.pstep >= 0 && mb.pstep >= d.psteps);
+        gbase = d.gblk;
+        nbs = d.nb;
+        xrow = d.row;
+      }
+      for (int I = sg.y; take && ok && I < sg.z; ++I) {
+        const int64_t pb = gbase + packed_block(I, sg.x, nbs);
+        const T2* blk = G + pb * (int64_t)(BLK * BLK);
         for (int k = 0; k < C::CHUNKS; ++k) {
           if (!mbar_wait_bounded(&empty[stage], ph ^ 1, abort_flag, &sc->error,
                                  MV_WAIT_LIMIT_NS)) {
@@ -186,7 +199,7 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
             break;
           }
           if (k == 0)
-            meta[stage] = make_int4(I, sg.x, sg.w,
+            meta[stage] = make_int4((int)pb, I == sg.x ? 1 : 0, sg.w,
                                     (I == sg.y ? 1 : 0) | (I == sg.z - 1 ? 2 : 0));
           uint8_t* st = mv_smem + stage * C::STAGE;
           mbar_expect_tx(&full[stage], C::STAGE);
@@ -194,10 +207,10 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
                          &full[stage], stream_policy);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            bulk_load(st + C::G_BYTES + r * C::XI_BYTES, a.x[r] + (int64_t)I * BLK,
-                      C::XI_BYTES, &full[stage]);
+            bulk_load(st + C::G_BYTES + r * C::XI_BYTES,
+                      a.x[r] + xrow + (int64_t)I * BLK, C::XI_BYTES, &full[stage]);
             bulk_load(st + C::G_BYTES + R * C::XI_BYTES + r * C::XJ_BYTES,
-                      a.x[r] + (int64_t)sg.x * BLK + k * C::CC, C::XJ_BYTES,
+                      a.x[r] + xrow + (int64_t)sg.x * BLK + k * C::CC, C::XJ_BYTES,
                       &full[stage]);
           }
           issued[stage]++;
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
     const int4 m = ok ? meta[stage] : make_int4(-1, 0, 0, 0);
     const bool work = ok && m.x >= 0;
     if (work) {
-      const int I = m.x, J = m.y;
+      const bool diag = m.y != 0;
       if (m.w & 1) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -316,7 +329,7 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
           ph ^= 1;
         }
       }
-      if (ok && I != J) {
+      if (ok && !diag) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
     named_barrier(1, 32 * C::CW);
     if (!work || *abort_flag) break;
     const int rr = (int)threadIdx.x - 32;
-    if (m.x != m.y && rr < R * BLK) {
+    if (!m.y && rr < R * BLK) {
       const int r = rr / BLK, row = rr % BLK;
       T sr = 0, si = 0;
 #pragma unroll
@@ -362,7 +375,7 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
       T2 v;
       v.x = sr;
       v.y = si;
-      a.tilepart[r][packed_block(m.x, m.y, nb) * BLK + row] = v;
+      a.tilepart[r][(int64_t)m.x * BLK + row] = v;
     }
     rp ^= 1;
   }
