@@ -11,11 +11,12 @@
 // (of one scene, in the batching form).  A CTA's producer thread streams each
 // block once from HBM into a shared-memory ring, in 32 KB chunks of stored
 // columns; each consumer warp owns WC columns of every chunk (16 of each
-// block), each lane 4 consecutive rows r:
-//   * y_J[c] = sum_r conj(T[r][c]) x_I[r] accumulates over the whole segment
-//     in registers and is reduced across lanes once at the end (segment
-//     partial); on a diagonal block (T Hermitian, stored in full) this alone
-//     is the block's product;
+// block), each lane 4 rows r of them (mv_row):
+//   * y_J[c] = sum_r conj(T[r][c]) x_I[r]: each lane's 4-row sum per block is
+//     added to a register accumulator that runs over the whole segment and
+//     is reduced across lanes once at the end (segment partial); on a
+//     diagonal block (T Hermitian, stored in full) this alone is the block's
+//     product;
 //   * y_I[r] = sum_c T[r][c] x_J[c] is reduced across the 8 warps through
 //     shared memory per off-diagonal block (block partial).
 // The consumer (gather_row) sums, per output block K, the segment partials
@@ -39,28 +40,48 @@ struct Vec<double> {
   using T2 = double2;
 };
 
-// Four consecutive complex entries of one stored column, from shared memory.
-__device__ __forceinline__ void load4_smem(const float2* p, float2 (&g)[4]) {
-  const float4* q = reinterpret_cast<const float4*>(p);
-  const float4 a = q[0], b = q[1];
+// Rows of a block that consumer lane `lane` handles (q = 0..3).  FP32: rows
+// 2 lane, 2 lane + 1, 64 + 2 lane, 64 + 2 lane + 1, so that each 16-byte
+// load of a stored column covers 512 contiguous bytes across the warp (four
+// shared-memory wavefronts, no bank conflict).  FP64: four consecutive rows
+// (the FP64 pass is bound by the FP64 pipe, not by shared memory).
+template <typename T>
+__device__ __forceinline__ int mv_row(int lane, int q);
+template <>
+__device__ __forceinline__ int mv_row<float>(int lane, int q) {
+  return (q >> 1) * 64 + 2 * lane + (q & 1);
+}
+template <>
+__device__ __forceinline__ int mv_row<double>(int lane, int q) {
+  return lane * 4 + q;
+}
+
+// The lane's four entries of one stored column, from shared memory.
+__device__ __forceinline__ void load4_smem(const float2* col, int lane,
+                                           float2 (&g)[4]) {
+  const float4 a = reinterpret_cast<const float4*>(col + 2 * lane)[0];
+  const float4 b = reinterpret_cast<const float4*>(col + 64 + 2 * lane)[0];
   g[0] = make_float2(a.x, a.y);
   g[1] = make_float2(a.z, a.w);
   g[2] = make_float2(b.x, b.y);
   g[3] = make_float2(b.z, b.w);
 }
-__device__ __forceinline__ void load4_smem(const double2* p, double2 (&g)[4]) {
+__device__ __forceinline__ void load4_smem(const double2* col, int lane,
+                                           double2 (&g)[4]) {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) g[c] = p[c];
+  for (int c = 0; c < 4; ++c) g[c] = col[lane * 4 + c];
 }
 
-// acc += a * b on both components, with the rounding of two scalar FMAs:
-// one packed FP32x2 FMA (FFMA2) on sm_100 and later, two FP64 FMAs.
-__device__ __forceinline__ void mac2(float2& acc, float a, float2 b) {
-  acc = __ffma2_rn(make_float2(a, a), b, acc);
-}
+// acc += a * b on both components (FP64: two scalar FMAs).
 __device__ __forceinline__ void mac2(double2& acc, double a, double2 b) {
   acc.x = fma(a, b.x, acc.x);
   acc.y = fma(a, b.y, acc.y);
+}
+
+// acc += a * b componentwise: one packed FP32x2 FMA (FFMA2), rounding as two
+// scalar FMAs.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 acc) {
+  return __ffma2_rn(a, b, acc);
 }
 
 // Shared-memory pipeline of the matvec.  A stage holds one chunk of CC
@@ -278,16 +299,21 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
             mv_smem + stage * C::STAGE + C::G_BYTES + r * C::XI_BYTES);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          xa[r][q] = xis[lane * 4 + q];
+          xa[r][q] = xis[mv_row<T>(lane, q)];
           xb[r][q].x = xa[r][q].y;
           xb[r][q].y = -xa[r][q].x;
         }
       }
-      T2 yi[R][4];  // y_I partials of this lane's 4 rows
+      // y_I partials of this lane's 4 rows.  FP32 keeps two packed sums per
+      // row, u = sum e (x.re, -x.im) and v = sum e (x.im, x.re) over the
+      // entries e = (re, im) of the row and x = x_J[c], so that every entry
+      // enters an FFMA2 as loaded: y_I = (u.x + u.y, v.x + v.y).  FP64 keeps
+      // (re, im) in yu.
+      T2 yu[R][4], yv[R][4];
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) yi[r][q].x = yi[r][q].y = T(0);
+        for (int q = 0; q < 4; ++q) yu[r][q].x = yu[r][q].y = yv[r][q].x = yv[r][q].y = T(0);
 #pragma unroll
       for (int k = 0; k < C::CHUNKS; ++k) {
         if (k > 0 && ok)
@@ -300,24 +326,42 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
           for (int j = 0; j < C::WC; ++j) {
             const int col = cw * C::WC + j;
             T2 g[4];
-            load4_smem(gs + col * BLK + lane * 4, g);
+            load4_smem(gs + col * BLK, lane, g);
             const int aa = k * C::WC + j;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
               const T2 ja = reinterpret_cast<const T2*>(
                   st + C::G_BYTES + R * C::XI_BYTES + r * C::XJ_BYTES)[col];
-              T2 jb;  // (-im, re) of x_J[c]
-              jb.x = -ja.y;
-              jb.y = ja.x;
+              if constexpr (sizeof(T) == 4) {
+                // y_J[c] += sum_r conj(e) x_I[r]: p = sum e (x.re, x.im),
+                // q = sum e (x.im, -x.re), folded once per column
+                const float2 cj = make_float2(ja.x, -ja.y);
+                const float2 sj = make_float2(ja.y, ja.x);
+                float2 p = make_float2(0.f, 0.f), qs = make_float2(0.f, 0.f);
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const T2 e = g[q];
-                // y_J[c] += conj(e) x_I[r] = e.re (x.re, x.im) + e.im (x.im, -x.re)
-                mac2(yj[r][aa], e.x, xa[r][q]);
-                mac2(yj[r][aa], e.y, xb[r][q]);
-                // y_I[r] += e x_J[c] = e.re (x.re, x.im) + e.im (-x.im, x.re)
-                mac2(yi[r][q], e.x, ja);
-                mac2(yi[r][q], e.y, jb);
+                for (int q = 0; q < 4; ++q) {
+                  const float2 e = g[q];
+                  p = fma2(e, xa[r][q], p);
+                  qs = fma2(e, xb[r][q], qs);
+                  yu[r][q] = fma2(e, cj, yu[r][q]);
+                  yv[r][q] = fma2(e, sj, yv[r][q]);
+                }
+                yj[r][aa].x += p.x + p.y;
+                yj[r][aa].y += qs.x + qs.y;
+              } else {
+                T2 jb;  // (-im, re) of x_J[c]
+                jb.x = -ja.y;
+                jb.y = ja.x;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const T2 e = g[q];
+                  // y_J[c] += conj(e) x_I[r] = e.re (x.re, x.im) + e.im (x.im, -x.re)
+                  mac2(yj[r][aa], e.x, xa[r][q]);
+                  mac2(yj[r][aa], e.y, xb[r][q]);
+                  // y_I[r] += e x_J[c] = e.re (x.re, x.im) + e.im (-x.im, x.re)
+                  mac2(yu[r][q], e.x, ja);
+                  mac2(yu[r][q], e.y, jb);
+                }
               }
             }
           }
@@ -333,8 +377,14 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            red[((rp * R + r) * C::CW + cw) * BLK + lane * 4 + q] = yi[r][q];
+          for (int q = 0; q < 4; ++q) {
+            T2 v = yu[r][q];
+            if constexpr (sizeof(T) == 4) {
+              v.x = yu[r][q].x + yu[r][q].y;
+              v.y = yv[r][q].x + yv[r][q].y;
+            }
+            red[((rp * R + r) * C::CW + cw) * BLK + mv_row<T>(lane, q)] = v;
+          }
       }
       if (ok && (m.w & 2)) {
         // segment done: y_J over all rows of its blocks, one lane per column
