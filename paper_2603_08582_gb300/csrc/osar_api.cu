@@ -456,19 +456,19 @@ void refresh_iters_estimate(osar_ctx* ctx) {
 // the grid.  On g SMs the product takes D / g (D = its tensor flops over
 // the split-BF16 rate one SM sustains beside the burst); meanwhile a Gram
 // pass takes max(bytes / HBM bandwidth, bytes / ((S - g) x per-SM
-// bandwidth)) x contention (one SM pulls at most about 73 GB/s, and the
+// bandwidth)) x contention (one SM pulls at most about 84 GB/s, and the
 // product's own traffic slows the pass by about 8 %), and the rest of the
 // burst runs at full speed.  The g that finishes both soonest is compared
-// with running the product alone on the whole GPU before the burst (0, the
-// full grid).  The constants were measured on GB300 with the 128 x 128
-// workload (one SM: 1.23e13 f/s alone, about 0.9e13 beside the burst).
+// with running the product alone on the whole GPU after the burst (0).  The
+// constants were measured on GB300 with the 128 x 128 workload (one SM:
+// 1.23e13 f/s alone, about 1.2e13 beside the burst).
 int synth_grid(const osar_ctx* ctx, bool main_idle) {
   if (ctx->cfg.synth_ctas > 0) return std::min(ctx->cfg.synth_ctas, ctx->sm_count);
   // nothing in flight on the main stream (the caller waited for the last
   // burst): the product has the GPU to itself
   if (main_idle) return 0;
-  constexpr double kSmRateAlone = 1.23e13, kSmRateBeside = 0.9e13;  // f/s
-  constexpr double kHbm = 6.8e12, kSmBw = 73e9, kContention = 1.08;  // B/s
+  constexpr double kSmRateAlone = 1.23e13, kSmRateBeside = 1.2e13;  // f/s
+  constexpr double kHbm = 6.8e12, kSmBw = 84e9, kContention = 1.08;  // B/s
   const double flops = 24.0 * ctx->Kp * (double)ctx->Np * ctx->Mp;
   const double bytes = (double)ctx->nblk * BLK * BLK * 8.0;
   const double pass = bytes / kHbm;
@@ -503,19 +503,26 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
   cudaError_t e = cudaSuccess;
   if (ctx->side && !capturing(ctx->stream)) {
     refresh_iters_estimate(ctx);
-    // The synthesis buffers are free once the previous pulse's Gram update,
-    // their last reader, is done (ev_free); the burst after it only reads
-    // the Gram, b and the coefficient vectors.
-    if (ctx->free_stale) e = cudaEventRecord(ctx->ev_free, ctx->stream);
-    ctx->free_stale = false;
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_free, 0);
-    if (e == cudaSuccess) {
-      const int grid = synth_grid(ctx, idle);
-      LaunchOn on(ctx, ctx->side);
-      e = synthesize(ctx, gamma, grid);
+    const int grid = synth_grid(ctx, idle);
+    if (grid > 0) {
+      // The synthesis buffers are free once the previous pulse's Gram
+      // update, their last reader, is done (ev_free); the burst after it
+      // only reads the Gram, b and the coefficient vectors.
+      if (ctx->free_stale) e = cudaEventRecord(ctx->ev_free, ctx->stream);
+      ctx->free_stale = false;
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_free, 0);
+      if (e == cudaSuccess) {
+        LaunchOn on(ctx, ctx->side);
+        e = synthesize(ctx, gamma, grid);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_synth, ctx->side);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_synth, 0);
+    } else {
+      // the product is best run alone on the whole GPU: in order on the
+      // main stream, after the burst (on the side stream its persistent
+      // CTAs would hold SMs that the burst's launches wait for)
+      e = synthesize(ctx, gamma, 0);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_synth, ctx->side);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_synth, 0);
   } else {
     // a captured push leaves no usable ev_free behind
     if (ctx->side) ctx->free_stale = true;
