@@ -459,13 +459,13 @@ cudaError_t batch_launch_data_update(osar_batch* B) {
 
 cudaError_t batch_launch_matvec(osar_batch* B, const void* xt, int gated,
                                 int pstep) {
-  const int grid = std::min(B->nseg, B->sm_count);
-  if (grid <= 0) return cudaSuccess;
+  if (B->nseg <= 0) return cudaSuccess;
   const MvBatch mb{B->seg_scene, B->desc, B->sc, gated, pstep};
   auto go = [&](auto zero) {
     using T = decltype(zero);
     using T2 = typename Vec<T>::T2;
     using C = Mv<T, 1>;
+    const int grid = std::min(B->nseg, C::CTAS * B->sm_count);
     MvArgs<T, 1> a = {};
     a.x[0] = (const T2*)xt;
     a.segpart[0] = (T2*)B->segpart;

@@ -430,8 +430,8 @@ void launch_mv(osar_ctx* ctx, MvArgs<T, R> a, int gated) {
               KEEP_L2_BYTES;
   cudaFuncSetAttribute(k_matvec<T, R, false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-  const unsigned grid =
-      (unsigned)(ctx->nseg < ctx->sm_count ? ctx->nseg : ctx->sm_count);
+  const int slots = C::CTAS * ctx->sm_count;
+  const unsigned grid = (unsigned)(ctx->nseg < slots ? ctx->nseg : slots);
   k_matvec<T, R, false><<<grid, C::THREADS, C::SMEM, ctx->stream>>>(
       (const typename Vec<T>::T2*)ctx->g_hi, a, ctx->segs, ctx->nseg, ctx->nb,
       ctx->scal, gated, matvec_queue(ctx->scal), MvBatch{});

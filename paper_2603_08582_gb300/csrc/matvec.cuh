@@ -90,6 +90,11 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 acc) {
 // by TMA bulk copies issued by one producer thread; CW consumer warps work
 // on every chunk, WC columns each.  R = 2 applies the Gram to two vectors
 // in one pass (the last power step of a pulse and the first FISTA step).
+// The one-vector FP32 pass runs two CTAs per SM (16 consumer warps per SM
+// to hide the latency of the packed-FMA chains), each with a 3-stage ring
+// and one block-partial buffer; the others run one CTA per SM with a ring of
+// up to 6 stages.  The chunking, the warps per CTA and every sum's order
+// are the same in all of them.
 template <typename T, int R>
 struct Mv {
   using T2 = typename Vec<T>::T2;
@@ -102,18 +107,25 @@ struct Mv {
   static constexpr int XI_BYTES = BLK * (int)sizeof(T2);
   static constexpr int XJ_BYTES = CC * (int)sizeof(T2);
   static constexpr int STAGE = G_BYTES + R * (XI_BYTES + XJ_BYTES);
-  static constexpr int RED_BYTES = 2 * R * CW * BLK * (int)sizeof(T2);
+  static constexpr int CTAS = sizeof(T) == 4 && R == 1 ? 2 : 1;  // per SM
+  static constexpr int RB = CTAS == 2 ? 1 : 2;  // block-partial buffers
+  static constexpr int RED_BYTES = RB * R * CW * BLK * (int)sizeof(T2);
   static constexpr int FIXED = RED_BYTES + 16;
   static constexpr int PER_STAGE = STAGE + 2 * 8 + 16;         // + barriers, meta
-  static constexpr int NST = (227 * 1024 - FIXED) / PER_STAGE > 6
-                                 ? 6 : (227 * 1024 - FIXED) / PER_STAGE;  // ring depth
+  // shared memory of one CTA: 228 KB per SM, 1 KB of it reserved per CTA
+  static constexpr int BUDGET = CTAS == 2 ? 228 * 1024 / 2 - 1024 : 227 * 1024;
+  static constexpr int NST = (BUDGET - FIXED) / PER_STAGE > 6
+                                 ? 6 : (BUDGET - FIXED) / PER_STAGE;  // ring depth
   static constexpr int SMEM = NST * STAGE + RED_BYTES + 2 * NST * 8 +
                               NST * 16 + 16;
   static constexpr int THREADS = 32 * (CW + 1);  // producer warp + consumers
 };
-static_assert(Mv<float, 2>::NST >= 4 && Mv<double, 1>::NST >= 4,
+static_assert(Mv<float, 1>::NST >= 3 && Mv<float, 2>::NST >= 4 &&
+                  Mv<double, 1>::NST >= 4,
               "matvec ring too shallow");
-static_assert(Mv<float, 2>::SMEM <= 227 * 1024 && Mv<double, 1>::SMEM <= 227 * 1024,
+static_assert(Mv<float, 1>::SMEM <= Mv<float, 1>::BUDGET &&
+                  Mv<float, 2>::SMEM <= Mv<float, 2>::BUDGET &&
+                  Mv<double, 1>::SMEM <= Mv<double, 1>::BUDGET,
               "matvec ring exceeds shared memory");
 
 // The R right-hand sides of one pass and their partial-sum outputs.
@@ -149,7 +161,7 @@ constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
 // dictionary product.  Every wait is bounded; on a timeout the CTA records
 // the error, stops at the next per-block barrier and drains its copies.
 template <typename T, int R, bool BATCH>
-__global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
+__global__ void __launch_bounds__(Mv<T, R>::THREADS, Mv<T, R>::CTAS)
     k_matvec(const typename Vec<T>::T2* __restrict__ G, const MvArgs<T, R> a,
              const int4* __restrict__ segs, int nseg, int nb,
              DevScalars* __restrict__ sc, int gated,
@@ -163,7 +175,7 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
     if (all) return;  // every vector's solution has met the stop rule
   }
   extern __shared__ __align__(128) uint8_t mv_smem[];
-  T2* red = reinterpret_cast<T2*>(mv_smem + C::NST * C::STAGE);  // [2][R][CW][BLK]
+  T2* red = reinterpret_cast<T2*>(mv_smem + C::NST * C::STAGE);  // [RB][R][CW][BLK]
   uint64_t* full = reinterpret_cast<uint64_t*>(mv_smem + C::NST * C::STAGE +
                                                C::RED_BYTES);
   uint64_t* empty = full + C::NST;
@@ -410,9 +422,9 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
     }
     // Per-block barrier of the consumer warps: the block partial is summed
     // over the warps in a fixed order, and the loop ends here for everyone
-    // at once (end of work or an abort raised before the barrier).
-    named_barrier(1, 32 * C::CW);
-    if (!work || *abort_flag) break;
+    // at once (end of work, or an abort any warp saw before the barrier: the
+    // decision is the barrier's OR over all consumer threads).
+    if (named_barrier_or(1, 32 * C::CW, !work || *abort_flag)) break;
     const int rr = (int)threadIdx.x - 32;
     if (!m.y && rr < R * BLK) {
       const int r = rr / BLK, row = rr % BLK;
@@ -427,7 +439,10 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, 1)
       v.y = si;
       a.tilepart[r][(int64_t)m.x * BLK + row] = v;
     }
-    rp ^= 1;
+    if (C::RB == 2)
+      rp ^= 1;
+    else
+      named_barrier(1, 32 * C::CW);  // one buffer: read before the next block's writes
   }
 }
 
