@@ -151,6 +151,7 @@ struct osar_ctx {
   int64_t iters_seq = 0;           // counts queued so far
   int iters_est = 20;              // FISTA steps expected in a burst
   bool free_stale = false;         // ev_free predates a captured push
+  bool synth_side = false;         // the last push synthesised on `side`
   // osar_get_coeffs_async completion events (OSAR_COPY_SLOTS)
   cudaEvent_t copy_ev[4] = {};
   // pinned staging ring for pulse data (slots of Kp complex)

@@ -420,12 +420,19 @@ bool capturing(cudaStream_t s) {
 
 // Forward block of a pulse (Eq. 4 with the dictionary of Eq. 5): per-pixel
 // phase terms, phase matrix, then A_s = F_s D for dictionary models.
-cudaError_t synthesize(osar_ctx* ctx, const double gamma[3], int grid_cap) {
+cudaError_t synthesize_phase(osar_ctx* ctx, const double gamma[3], int grid_cap) {
   cudaError_t e = launch_pixel_turns(ctx, gamma);
   if (e == cudaSuccess) e = launch_phase(ctx, grid_cap);
-  if (e == cudaSuccess && ctx->dict)
-    e = ctx->prec == OSAR_SPLIT_BF16 ? launch_dict_tc(ctx, grid_cap)
-                                     : launch_dict_simt(ctx);
+  return e;
+}
+cudaError_t synthesize_dict(osar_ctx* ctx, int grid_cap) {
+  if (!ctx->dict) return cudaSuccess;
+  return ctx->prec == OSAR_SPLIT_BF16 ? launch_dict_tc(ctx, grid_cap)
+                                      : launch_dict_simt(ctx);
+}
+cudaError_t synthesize(osar_ctx* ctx, const double gamma[3], int grid_cap) {
+  cudaError_t e = synthesize_phase(ctx, gamma, grid_cap);
+  if (e == cudaSuccess) e = synthesize_dict(ctx, grid_cap);
   return e;
 }
 
@@ -505,16 +512,28 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
     refresh_iters_estimate(ctx);
     const int grid = synth_grid(ctx, idle);
     if (grid > 0) {
-      // The synthesis buffers are free once the previous pulse's Gram
-      // update, their last reader, is done (ev_free); the burst after it
-      // only reads the Gram, b and the coefficient vectors.
-      if (ctx->free_stale) e = cudaEventRecord(ctx->ev_free, ctx->stream);
+      // With a dictionary the phase operand F is read only by the product:
+      // when the previous product ran earlier on the side stream, the phases
+      // go first.  The product's output (and, without a dictionary, the
+      // phase planes themselves) is free once the previous pulse's Gram
+      // update, its last reader, is done (ev_free); so are the phase
+      // buffers when the previous synthesis ran on the main stream.  The
+      // burst after the Gram update only reads the Gram, b and the
+      // coefficient vectors.
+      const bool early = ctx->dict && ctx->synth_side;
+      if (early) {
+        LaunchOn on(ctx, ctx->side);
+        e = synthesize_phase(ctx, gamma, grid);
+      }
+      if (ctx->free_stale && e == cudaSuccess)
+        e = cudaEventRecord(ctx->ev_free, ctx->stream);
       ctx->free_stale = false;
       if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_free, 0);
       if (e == cudaSuccess) {
         LaunchOn on(ctx, ctx->side);
-        e = synthesize(ctx, gamma, grid);
+        e = early ? synthesize_dict(ctx, grid) : synthesize(ctx, gamma, grid);
       }
+      ctx->synth_side = true;
       if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_synth, ctx->side);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_synth, 0);
     } else {
@@ -522,11 +541,13 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
       // main stream, after the burst (on the side stream its persistent
       // CTAs would hold SMs that the burst's launches wait for)
       e = synthesize(ctx, gamma, 0);
+      ctx->synth_side = false;
     }
   } else {
     // a captured push leaves no usable ev_free behind
     if (ctx->side) ctx->free_stale = true;
     e = synthesize(ctx, gamma, 0);
+    ctx->synth_side = false;
   }
   if (e == cudaSuccess) e = launch_data_update(ctx);
   if (e == cudaSuccess)

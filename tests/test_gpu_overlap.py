@@ -109,3 +109,25 @@ def test_async_coefficient_reads_in_a_pipelined_loop():
         assert np.array_equal(a, b)
     with pytest.raises(osar.OsarError):
         g.wait_coeffs(osar.COPY_SLOTS)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fp64"])
+def test_overlap_alternating_main_and_side_synthesis(prec):
+    # A host wait leaves the main stream idle, so the next push synthesises
+    # in order on the main stream; the push after it goes to the side stream
+    # again and must not start its phases while that synthesis still reads
+    # the phase buffers.
+    w = _workload()
+    problem = build_problem(w)
+    ref, _ = _run(w, prec, problem, overlap=False)
+    cfg = gpu_config(w, prec)
+    cfg.overlap_synthesis = 1
+    g = osar.Osar(cfg)
+    track, _, _, data = problem
+    for s in range(track.shape[0]):
+        g.push_pulse(track[s], data[s])
+        g.iterate(12, 0.0, want_count=False)
+        if s % 3 == 1:
+            g.synchronize()
+    g.synchronize()
+    _same(ref, g)
