@@ -60,6 +60,10 @@ def parse():
                          "product, bit 1 Gram update (0: one SM per tile)")
     ap.add_argument("--synth-ctas", type=int, default=0,
                     help="SMs for the overlapped dictionary product (0: auto)")
+    ap.add_argument("--defer-gram", type=int, choices=[0, 1], default=0,
+                    help="1: each pulse's Gram update runs on the side stream "
+                         "beside its power steps and burst, which add the "
+                         "pulse's block term to G_{n-1} x")
     ap.add_argument("--workload", choices=["c2", "probe8k", "probe_dict"],
                     default="c2",
                     help="c2: the 128x128 headline workload; probe8k: a "
@@ -207,7 +211,7 @@ def workload(name="c2"):
 
 
 def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
-             fuse=True):
+             fuse=True, defer=False):
     from paper_2603_08582_gb300 import osar
     gauss = w.dictionary == "gaussian"
     cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
@@ -217,7 +221,9 @@ def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
                            dict_seed=w.dict_seed, lam=w.lambda_rel,
                            stream=stream, overlap_synthesis=overlap,
                            synth_ctas=synth_ctas, tc_pairs=tc_pairs,
-                           fuse_first_step=fuse)
+                           fuse_first_step=fuse,
+                           defer_gram=(defer and overlap and gauss
+                                       and precision == "split_bf16"))
     return osar.Osar(cfg)
 
 
@@ -252,7 +258,8 @@ def run_ours(args):
     W, K = args.warmup, args.steps
     stream = torch.cuda.Stream()
     ov = dict(overlap=not args.no_overlap, synth_ctas=args.synth_ctas,
-              tc_pairs=args.tc_pairs, fuse=not args.no_fuse)
+              tc_pairs=args.tc_pairs, fuse=not args.no_fuse,
+              defer=bool(args.defer_gram) and not args.no_overlap)
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
     total = W + K + 1
     track, data = pulse_data(ctx, w, total)
@@ -425,6 +432,7 @@ def run_ours(args):
                    "tc_pairs": {0: "off", 1: "dictionary product", 2: "Gram update",
                                 3: "dictionary product and Gram update"}[args.tc_pairs & 3],
                    "fused_first_step": not args.no_fuse,
+                   "deferred_gram_update": bool(ov["defer"]),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (packed Gram 4.3 GB streamed per step)"},
         "clocks": clocks,

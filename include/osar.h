@@ -142,6 +142,20 @@ typedef struct {
      is copied at create. */
   int32_t n_lambdas;
   const double* lambda_list;
+  /* SPLIT_BF16 with a dictionary, overlap_synthesis = 1, one lambda and
+     n_freq <= 2048.  1 takes the Gram update off the critical path: the
+     power steps and FISTA steps of pulse n apply G_n x as
+     G_{n-1} x + A_n^H (A_n x) (two reads of the K x M block A_n besides the
+     pass over G_{n-1}) while the side stream forms G_n = G_{n-1} + A_n^H A_n
+     into a second Gram buffer; forward blocks alternate between two block
+     buffers, and the next push swaps the Gram buffers.  The Gram is bitwise
+     the one of 0; the iterates agree with 0 to rounding.  Needs a second
+     Gram and block in device memory.  osar_get_gram*, osar_save,
+     osar_gram_apply* and osar_unroll_grad first wait for the pending update
+     (the rest of that pulse's burst then reads G_n).  A push while
+     cuda_stream is being captured returns OSAR_E_STATE.  0: the update runs
+     on cuda_stream before the power steps. */
+  int32_t defer_gram;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
@@ -149,7 +163,7 @@ typedef struct {
    30 / 4 power steps, margin 0.01, carried momentum, compensated = 1,
    overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
    (both tensor-core products on SM pairs), fuse_first_step = 1,
-   n_lambdas = 1. */
+   n_lambdas = 1, defer_gram = 0. */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128

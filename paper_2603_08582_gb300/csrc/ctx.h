@@ -59,7 +59,7 @@ inline unsigned* matvec_queue(DevScalars* s) {
 
 enum KernelClass {
   KCL_PHASE = 0, KCL_DICT = 1, KCL_GRAM = 2, KCL_BUPD = 3, KCL_MATVEC = 4,
-  KCL_FIN = 5, KCL_POWFIN = 6, KCL_SCALAR = 7, KCL_COUNT = 8
+  KCL_FIN = 5, KCL_POWFIN = 6, KCL_CORR = 7, KCL_COUNT = 8
 };
 
 struct ProfEvent {
@@ -152,6 +152,19 @@ struct osar_ctx {
   int iters_est = 20;              // FISTA steps expected in a burst
   bool free_stale = false;         // ev_free predates a captured push
   bool synth_side = false;         // the last push synthesised on `side`
+  // deferred Gram update (defer_gram): G_n forms on `side` into the second
+  // buffer while pulse n's passes read G_{n-1} and add A_n^H A_n x
+  void* gn_hi = nullptr;               // the other Gram buffer
+  __nv_bfloat162* gn_lo = nullptr;
+  __nv_bfloat16* Apl_alt = nullptr;    // the other forward-block buffer
+  CUtensorMap map_alt_rows1;           // Apl_alt, box (KC, 128, 1)
+  CUtensorMap map_alt_rows2;           // Apl_alt, box (KC, 128, 2)
+  cudaEvent_t ev_gram = nullptr;       // side: the pending Gram update done
+  cudaEvent_t ev_mark[2] = {};         // main: all work before push n (n % 2)
+  bool gram_pending = false;           // g_hi holds G_{n-1}, gn_hi gets G_n
+  float2* corr = nullptr;              // A_n^H A_n x per partial set (2 x Mp)
+  float2* corr_u = nullptr;            // A_n x: nb block partials, then the sum
+  unsigned* corr_tick = nullptr;       // last-CTA ticket of the A_n x sums
   // osar_get_coeffs_async completion events (OSAR_COPY_SLOTS)
   cudaEvent_t copy_ev[4] = {};
   // pinned staging ring for pulse data (slots of Kp complex)
@@ -185,9 +198,22 @@ struct osar_ctx {
 
 namespace osar {
 
+// ---- deferred Gram update ---------------------------------------------------
+// the main stream waits for a pending Gram update, whose result its passes
+// then read directly (no-op when none is pending)
+cudaError_t settle_gram(osar_ctx* ctx);
+
 // ---- launch bracketing for the per-kernel profile -------------------------
 void prof_begin(osar_ctx* ctx, int kind, ProfEvent* ev);
 void prof_end(osar_ctx* ctx, ProfEvent* ev);
+
+// ---- k_defer.cu -------------------------------------------------------------
+// corr[set] = A_n^H (A_n x) for the pending forward block (nothing when no
+// Gram update is pending); gate: skip when that flag is set
+cudaError_t launch_corr(osar_ctx* ctx, const void* xt, int set,
+                        const int32_t* gate);
+// the correction a finalize adds for partial set `set`, or nullptr
+const float2* corr_set(const osar_ctx* ctx, int set);
 
 // ---- k_phase.cu -------------------------------------------------------------
 cudaError_t launch_pixel_turns(osar_ctx* ctx, const double gamma[3]);
@@ -206,7 +232,10 @@ bool make_tensor_maps(osar_ctx* ctx, std::string* err);
 // follows is a short full-grid kernel)
 cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap);
 int dict_slices(int np);
-cudaError_t launch_gram_tc(osar_ctx* ctx);
+// G += A^H A in place, or, with dst_hi set, dst = G + A^H A (G unchanged);
+// grid_cap > 0: at most that many SMs
+cudaError_t launch_gram_tc(osar_ctx* ctx, void* dst_hi = nullptr,
+                           __nv_bfloat162* dst_lo = nullptr, int grid_cap = 0);
 
 // ---- k_fista.cu ------------------------------------------------------------
 cudaError_t launch_data_update(osar_ctx* ctx);

@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(FIN_THREADS)
                      const double2* __restrict__ b, double2* __restrict__ c,
                      double2* __restrict__ z, T2* __restrict__ zt,
                      double2* __restrict__ part, DevScalars* sc,
-                     DevScalars* gs, int count_pass) {
+                     DevScalars* gs, int count_pass,
+                     const float2* __restrict__ corr) {
   // sc: this solution's scalars; gs: the shared ones (tau, tol, passes)
   if (sc->converged) return;
   __shared__ double sh[3];  // tau, alpha, beta
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
     sh[2] = (t - 1.0) / t_next;
   }
   const int K = blockIdx.x, i = threadIdx.x, idx = K * BLK + i;
-  const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
+  const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K, corr);
   double p0 = 0.0, p1 = 0.0;
   if (i < BLK) {
     const double tau = sh[0], alpha = sh[1], beta = sh[2];
@@ -122,9 +123,9 @@ __global__ void __launch_bounds__(FIN_THREADS)
                      const int* __restrict__ seg_begin, int nb,
                      const double2* __restrict__ v, double2* __restrict__ w,
                      double2* __restrict__ part, DevScalars* sc, int last_step,
-                     double margin) {
+                     double margin, const float2* __restrict__ corr) {
   const int K = blockIdx.x, i = threadIdx.x, idx = K * BLK + i;
-  const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
+  const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K, corr);
   double p0 = 0.0, p1 = 0.0;
   if (i < BLK) {
     w[idx] = y;
@@ -473,8 +474,10 @@ void launch_mv(osar_ctx* ctx, const void* xt, void* segp, void* tilep,
   launch_mv<T, 1>(ctx, a, gated);
 }
 
-// Launch the matvec on the working-precision copy of a vector.
+// Launch the matvec on the working-precision copy of a vector (and, with a
+// deferred Gram update pending, the pending block's term into set 0).
 void matvec(osar_ctx* ctx, const void* xt, int gated) {
+  launch_corr(ctx, xt, 0, gated ? stop_flag(ctx, 0) : nullptr);
   ProfEvent ev;
   prof_begin(ctx, KCL_MATVEC, &ev);
   if (ctx->prec == OSAR_FP64)
@@ -551,6 +554,8 @@ cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
       // the burst that follows starts from z = c_hat: apply the Gram to it
       // in the same pass as the last power step
       cudaError_t e = launch_burst_begin(ctx);
+      if (e == cudaSuccess) e = launch_corr(ctx, ctx->vt, 0, nullptr);
+      if (e == cudaSuccess) e = launch_corr(ctx, ctx->zt, 1, nullptr);
       if (e != cudaSuccess) return e;
       ProfEvent ev;
       prof_begin(ctx, KCL_MATVEC, &ev);
@@ -574,14 +579,14 @@ cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
       k_power_finalize<double2, double><<<nb, FIN_THREADS, 0, ctx->stream>>>(
           (const double2*)ctx->segpart, (const double2*)ctx->tilepart,
           ctx->seg_begin, ctx->nb, ctx->v, ctx->w, ctx->part, ctx->scal, last,
-          ctx->cfg.lipschitz_margin);
+          ctx->cfg.lipschitz_margin, nullptr);
       k_power_normalize<double2><<<nb, BLK, 0, ctx->stream>>>(
           ctx->w, ctx->v, (double2*)ctx->vt, ctx->Mp, ctx->scal);
     } else {
       k_power_finalize<float2, float><<<nb, FIN_THREADS, 0, ctx->stream>>>(
           (const float2*)ctx->segpart, (const float2*)ctx->tilepart,
           ctx->seg_begin, ctx->nb, ctx->v, ctx->w, ctx->part, ctx->scal, last,
-          ctx->cfg.lipschitz_margin);
+          ctx->cfg.lipschitz_margin, corr_set(ctx, 0));
       k_power_normalize<float2><<<nb, BLK, 0, ctx->stream>>>(
           ctx->w, ctx->v, (float2*)ctx->vt, ctx->Mp, ctx->scal);
     }
@@ -649,7 +654,8 @@ void fista_finalize(osar_ctx* ctx, int l, int s, int count_pass) {
   k_fista_finalize<T2, Acc><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
       (const T2*)seg_set(ctx, s), (const T2*)tile_set(ctx, s), ctx->seg_begin,
       ctx->nb, ctx->b, ctx->c + l * Mp, ctx->z + l * Mp, (T2*)ctx->zt + l * Mp,
-      ctx->part, ctx->scal + l, ctx->scal, count_pass);
+      ctx->part, ctx->scal + l, ctx->scal, count_pass,
+      ctx->n_lam == 1 ? corr_set(ctx, s) : nullptr);
 }
 
 }  // namespace

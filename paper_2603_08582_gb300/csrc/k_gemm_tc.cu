@@ -99,8 +99,10 @@ struct TcParams {
   float2* part;    // mode 0: [slice][rows][part_ld] partial sums
   int part_ld;
   int64_t part_slice;
-  float2* g_hi;
+  float2* g_hi;          // the Gram written
   __nv_bfloat162* g_lo;  // compensation word, bf16 (re, im), or NULL
+  const float2* gs_hi;   // the Gram read (g_hi for an update in place)
+  const __nv_bfloat162* gs_lo;
   int nb;
   int* err;
 };
@@ -391,8 +393,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int64_t off = piece_off(t, pc);
       uint8_t* dst = slots + b * G_SLOT;
       mbar_expect_tx(&gf[b], bytes);
-      bulk_load(dst, p.g_hi + off, G_PIECE_HI, &gf[b]);
-      if (comp) bulk_load(dst + G_PIECE_HI, p.g_lo + off, G_PIECE_LO, &gf[b]);
+      bulk_load(dst, p.gs_hi + off, G_PIECE_HI, &gf[b]);
+      if (comp) bulk_load(dst + G_PIECE_HI, p.gs_lo + off, G_PIECE_LO, &gf[b]);
     };
     uint32_t issued[2] = {0, 0};
     if (loader && unit < p.n_tiles) {
@@ -502,12 +504,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       __nv_bfloat162 l0[16], l1[16];
       float2* gh = nullptr;
       __nv_bfloat162* gl = nullptr;
+      const float2* src_hi = nullptr;
+      const __nv_bfloat162* src_lo = nullptr;
       if (p.mode == 1 && store) {
         const int64_t blk = PAIR ? packed_block(ti, tj, p.nb) : (int64_t)tile.z;
         const int64_t off = blk * (BLK * BLK) + (int64_t)(colh * 64) * BLK + row;
         gh = p.g_hi + off;
         gl = comp ? p.g_lo + off : nullptr;
-        load_piece(gh, gl, h0, l0, comp);  // prefetch before the MMAs finish
+        src_hi = p.gs_hi + off;
+        src_lo = comp ? p.gs_lo + off : nullptr;
+        load_piece(src_hi, src_lo, h0, l0, comp);  // prefetch before the MMAs finish
       }
       if (!mbar_wait_bounded(&tfull[acc], aph, abort_flag, p.err,
                              WAIT_LIMIT_NS)) {
@@ -526,9 +532,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (p.mode == 1 && store && pc < 3) {
           const int64_t nxt = (int64_t)(16 * (pc + 1)) * BLK;
           if (pc & 1)
-            load_piece(gh + nxt, comp ? gl + nxt : nullptr, h0, l0, comp);
+            load_piece(src_hi + nxt, comp ? src_lo + nxt : nullptr, h0, l0, comp);
           else
-            load_piece(gh + nxt, comp ? gl + nxt : nullptr, h1, l1, comp);
+            load_piece(src_hi + nxt, comp ? src_lo + nxt : nullptr, h1, l1, comp);
         }
         tmem_wait_ld();
         if (!store) continue;
@@ -733,6 +739,10 @@ bool make_tensor_maps(osar_ctx* ctx, std::string* err) {
     return false;
   if (!encode_planes(&ctx->map_a_rows2, ctx->Apl, ctx->Kp, ctx->Mp, 6, 2, err))
     return false;
+  if (ctx->Apl_alt &&
+      (!encode_planes(&ctx->map_alt_rows1, ctx->Apl_alt, ctx->Kp, ctx->Mp, 6, 1, err) ||
+       !encode_planes(&ctx->map_alt_rows2, ctx->Apl_alt, ctx->Kp, ctx->Mp, 6, 2, err)))
+    return false;
   if (ctx->dict) {
     if (!encode_planes(&ctx->map_d_rows1, ctx->Dpl, ctx->Np, ctx->Mp, 4, 1, err))
       return false;
@@ -784,7 +794,8 @@ cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_tc(osar_ctx* ctx) {
+cudaError_t launch_gram_tc(osar_ctx* ctx, void* dst_hi, __nv_bfloat162* dst_lo,
+                           int grid_cap) {
   const bool pairs = (ctx->cfg.tc_pairs & 2) != 0;
   TcParams p = {};
   p.tiles = pairs ? ctx->gram_pairs : ctx->gram_tiles;
@@ -795,13 +806,15 @@ cudaError_t launch_gram_tc(osar_ctx* ctx) {
   p.b_lo = 3;
   p.neg_second = 0;
   p.mode = 1;
-  p.g_hi = (float2*)ctx->g_hi;
-  p.g_lo = ctx->g_lo;
+  p.gs_hi = (const float2*)ctx->g_hi;
+  p.gs_lo = ctx->g_lo;
+  p.g_hi = dst_hi ? (float2*)dst_hi : (float2*)ctx->g_hi;
+  p.g_lo = dst_hi ? dst_lo : ctx->g_lo;
   p.nb = ctx->nb;
   p.err = &ctx->scal->error;
   return launch_tc(ctx, ctx->map_a_rows1,
                    pairs ? ctx->map_a_rows1 : ctx->map_a_rows2, p, KCL_GRAM,
-                   pairs, 0);
+                   pairs, grid_cap);
 }
 
 bool encode_plane_map(CUtensorMap* m, void* base, int cols, int rows,
@@ -826,6 +839,8 @@ cudaError_t launch_gram_tc_tiles(cudaStream_t st, int sm_count,
   p.mode = 1;
   p.g_hi = g_hi;
   p.g_lo = g_lo;
+  p.gs_hi = g_hi;
+  p.gs_lo = g_lo;
   p.err = err;
   return launch_tc_grid<false>(st, sm_count, 0, m1, m2, p, 0);
 }

@@ -73,7 +73,8 @@ extern "C" osar_status osar_gram_apply_static(osar_ctx* ctx,
     return OSAR_E_INVALID;
   }
   void* scratch = nullptr;
-  cudaError_t e = scratch_address(&scratch);
+  cudaError_t e = osar::settle_gram(ctx);  // a deferred update: its result
+  if (e == cudaSuccess) e = scratch_address(&scratch);
   if (e == cudaSuccess)
     e = osar::launch_gram_apply_scratch(
         ctx, static_cast<const double2*>(x_dev_c128),

@@ -452,13 +452,15 @@ constexpr int FIN_THREADS = FIN_GROUPS * BLK;  // 1024
 // y_K = sum of the segment partials of block column K and the block partials
 // of (K, J), J > K, accumulated in Acc (FP32 on the FP32-Gram paths).  The
 // partial list is split over FIN_GROUPS thread groups and the group sums are
-// combined in a fixed order.  Called by every thread; threads < BLK get the
-// sum for coefficient threadIdx.x.
+// combined in a fixed order; a deferred Gram update's term (corr, FP32
+// paths) is added last.  Called by every thread; threads < BLK get the sum
+// for coefficient threadIdx.x.
 template <typename T2, typename Acc>
 __device__ __forceinline__ double2 gather_row(const T2* __restrict__ segpart,
                                               const T2* __restrict__ tilepart,
                                               const int* __restrict__ seg_begin,
-                                              int nb, int K) {
+                                              int nb, int K,
+                                              const float2* __restrict__ corr = nullptr) {
   __shared__ Acc red_r[FIN_GROUPS][BLK], red_i[FIN_GROUPS][BLK];
   const int g = threadIdx.x / BLK, i = threadIdx.x % BLK;
   const int s0 = seg_begin[K], nseg = seg_begin[K + 1] - s0;
@@ -482,6 +484,11 @@ __device__ __forceinline__ double2 gather_row(const T2* __restrict__ segpart,
     for (int k = 0; k < FIN_GROUPS; ++k) {
       sr += red_r[k][i];
       si += red_i[k][i];
+    }
+    if (corr) {
+      const float2 cv = corr[K * BLK + i];
+      sr += (Acc)cv.x;
+      si += (Acc)cv.y;
     }
     y = make_double2((double)sr, (double)si);
   }

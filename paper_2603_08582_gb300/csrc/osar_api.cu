@@ -68,7 +68,8 @@ void free_all(osar_ctx* ctx) {
                   ctx->Apl, ctx->Fpl, ctx->Dpl, ctx->sim_rho, ctx->sim_nz,
                   ctx->sim_idx, ctx->sim_d, ctx->dict_part, ctx->gram_pairs,
                   ctx->dict_pairs, ctx->segpart2, ctx->tilepart2,
-                  ctx->segpart_x, ctx->tilepart_x};
+                  ctx->segpart_x, ctx->tilepart_x, ctx->gn_hi, ctx->gn_lo,
+                  ctx->Apl_alt, ctx->corr, ctx->corr_u, ctx->corr_tick};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
@@ -76,7 +77,8 @@ void free_all(osar_ctx* ctx) {
   for (int i = 0; i < RING; ++i)
     if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);
   if (ctx->h_iters) cudaFreeHost(ctx->h_iters);
-  for (cudaEvent_t ev : {ctx->ev_free, ctx->ev_synth})
+  for (cudaEvent_t ev : {ctx->ev_free, ctx->ev_synth, ctx->ev_gram,
+                         ctx->ev_mark[0], ctx->ev_mark[1]})
     if (ev) cudaEventDestroy(ev);
   for (cudaEvent_t ev : ctx->ev_iters)
     if (ev) cudaEventDestroy(ev);
@@ -141,6 +143,13 @@ osar_status validate(const osar_config* c, std::string* why) {
       if (!is_finite(c->lambda_list[l]) || c->lambda_list[l] < 0)
         return *why = "lambda_list values must be finite and >= 0", OSAR_E_INVALID;
   }
+  if (c->defer_gram != 0 && c->defer_gram != 1)
+    return *why = "defer_gram must be 0 or 1", OSAR_E_INVALID;
+  if (c->defer_gram &&
+      (c->precision != OSAR_SPLIT_BF16 || c->dict_kind == OSAR_DICT_IDENTITY ||
+       !c->overlap_synthesis || c->n_lambdas != 1 || c->n_freq > 2048))
+    return *why = "defer_gram needs SPLIT_BF16, a dictionary, overlap_synthesis, "
+                  "one lambda and n_freq <= 2048", OSAR_E_INVALID;
   return OSAR_OK;
 }
 
@@ -315,6 +324,15 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
       AL(ctx->D, cplx * Mp * Np);
     }
   }
+  if (cfg->defer_gram) {
+    // second Gram and forward-block buffers, the pending block's term
+    AL(ctx->gn_hi, cplx * bb * ctx->nblk);
+    if (ctx->g_lo) AL(ctx->gn_lo, 4 * bb * ctx->nblk);
+    AL(ctx->Apl_alt, 2 * 6 * Mp * Kp);
+    AL(ctx->corr, 8 * 2 * Mp);
+    AL(ctx->corr_u, 8 * ((int64_t)ctx->nb + 1) * Kp);
+    AL(ctx->corr_tick, sizeof(unsigned));
+  }
   AL(ctx->sim_rho, 16 * Np);
   AL(ctx->sim_nz, 16 * Mp);
   AL(ctx->sim_idx, 4 * Mp);
@@ -338,6 +356,11 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess)
       e = cudaMallocHost((void**)&ctx->h_iters, sizeof(int32_t) * osar_ctx::ITERS_RING);
+    if (cfg->defer_gram)
+      for (cudaEvent_t* ev : {&ctx->ev_gram, &ctx->ev_mark[0], &ctx->ev_mark[1]}) {
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(*ev, ctx->stream);
+      }
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "side stream"));
   }
 
@@ -497,6 +520,80 @@ int synth_grid(const osar_ctx* ctx, bool main_idle) {
   return best_g;
 }
 
+// SMs for the side stream in the deferred mode, where this pulse's Gram
+// update and the next pulse's synthesis run there beside this pulse's power
+// steps and burst: the model of synth_grid with both products on the side
+// (the Gram update at 1.05e13 f/s per SM, its measured rate), the pass
+// reading the pending block twice besides the Gram, and no option of running
+// the products alone.
+int defer_grid(const osar_ctx* ctx) {
+  if (ctx->cfg.synth_ctas > 0) return std::min(ctx->cfg.synth_ctas, ctx->sm_count);
+  constexpr double kDictRate = 1.2e13, kGramRate = 1.05e13;  // f/s per SM
+  constexpr double kHbm = 6.8e12, kSmBw = 105e9, kContention = 1.15;  // B/s
+  const double dict_f = 24.0 * ctx->Kp * (double)ctx->Np * ctx->Mp;
+  const double gram_f = 3.0 * 2.0 * BLK * 2.0 * BLK * 2.0 * ctx->Kp * (double)ctx->nblk;
+  const double side = dict_f / kDictRate + gram_f / kGramRate;  // SM-seconds
+  const double bytes =
+      (double)ctx->nblk * BLK * BLK * 8.0 + 2.0 * 8.0 * ctx->Mp * ctx->Kp;
+  const double pass = bytes / kHbm;
+  const int power = ctx->n <= 1 ? ctx->cfg.power_iters_first : ctx->cfg.power_iters;
+  const double passes = power + ctx->iters_est;
+  const int S = ctx->sm_count;
+  double best = 0.0;
+  int best_g = S / 2;
+  for (int g = 16; g <= S - 16; g += 4) {
+    const double t_side = side / g;
+    const double t_pass = std::max(pass, bytes / ((S - g) * kSmBw)) * kContention;
+    const double beside = t_side / t_pass;  // passes made while the side works
+    const double t = passes <= beside ? t_side : t_side + (passes - beside) * pass;
+    if (best == 0.0 || t < best) {
+      best = t;
+      best_g = g;
+    }
+  }
+  return best_g;
+}
+
+// Deferred push (defer_gram).  Pulse n's passes read G_{n-1} plus the term
+// of A_n; the side stream forms A_n (after the main stream is done with the
+// block buffer's previous content, A_{n-2}) and then G_n = G_{n-1} + A_n^H
+// A_n into the other Gram buffer (after the main stream is done with pulse
+// n-1's passes, the last readers of G_{n-2} there).  The next push makes
+// the main stream wait for G_n and swaps the buffers.
+osar_status push_deferred(osar_ctx* ctx, const double gamma[3]) {
+  refresh_iters_estimate(ctx);
+  const int par = ctx->n & 1;
+  cudaError_t e = settle_gram(ctx);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_mark[par], ctx->stream);
+  std::swap(ctx->Apl, ctx->Apl_alt);
+  std::swap(ctx->map_a_rows1, ctx->map_alt_rows1);
+  std::swap(ctx->map_a_rows2, ctx->map_alt_rows2);
+  const int grid = defer_grid(ctx);
+  if (e == cudaSuccess) {
+    LaunchOn on(ctx, ctx->side);
+    e = cudaStreamWaitEvent(ctx->side, ctx->ev_mark[par ^ 1], 0);
+    if (e == cudaSuccess) e = synthesize(ctx, gamma, grid);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_synth, ctx->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_mark[par], 0);
+    if (e == cudaSuccess) e = launch_gram_tc(ctx, ctx->gn_hi, ctx->gn_lo, grid);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_gram, ctx->side);
+  }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_synth, 0);
+  if (e == cudaSuccess) e = launch_data_update(ctx);
+  ctx->gram_pending = true;
+  ctx->synth_side = true;
+  ctx->n += 1;
+  ctx->fresh = true;
+  ctx->first_ready = false;
+  if (e == cudaSuccess)
+    e = launch_power_steps(ctx,
+                           ctx->n == 1 ? ctx->cfg.power_iters_first
+                                       : ctx->cfg.power_iters,
+                           ctx->cfg.fuse_first_step != 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_push_pulse");
+  return OSAR_OK;
+}
+
 // True when every launch on the main stream has finished (the caller waited
 // for the last burst before pushing).
 bool main_idle(osar_ctx* ctx) {
@@ -508,6 +605,12 @@ bool main_idle(osar_ctx* ctx) {
 // idle: main_idle() taken before the pulse's data copy was queued.
 osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
   cudaError_t e = cudaSuccess;
+  if (ctx->cfg.defer_gram) {
+    if (capturing(ctx->stream))
+      return fail(ctx, OSAR_E_STATE,
+                  "defer_gram: a push cannot be captured into a CUDA graph");
+    return push_deferred(ctx, gamma);
+  }
   if (ctx->side && !capturing(ctx->stream)) {
     refresh_iters_estimate(ctx);
     const int grid = synth_grid(ctx, idle);
@@ -570,6 +673,18 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
 
 namespace osar {
 
+cudaError_t settle_gram(osar_ctx* ctx) {
+  if (!ctx->gram_pending) return cudaSuccess;
+  const cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->ev_gram, 0);
+  if (e != cudaSuccess) return e;
+  std::swap(ctx->g_hi, ctx->gn_hi);
+  std::swap(ctx->g_lo, ctx->gn_lo);
+  ctx->gram_pending = false;
+  // a fused first step's pass lacks the block's term: the step runs its own
+  ctx->first_ready = false;
+  return cudaSuccess;
+}
+
 void prof_begin(osar_ctx* ctx, int kind, ProfEvent* ev) {
   ev->kind = -1;
   if (!ctx->prof_on) return;
@@ -625,6 +740,7 @@ void osar_config_default(osar_config* c) {
   c->fuse_first_step = 1;
   c->n_lambdas = 1;
   c->lambda_list = nullptr;
+  c->defer_gram = 0;
 }
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
@@ -802,6 +918,7 @@ osar_status osar_get_gram(osar_ctx* ctx, double* out_c128) {
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!out_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_gram: NULL");
+  CK(ctx, settle_gram(ctx));
   const int64_t M = ctx->M;
   int64_t rows = (int64_t)(256ll << 20) / (16 * M);
   if (rows < 1) rows = 1;
@@ -832,6 +949,7 @@ osar_status osar_get_gram_entries(osar_ctx* ctx, const int32_t* rows,
   if (count < 0 || (count > 0 && (!rows || !cols || !out_c128)))
     return fail(ctx, OSAR_E_INVALID, "osar_get_gram_entries: bad arguments");
   if (count == 0) return OSAR_OK;
+  CK(ctx, settle_gram(ctx));
   std::vector<int2> rc(count);
   for (int q = 0; q < count; ++q) {
     if (rows[q] < 0 || rows[q] >= ctx->M || cols[q] < 0 || cols[q] >= ctx->M)
@@ -871,6 +989,7 @@ osar_status osar_gram_apply(osar_ctx* ctx, const double* x_c128,
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!x_c128 || !y_c128) return fail(ctx, OSAR_E_INVALID, "osar_gram_apply: NULL");
+  CK(ctx, settle_gram(ctx));
   CK(ctx, cudaMemsetAsync(ctx->xtmp, 0, sizeof(double2) * ctx->Mp, ctx->stream));
   CK(ctx, cudaMemcpyAsync(ctx->xtmp, x_c128, sizeof(double2) * ctx->M,
                           cudaMemcpyHostToDevice, ctx->stream));
@@ -920,6 +1039,7 @@ osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
   if (st != OSAR_OK) return st;
   if (ctx->n == 0)
     return fail(ctx, OSAR_E_STATE, "osar_unroll_grad before the first pulse");
+  CK(ctx, settle_gram(ctx));
   if (steps < 1 || ckpt_every < 1 || !is_finite(tau) || tau <= 0 ||
       !is_finite(lambda) || lambda < 0 || !is_finite(t0) || t0 < 1 ||
       !c0_c128 || !c_true_c128)
@@ -1048,6 +1168,7 @@ osar_status osar_save(osar_ctx* ctx, const char* path) {
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!path) return fail(ctx, OSAR_E_INVALID, "osar_save: NULL path");
+  CK(ctx, settle_gram(ctx));
   FILE* f = fopen(path, "wb");
   if (!f) return fail(ctx, OSAR_E_IO, std::string("cannot open ") + path);
   CkptHeader h = {};

@@ -26,7 +26,7 @@ PRECISIONS = {"fp64": OSAR_FP64, "fp32": OSAR_FP32, "split_bf16": OSAR_SPLIT_BF1
 
 KERNEL_CLASSES = {"phase": 0, "dict_gemm": 1, "gram_gemm": 2, "data_update": 3,
                   "matvec": 4, "fista_finalize": 5, "power_finalize": 6,
-                  "scalar": 7}
+                  "block_term": 7}
 
 # Symbols declared in include/osar.h (checked by the CPU test suite).
 EXPORTS = [
@@ -65,6 +65,7 @@ class OsarConfig(C.Structure):
         ("overlap_synthesis", C.c_int32), ("synth_ctas", C.c_int32),
         ("tc_pairs", C.c_int32), ("fuse_first_step", C.c_int32),
         ("n_lambdas", C.c_int32), ("lambda_list", C.c_void_p),
+        ("defer_gram", C.c_int32),
     ]
 
 
@@ -162,7 +163,8 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
                 lam=0.05, lambda_relative=True, power_iters_first=30,
                 power_iters=4, lipschitz_margin=0.01, restart_momentum=False,
                 compensated=True, stream=None, overlap_synthesis=True,
-                synth_ctas=0, tc_pairs=3, fuse_first_step=True, lambdas=None):
+                synth_ctas=0, tc_pairs=3, fuse_first_step=True, lambdas=None,
+                defer_gram=False):
     """Build an osar_config.  dictionary: None (identity), "gaussian"
     (seeded Philox atoms, needs n_atoms) or an N x M complex array."""
     cfg = default_config()
@@ -194,6 +196,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
     cfg.synth_ctas = int(synth_ctas)
     cfg.tc_pairs = int(tc_pairs)  # bit 0 dictionary product, bit 1 Gram update
     cfg.fuse_first_step = 1 if fuse_first_step else 0
+    cfg.defer_gram = 1 if defer_gram else 0
     if lambdas is not None and len(lambdas) > 1:
         # lambda path: one solution per value (relative or absolute like lam)
         lv = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))

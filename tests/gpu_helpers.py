@@ -11,7 +11,8 @@ from tests.helpers import build_problem, oracle_config
 
 def gpu_config(w, precision, lam=0.05, lambda_relative=True,
                power_iters_first=30, power_iters=4, margin=0.01,
-               restart_momentum=False, compensated=True, host_dictionary=None):
+               restart_momentum=False, compensated=True, host_dictionary=None,
+               defer_gram=False):
     if w.dictionary == "gaussian" and host_dictionary is None:
         dictionary, n_atoms = "gaussian", w.m_atoms
     elif host_dictionary is not None:
@@ -24,12 +25,13 @@ def gpu_config(w, precision, lam=0.05, lambda_relative=True,
         dict_seed=w.dict_seed, lam=lam, lambda_relative=lambda_relative,
         power_iters_first=power_iters_first, power_iters=power_iters,
         lipschitz_margin=margin, restart_momentum=restart_momentum,
-        compensated=compensated)
+        compensated=compensated, defer_gram=defer_gram)
 
 
 def run_pair(w, precision, steps, tol=0.0, pulses=None, lam=0.05,
              lambda_relative=True, restart_momentum=False, per_pulse=None,
-             compensated=True, problem=None, host_dictionary=None):
+             compensated=True, problem=None, host_dictionary=None,
+             defer_gram=False):
     """Push the same pulses through the oracle and the GPU; call
     per_pulse(s, oracle, gpu) after each burst.  Returns (oracle, gpu)."""
     track, dic, c_true, data = problem if problem is not None else build_problem(w)
@@ -41,7 +43,8 @@ def run_pair(w, precision, steps, tol=0.0, pulses=None, lam=0.05,
                                lambda_relative=lambda_relative,
                                restart_momentum=restart_momentum,
                                compensated=compensated,
-                               host_dictionary=host_dictionary))
+                               host_dictionary=host_dictionary,
+                               defer_gram=defer_gram))
     for s in range(P):
         of.push_pulse(track[s], data[s])
         gpu.push_pulse(track[s], data[s])

@@ -49,6 +49,26 @@ def test_config_defaults_and_layout(lib):
     assert cfg.overlap_synthesis == 1 and cfg.synth_ctas == 0
     assert cfg.tc_pairs == 3 and cfg.fuse_first_step == 1
     assert cfg.n_lambdas == 1 and cfg.lambda_list is None
+    assert cfg.defer_gram == 0
+
+
+@pytest.mark.parametrize("changes", [
+    {"defer_gram": 2},
+    {"defer_gram": 1},                                   # FP64, identity dictionary
+    {"defer_gram": 1, "precision": osar.OSAR_SPLIT_BF16},  # no dictionary
+    {"defer_gram": 1, "precision": osar.OSAR_FP32,
+     "dict_kind": osar.OSAR_DICT_GAUSSIAN, "n_atoms": 300},
+    {"defer_gram": 1, "precision": osar.OSAR_SPLIT_BF16,
+     "dict_kind": osar.OSAR_DICT_GAUSSIAN, "n_atoms": 300, "overlap_synthesis": 0},
+])
+def test_create_rejects_unsupported_deferred_update(lib, changes):
+    cfg = osar.default_config()
+    for k, v in changes.items():
+        setattr(cfg, k, v)
+    h = C.c_void_p()
+    assert lib.osar_create(C.byref(cfg), C.byref(h)) == osar.OSAR_E_INVALID
+    assert h.value is None
+    assert b"defer_gram" in lib.osar_last_error(None)
 
 
 @pytest.mark.parametrize("field,value", [
