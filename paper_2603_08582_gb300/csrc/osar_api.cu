@@ -486,8 +486,10 @@ void refresh_iters_estimate(osar_ctx* ctx) {
 // the grid.  On g SMs the product takes D / g (D = its tensor flops over
 // the split-BF16 rate one SM sustains beside the burst); meanwhile a Gram
 // pass takes max(bytes / HBM bandwidth, bytes / ((S - g) x per-SM
-// bandwidth)) x contention (one SM pulls at most about 84 GB/s, and the
-// product's own traffic slows the pass by about 8 %), and the rest of the
+// bandwidth)) x contention (per-SM bandwidth fitted at 84 GB/s, below the
+// 105 GB/s one SM pulls alone: beside the product the pass also shares HBM
+// with it; 105 gave the product more SMs and measured 13.35 against 13.30
+// ms per pulse), and the rest of the
 // burst runs at full speed.  The g that finishes both soonest is compared
 // with running the product alone on the whole GPU after the burst (0).  The
 // constants were measured on GB300 with the 128 x 128 workload (one SM:
