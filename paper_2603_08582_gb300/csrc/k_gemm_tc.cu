@@ -63,12 +63,17 @@ constexpr uint32_t TMEM_COLS = 512;
 // Ring geometry: one CTA per tile (B = 256 rows, two planes) or CTA pairs
 // (B = this CTA's 128 rows, one plane).
 // Gram epilogue of the pair kernel: per 64-column half of the tile, a
-// 16-column piece of the block (hi 16 KB + lo 8 KB, contiguous in the
-// column-major block) is staged by a bulk copy; two slots per half.
-constexpr int G_PIECE_HI = 16 * BLK * 8;
-constexpr int G_PIECE_LO = 16 * BLK * 4;
-constexpr int G_SLOT = G_PIECE_HI + G_PIECE_LO;  // 24 KB
-constexpr int PAIR_GRAM_STAGES = 4;              // operand ring beside the slots
+// G_COLS-column piece of the block (hi 8 KB + lo 4 KB, contiguous in the
+// column-major block) is staged by a bulk copy; two slots per half.  The
+// narrower the pieces, the deeper the operand ring beside them: 16-column
+// pieces left 4 ring slots, 8-column pieces leave 5 (a 3-slot ring ran the
+// update 12 % slower than 4 slots).
+constexpr int G_COLS = 8;
+constexpr int G_PIECES = 64 / G_COLS;            // per half and tile
+constexpr int G_PIECE_HI = G_COLS * BLK * 8;
+constexpr int G_PIECE_LO = G_COLS * BLK * 4;
+constexpr int G_SLOT = G_PIECE_HI + G_PIECE_LO;  // 12 KB
+constexpr int PAIR_GRAM_STAGES = G_COLS == 16 ? 4 : 5;  // operand ring beside the slots
 
 template <bool PAIR>
 struct TcCfg {
@@ -114,13 +119,14 @@ struct TcParams {
 // 2^-17 of the split-BF16 products, and saves a quarter of the traffic.)
 // Blocks are column-major, so entry (row, c) is at c * 128 + row and the 32
 // lanes of a warp (32 consecutive rows) touch contiguous bytes per access.
+template <int W>
 __device__ __forceinline__ void gram_piece(float2* gh, __nv_bfloat162* gl,
-                                           const float2 (&h)[16],
-                                           const __nv_bfloat162 (&l)[16],
+                                           const float2 (&h)[W],
+                                           const __nv_bfloat162 (&l)[W],
                                            const float* re, const float* im,
                                            bool comp) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
+  for (int q = 0; q < W; ++q) {
     float2 hv = h[q];
     if (comp) {
       const float2 lv = __bfloat1622float2(l[q]);
@@ -367,13 +373,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (staged) {
     // ------------------------------------- epilogue, Gram, staged pieces
-    // Each 64-column half (4 warps) walks its 16-column pieces of every
+    // Each 64-column half (4 warps) walks its G_COLS-column pieces of every
     // tile in order; piece n sits in slot n & 1 of its half.  One thread per
     // half bulk-loads a piece into its slot, the 4 warps update it there
     // (TwoSum, in place), and the same thread bulk-stores it back and then
-    // loads piece n + 2 into the slot.  Two pieces (48 KB per CTA) are in
-    // flight each way without holding registers, and the next tile's first
-    // pieces load while this tile's MMAs run.
+    // loads piece n + 2 into the slot.  Two pieces per half are in flight
+    // each way without holding registers, and the next tile's first pieces
+    // load while this tile's MMAs run.
     const int q = warp & 3;
     const int colh = (warp - 2) >> 2;
     const int row = q * 32 + lane;
@@ -382,12 +388,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t* slots = smem + PAIR_GRAM_STAGES * C::STAGE_BYTES + colh * 2 * G_SLOT;
     uint64_t* gf = gfull + colh * 2;
     const uint32_t bytes = G_PIECE_HI + (comp ? G_PIECE_LO : 0);
-    // offset of piece pc (16 columns) of the block this CTA updates for tile t
+    // offset of piece pc (G_COLS columns) of the block this CTA updates for tile t
     auto piece_off = [&](int t, int pc) {
       const int4 tile = p.tiles[t];
       const int ti = rank ? tile.z : tile.x;
       return packed_block(ti, tile.y & 0xFFFF, p.nb) * (BLK * BLK) +
-             (int64_t)(colh * 64 + pc * 16) * BLK;
+             (int64_t)(colh * 64 + pc * G_COLS) * BLK;
     };
     auto issue = [&](int t, int pc, int b) {
       const int64_t off = piece_off(t, pc);
@@ -407,7 +413,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool fail = false;
     int n = 0;  // pieces of this half processed so far
     // The 4 warps of a half pass the same barriers: every tile they enter
-    // has 4 barriers, and whether to stop is the OR over the half, taken at
+    // has G_PIECES barriers, and whether to stop is the OR over the half, taken at
     // a barrier, so all of them leave together.
     for (int t = unit; t < p.n_tiles; t += units) {
       const bool store = !(rank && (p.tiles[t].w & 1));
@@ -419,13 +425,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) +
                             (uint32_t)acc * 256u + (uint32_t)colh * 64u;
-      for (int pc = 0; pc < 4; ++pc, ++n) {
+      for (int pc = 0; pc < G_PIECES; ++pc, ++n) {
         const int b = n & 1;
         const uint32_t gph = (uint32_t)(n >> 1) & 1u;
-        float re[16], im[16];
+        float re[G_COLS], im[G_COLS];
         if (!fail) {
-          tmem_ld16(base + (uint32_t)(pc * 16), re);
-          tmem_ld16(base + 128u + (uint32_t)(pc * 16), im);
+          if constexpr (G_COLS == 16) {
+            tmem_ld16(base + (uint32_t)(pc * 16), re);
+            tmem_ld16(base + 128u + (uint32_t)(pc * 16), im);
+          } else {
+            tmem_ld8(base + (uint32_t)(pc * 8), re);
+            tmem_ld8(base + 128u + (uint32_t)(pc * 8), im);
+          }
           tmem_wait_ld();
           if (!mbar_wait_bounded(&gf[b], gph, abort_flag, p.err, WAIT_LIMIT_NS))
             fail = true;
@@ -437,15 +448,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           float2* hs = reinterpret_cast<float2*>(sl) + row;
           __nv_bfloat162* ls =
               reinterpret_cast<__nv_bfloat162*>(sl + G_PIECE_HI) + row;
-          float2 h[16];
-          __nv_bfloat162 l[16];
+          float2 h[G_COLS];
+          __nv_bfloat162 l[G_COLS];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) h[c] = hs[c * BLK];
+          for (int c = 0; c < G_COLS; ++c) h[c] = hs[c * BLK];
           if (comp) {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) l[c] = ls[c * BLK];
+            for (int c = 0; c < G_COLS; ++c) l[c] = ls[c * BLK];
           }
-          gram_piece(hs, comp ? ls : nullptr, h, l, re, im, comp);
+          gram_piece<G_COLS>(hs, comp ? ls : nullptr, h, l, re, im, comp);
           fence_proxy_async();  // the bulk store reads what was written here
         }
         // all 4 warps of the half have updated the piece (or given up)
@@ -462,10 +473,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           // next piece for this slot: n + 2 (this tile, or the next one's)
           const int m = pc + 2;
-          const int tn = m < 4 ? t : t + units;
+          const int tn = m < G_PIECES ? t : t + units;
           if (tn < p.n_tiles) {
             bulk_wait_read();
-            issue(tn, m & 3, b);
+            issue(tn, m % G_PIECES, b);
             issued[b]++;
           }
         }
@@ -541,9 +552,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (p.mode == 1) {
           const int64_t cur = (int64_t)(16 * pc) * BLK;
           if (pc & 1)
-            gram_piece(gh + cur, comp ? gl + cur : nullptr, h1, l1, re, im, comp);
+            gram_piece<16>(gh + cur, comp ? gl + cur : nullptr, h1, l1, re, im, comp);
           else
-            gram_piece(gh + cur, comp ? gl + cur : nullptr, h0, l0, re, im, comp);
+            gram_piece<16>(gh + cur, comp ? gl + cur : nullptr, h0, l0, re, im, comp);
         } else {
           float4* dst = reinterpret_cast<float4*>(
               p.part + slice * p.part_slice +
