@@ -66,14 +66,16 @@ constexpr uint32_t TMEM_COLS = 512;
 // G_COLS-column piece of the block (hi 8 KB + lo 4 KB, contiguous in the
 // column-major block) is staged by a bulk copy; two slots per half.  The
 // narrower the pieces, the deeper the operand ring beside them: 16-column
-// pieces left 4 ring slots, 8-column pieces leave 5 (a 3-slot ring ran the
-// update 12 % slower than 4 slots).
+// pieces left 4 ring slots, 8-column pieces leave 5 (3.8 against 4.2 ms per
+// update; a 3-slot ring ran 12 % slower than 4).  4-column pieces leave 6
+// but cost more in per-piece barriers and copies (4.2 ms).
 constexpr int G_COLS = 8;
 constexpr int G_PIECES = 64 / G_COLS;            // per half and tile
 constexpr int G_PIECE_HI = G_COLS * BLK * 8;
 constexpr int G_PIECE_LO = G_COLS * BLK * 4;
 constexpr int G_SLOT = G_PIECE_HI + G_PIECE_LO;  // 12 KB
-constexpr int PAIR_GRAM_STAGES = G_COLS == 16 ? 4 : 5;  // operand ring beside the slots
+constexpr int PAIR_GRAM_STAGES =  // operand ring beside the four slots
+    G_COLS == 16 ? 4 : G_COLS == 8 ? 5 : 6;
 
 template <bool PAIR>
 struct TcCfg {
@@ -433,9 +435,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if constexpr (G_COLS == 16) {
             tmem_ld16(base + (uint32_t)(pc * 16), re);
             tmem_ld16(base + 128u + (uint32_t)(pc * 16), im);
-          } else {
+          } else if constexpr (G_COLS == 8) {
             tmem_ld8(base + (uint32_t)(pc * 8), re);
             tmem_ld8(base + 128u + (uint32_t)(pc * 8), im);
+          } else {
+            tmem_ld4(base + (uint32_t)(pc * 4), re);
+            tmem_ld4(base + 128u + (uint32_t)(pc * 4), im);
           }
           tmem_wait_ld();
           if (!mbar_wait_bounded(&gf[b], gph, abort_flag, p.err, WAIT_LIMIT_NS))
