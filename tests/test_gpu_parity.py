@@ -200,16 +200,18 @@ def test_zero_data_keeps_zero_coefficients():
     assert gpu.state()["lambda"] == 0.0
 
 
-def test_full_size_128x128_sampled_entries_split_bf16():
-    """The 128 x 128 / M = 32768 workload in the bench's launch configuration:
-    Gram and data-vector entries on sampled atoms, and the matvec on sampled
-    rows, against the FP64 oracle computed column by column."""
+@pytest.mark.parametrize("defer", [False, True])
+def test_full_size_128x128_sampled_entries_split_bf16(defer):
+    """The 128 x 128 / M = 32768 workload in the bench's launch configuration
+    (and with the deferred Gram update): Gram and data-vector entries on
+    sampled atoms, and the matvec on sampled rows, against the FP64 oracle
+    computed column by column."""
     w = synth.workloads()["c2_128x128_split_bf16"]
     track = synth.workload_track(w)
     rng = np.random.default_rng(0)
     P = 3
     data = (rng.standard_normal((P, w.n_freq)) + 1j * rng.standard_normal((P, w.n_freq)))
-    gpu = osar.Osar(gpu_config(w, "split_bf16"))
+    gpu = osar.Osar(gpu_config(w, "split_bf16", defer_gram=defer))
     for s in range(P):
         gpu.push_pulse(track[s], data[s])
     gpu.iterate(2)
