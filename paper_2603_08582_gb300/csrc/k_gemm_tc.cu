@@ -33,10 +33,10 @@
 // of tile t overlaps the MMAs of tile t+1.
 // CTA-pair variant (clusters of two, cta_group::2): two tiles that share
 // their B rows run as one M = 256 MMA on two SMs, each SM loading its own A
-// rows and one of the two B planes (32 KB per ring slot instead of 48 KB);
-// in Gram mode the ring keeps 4 slots and the Gram read-modify-write is
-// staged through the freed shared memory by bulk copies; see
-// k_tc_cgemm<true>.
+// rows and one of the two B planes (32 KB per ring slot instead of 48 KB, 7
+// slots); in Gram mode the ring keeps 5 slots and the Gram read-modify-write
+// is staged through the rest of the shared memory by bulk copies in
+// 8-column pieces; see k_tc_cgemm<true>.
 //
 // Accumulation in the tensor pipe rounds its FP32 partial sums toward zero,
 // which biases long reductions (|A| shrinks by ~(steps) 2^-24).  The
@@ -114,7 +114,7 @@ struct TcParams {
   int* err;
 };
 
-// One 16-column piece of the Gram read-modify-write for this thread's row:
+// One W-column piece of the Gram read-modify-write for this thread's row:
 // hi + lo += delta with an error-free TwoSum, the new rounding error kept as
 // the bf16 compensation word.  (Keeping 8 bits of an error that is at most
 // half an FP32 ulp of hi still leaves the pair 2^-33-accurate, far below the
