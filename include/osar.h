@@ -307,6 +307,19 @@ osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
    stream, see overlap_synthesis). */
 osar_status osar_synchronize(osar_ctx* ctx);
 
+/* Failure-detection check.  Every wait inside the library's kernels (TMA
+   copies, tensor-core commits, peer CTAs) polls its barrier against the GPU
+   clock and gives up after a limit: it records a timeout in the context's
+   device error word, stops its CTA's other roles, drains what it issued and
+   returns, so the GPU stays usable and the next state read returns
+   OSAR_E_TIMEOUT.  This call exercises that path on purpose: one CTA waits,
+   through the same bounded wait, on a shared-memory barrier nothing arrives
+   on, with limit_ns in [1e6, 1e10] nanoseconds.  It synchronises and returns
+   OSAR_E_TIMEOUT when the wait gave up as designed (OSAR_E_CUDA if the
+   launch failed).  Nothing else is touched, but the context keeps the
+   recorded timeout: its state reads return OSAR_E_TIMEOUT from then on. */
+osar_status osar_probe_bounded_wait(osar_ctx* ctx, int64_t limit_ns);
+
 /* Per-kernel device timing.  When enabled, CUDA events bracket every
    launch of the listed kernel classes on the context's stream; reading the
    counters synchronises.  kernel: 0 phase, 1 dictionary GEMM, 2 Gram GEMM,

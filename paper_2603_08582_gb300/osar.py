@@ -38,6 +38,7 @@ EXPORTS = [
     "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
     "osar_gram_apply_static",
     "osar_simulate_pulse", "osar_unroll_grad", "osar_synchronize",
+    "osar_probe_bounded_wait",
     "osar_profile_enable",
     "osar_profile_read", "osar_profile_reset", "osar_profile_passes",
     "osar_launch_count",
@@ -114,6 +115,7 @@ def load_library(path: str = LIB_PATH):
         "osar_unroll_grad": (I32, [P, I32, I32, C.c_double, C.c_double,
                                      C.c_double, D, D, D, D, D, D, D]),
         "osar_synchronize": (I32, [P]),
+        "osar_probe_bounded_wait": (I32, [P, C.c_int64]),
         "osar_profile_enable": (I32, [P, I32]),
         "osar_profile_read": (I32, [P, I32, C.POINTER(C.c_int64), D]),
         "osar_profile_reset": (I32, [P]),
@@ -376,6 +378,12 @@ class Osar:
 
     def synchronize(self):
         self._check(self._lib.osar_synchronize(self._h))
+
+    def probe_bounded_wait(self, limit_ns: int) -> int:
+        """Run the failure-detection check (a bounded wait that nothing
+        completes); returns the status, OSAR_E_TIMEOUT when it gave up as
+        designed."""
+        return int(self._lib.osar_probe_bounded_wait(self._h, int(limit_ns)))
 
     # -- profiling ----------------------------------------------------------
     def profile_enable(self, on: bool = True):

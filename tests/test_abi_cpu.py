@@ -101,6 +101,7 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.osar_destroy(None) == osar.OSAR_OK
     assert lib.osar_iterate(None, 1, 0.0, None) == osar.OSAR_E_INVALID
     assert lib.osar_synchronize(None) == osar.OSAR_E_INVALID
+    assert lib.osar_probe_bounded_wait(None, 10**8) == osar.OSAR_E_INVALID
     assert b"libosar" in lib.osar_version()
 
 
