@@ -156,6 +156,11 @@ typedef struct {
      cuda_stream is being captured returns OSAR_E_STATE.  0: the update runs
      on cuda_stream before the power steps. */
   int32_t defer_gram;
+  /* Guard regions (a memory-checking aid): 0 off; > 0 (a multiple of 256, at
+     most 1 MiB) puts that many bytes, filled with 0xA5, behind every device
+     buffer the context (or a batch created with this config first) owns;
+     osar_check_guards reports buffers whose guard a kernel overwrote. */
+  int32_t guard_bytes;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
@@ -163,7 +168,7 @@ typedef struct {
    30 / 4 power steps, margin 0.01, carried momentum, compensated = 1,
    overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
    (both tensor-core products on SM pairs), fuse_first_step = 1,
-   n_lambdas = 1, defer_gram = 0. */
+   n_lambdas = 1, defer_gram = 0, guard_bytes = 0. */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128
@@ -320,6 +325,17 @@ osar_status osar_synchronize(osar_ctx* ctx);
    recorded timeout: its state reads return OSAR_E_TIMEOUT from then on. */
 osar_status osar_probe_bounded_wait(osar_ctx* ctx, int64_t limit_ns);
 
+/* Guard check (config guard_bytes > 0): synchronises, then sets *corrupted
+   to the number of device buffers whose guard region no longer holds its
+   fill; osar_last_error then names the first one.  With guards off,
+   *corrupted = 0. */
+osar_status osar_check_guards(osar_ctx* ctx, int32_t* corrupted);
+
+/* Test aid for the guard check: overwrites one byte of guard region `index`
+   (allocation order) from the host.  OSAR_E_INVALID when guards are off or
+   index is out of range. */
+osar_status osar_poke_guard(osar_ctx* ctx, int32_t index);
+
 /* Per-kernel device timing.  When enabled, CUDA events bracket every
    launch of the listed kernel classes on the context's stream; reading the
    counters synchronises.  kernel: 0 phase, 1 dictionary GEMM, 2 Gram GEMM,
@@ -410,6 +426,8 @@ osar_status osar_batch_info(const osar_batch* batch, int32_t* n_scenes,
                             int64_t* device_bytes, int64_t* launches,
                             int32_t* segment_blocks);
 osar_status osar_batch_synchronize(osar_batch* batch);
+/* Guard check of a batch (guard_bytes of the first scene's config). */
+osar_status osar_batch_check_guards(osar_batch* batch, int32_t* corrupted);
 const char* osar_batch_last_error(const osar_batch* batch);
 
 /* One-line description of the last error on ctx (or of the last failed

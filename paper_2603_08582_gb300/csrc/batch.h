@@ -33,6 +33,7 @@ struct SceneDesc {
 }  // namespace osar
 
 struct osar_batch {
+  osar::Guards guards;  // guard regions behind device buffers (guard_bytes)
   int S = 0;
   int prec = OSAR_FP32;
   int Kp = 0;

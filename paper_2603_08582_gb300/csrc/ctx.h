@@ -14,6 +14,7 @@
 
 #include "osar.h"
 #include "common.cuh"
+#include "guard.h"
 
 namespace osar {
 
@@ -177,6 +178,8 @@ struct osar_ctx {
   double2* sim_nz = nullptr;   // nonzero coefficient values (Mp)
   int* sim_idx = nullptr;      // nonzero coefficient indices (Mp)
   double2* sim_d = nullptr;    // simulated pulse (Kp)
+
+  osar::Guards guards;  // guard regions behind device buffers (guard_bytes)
 
   // differentiation-form scratch (allocated by the first unrolled gradient)
   void* adj_buf = nullptr;

@@ -247,10 +247,19 @@ cudaError_t run_unroll_grad(osar_ctx* ctx, int T, int C, double lambda,
   const size_t need = (vec + 256) * (2 * (size_t)nck + 2 * (size_t)C + 9) +
                       2 * (wvec + 256) + sizeof(double2) * ADJ_BLOCKS + 1024;
   if (ctx->adj_bytes < need) {
-    if (ctx->adj_buf) cudaFree(ctx->adj_buf);
+    if (ctx->adj_buf) {
+      cudaFree(ctx->adj_buf);
+      auto& rg = ctx->guards.regions;  // the freed buffer's guard goes too
+      for (size_t i = 0; i < rg.size(); ++i)
+        if (rg[i].name == "ctx->adj_buf") {
+          rg.erase(rg.begin() + (std::ptrdiff_t)i);
+          break;
+        }
+    }
     ctx->adj_buf = nullptr;
     ctx->adj_bytes = 0;
-    cudaError_t e = cudaMalloc(&ctx->adj_buf, need);
+    cudaError_t e = guarded_malloc(ctx->guards, &ctx->adj_buf, need, "ctx->adj_buf",
+                                   ctx->stream, nullptr);
     if (e != cudaSuccess) return e;
     ctx->adj_bytes = need;
   }

@@ -47,15 +47,12 @@ int64_t roundup(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 bool is_finite(double v) { return std::isfinite(v); }
 
 template <typename T>
-osar_status dev_alloc(osar_ctx* ctx, T** p, size_t bytes) {
-  cudaError_t e = cudaMalloc((void**)p, bytes);
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return cuda_fail(ctx, e, "cudaMalloc");
-  }
-  ctx->dev_bytes += (int64_t)bytes;
-  e = cudaMemsetAsync(*p, 0, bytes, ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+osar_status dev_alloc(osar_ctx* ctx, T** p, size_t bytes, const char* name) {
+  size_t total = 0;
+  cudaError_t e = guarded_malloc(ctx->guards, (void**)p, bytes, name,
+                                 ctx->stream, &total);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+  ctx->dev_bytes += (int64_t)total;
   return OSAR_OK;
 }
 
@@ -143,6 +140,8 @@ osar_status validate(const osar_config* c, std::string* why) {
       if (!is_finite(c->lambda_list[l]) || c->lambda_list[l] < 0)
         return *why = "lambda_list values must be finite and >= 0", OSAR_E_INVALID;
   }
+  if (c->guard_bytes < 0 || c->guard_bytes > (1 << 20) || c->guard_bytes % 256)
+    return *why = "guard_bytes must be a multiple of 256 in [0, 1 MiB]", OSAR_E_INVALID;
   if (c->defer_gram != 0 && c->defer_gram != 1)
     return *why = "defer_gram must be 0 or 1", OSAR_E_INVALID;
   if (c->defer_gram &&
@@ -272,10 +271,11 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   const int64_t bb = (int64_t)BLK * BLK;
 #define AL(p, bytes)                                 \
   do {                                               \
-    osar_status _s = dev_alloc(ctx, &(p), (bytes));  \
+    osar_status _s = dev_alloc(ctx, &(p), (bytes), #p);  \
     if (_s != OSAR_OK) return bail(_s);              \
   } while (0)
   const int L = ctx->n_lam;
+  ctx->guards.bytes = (size_t)cfg->guard_bytes;
   AL(ctx->scal, sizeof(DevScalars) * L);
   AL(ctx->b, 16 * Mp);
   AL(ctx->c, 16 * Mp * L);
@@ -743,6 +743,7 @@ void osar_config_default(osar_config* c) {
   c->n_lambdas = 1;
   c->lambda_list = nullptr;
   c->defer_gram = 0;
+  c->guard_bytes = 0;
 }
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
@@ -1058,6 +1059,29 @@ osar_status osar_synchronize(osar_ctx* ctx) {
   if (st != OSAR_OK) return st;
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->side) CK(ctx, cudaStreamSynchronize(ctx->side));
+  return OSAR_OK;
+}
+
+osar_status osar_check_guards(osar_ctx* ctx, int32_t* corrupted) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!corrupted) return fail(ctx, OSAR_E_INVALID, "osar_check_guards: NULL");
+  if (ctx->side) CK(ctx, cudaStreamSynchronize(ctx->side));
+  int bad = 0;
+  std::string first;
+  CK(ctx, check_guards(ctx->guards, ctx->stream, &bad, &first));
+  *corrupted = bad;
+  if (bad) ctx->last_error = "guard overwritten behind " + first;
+  return OSAR_OK;
+}
+
+osar_status osar_poke_guard(osar_ctx* ctx, int32_t index) {
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (index < 0 || index >= (int32_t)ctx->guards.regions.size())
+    return fail(ctx, OSAR_E_INVALID, "osar_poke_guard: no such guard");
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  CK(ctx, cudaMemset(ctx->guards.regions[index].addr + ctx->guards.bytes / 2, 0, 1));
   return OSAR_OK;
 }
 

@@ -54,14 +54,11 @@ osar_status bcuda(osar_batch* B, cudaError_t e, const char* where) {
 int64_t rup(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 template <typename T>
-cudaError_t balloc(osar_batch* B, T** p, size_t bytes) {
-  cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return e;
-  }
-  B->dev_bytes += (int64_t)bytes;
-  return cudaMemsetAsync(*p, 0, bytes ? bytes : 16, B->stream);
+cudaError_t balloc(osar_batch* B, T** p, size_t bytes, const char* name) {
+  size_t total = 0;
+  cudaError_t e = guarded_malloc(B->guards, (void**)p, bytes, name, B->stream, &total);
+  if (e == cudaSuccess) B->dev_bytes += (int64_t)total;
+  return e;
 }
 
 void free_batch(osar_batch* B) {
@@ -191,8 +188,13 @@ osar_status osar_batch_create(const osar_config* cfgs, int32_t n_scenes,
   }
   if (prec < OSAR_FP64 || prec > OSAR_SPLIT_BF16)
     return bfail(nullptr, OSAR_E_INVALID, "unknown precision");
+  const int gb = cfgs[0].guard_bytes;
+  if (gb < 0 || gb > (1 << 20) || gb % 256)
+    return bfail(nullptr, OSAR_E_INVALID,
+                 "guard_bytes must be a multiple of 256 in [0, 1 MiB]");
 
   osar_batch* B = new osar_batch();
+  B->guards.bytes = (size_t)gb;
   B->S = n_scenes;
   B->prec = prec;
   B->Kp = (int)rup(kmax, BLK);
@@ -275,7 +277,7 @@ osar_status osar_batch_create(const osar_config* cfgs, int32_t n_scenes,
   const int64_t R = rows, Kp = B->Kp;
 #define BA(p, bytes)                                        \
   do {                                                      \
-    cudaError_t _e = balloc(B, &(p), (bytes));              \
+    cudaError_t _e = balloc(B, &(p), (bytes), #p);          \
     if (_e != cudaSuccess) return bail(bcuda(B, _e, "cudaMalloc")); \
   } while (0)
   BA(B->desc, sizeof(SceneDesc) * n_scenes);
@@ -563,6 +565,17 @@ osar_status osar_batch_synchronize(osar_batch* B) {
   if (!B) return OSAR_E_INVALID;
   if (B->sticky != OSAR_OK) return B->sticky;
   BCK(B, cudaStreamSynchronize(B->stream));
+  return OSAR_OK;
+}
+
+osar_status osar_batch_check_guards(osar_batch* B, int32_t* corrupted) {
+  if (!B || !corrupted) return OSAR_E_INVALID;
+  if (B->sticky != OSAR_OK) return B->sticky;
+  int bad = 0;
+  std::string first;
+  BCK(B, check_guards(B->guards, B->stream, &bad, &first));
+  *corrupted = bad;
+  if (bad) B->last_error = "guard overwritten behind " + first;
   return OSAR_OK;
 }
 

@@ -38,7 +38,8 @@ EXPORTS = [
     "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
     "osar_gram_apply_static",
     "osar_simulate_pulse", "osar_unroll_grad", "osar_synchronize",
-    "osar_probe_bounded_wait",
+    "osar_probe_bounded_wait", "osar_check_guards", "osar_poke_guard",
+    "osar_batch_check_guards",
     "osar_profile_enable",
     "osar_profile_read", "osar_profile_reset", "osar_profile_passes",
     "osar_launch_count",
@@ -66,7 +67,7 @@ class OsarConfig(C.Structure):
         ("overlap_synthesis", C.c_int32), ("synth_ctas", C.c_int32),
         ("tc_pairs", C.c_int32), ("fuse_first_step", C.c_int32),
         ("n_lambdas", C.c_int32), ("lambda_list", C.c_void_p),
-        ("defer_gram", C.c_int32),
+        ("defer_gram", C.c_int32), ("guard_bytes", C.c_int32),
     ]
 
 
@@ -116,6 +117,9 @@ def load_library(path: str = LIB_PATH):
                                      C.c_double, D, D, D, D, D, D, D]),
         "osar_synchronize": (I32, [P]),
         "osar_probe_bounded_wait": (I32, [P, C.c_int64]),
+        "osar_check_guards": (I32, [P, C.POINTER(I32)]),
+        "osar_poke_guard": (I32, [P, I32]),
+        "osar_batch_check_guards": (I32, [P, C.POINTER(I32)]),
         "osar_profile_enable": (I32, [P, I32]),
         "osar_profile_read": (I32, [P, I32, C.POINTER(C.c_int64), D]),
         "osar_profile_reset": (I32, [P]),
@@ -166,7 +170,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
                 power_iters=4, lipschitz_margin=0.01, restart_momentum=False,
                 compensated=True, stream=None, overlap_synthesis=True,
                 synth_ctas=0, tc_pairs=3, fuse_first_step=True, lambdas=None,
-                defer_gram=False):
+                defer_gram=False, guard_bytes=0):
     """Build an osar_config.  dictionary: None (identity), "gaussian"
     (seeded Philox atoms, needs n_atoms) or an N x M complex array."""
     cfg = default_config()
@@ -199,6 +203,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
     cfg.tc_pairs = int(tc_pairs)  # bit 0 dictionary product, bit 1 Gram update
     cfg.fuse_first_step = 1 if fuse_first_step else 0
     cfg.defer_gram = 1 if defer_gram else 0
+    cfg.guard_bytes = int(guard_bytes)
     if lambdas is not None and len(lambdas) > 1:
         # lambda path: one solution per value (relative or absolute like lam)
         lv = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
@@ -379,6 +384,18 @@ class Osar:
     def synchronize(self):
         self._check(self._lib.osar_synchronize(self._h))
 
+    def last_error(self) -> str:
+        return self._lib.osar_last_error(self._h).decode()
+
+    def check_guards(self) -> int:
+        """Number of device buffers whose guard region was overwritten."""
+        n = C.c_int32(0)
+        self._check(self._lib.osar_check_guards(self._h, C.byref(n)))
+        return int(n.value)
+
+    def poke_guard(self, index: int) -> int:
+        return int(self._lib.osar_poke_guard(self._h, int(index)))
+
     def probe_bounded_wait(self, limit_ns: int) -> int:
         """Run the failure-detection check (a bounded wait that nothing
         completes); returns the status, OSAR_E_TIMEOUT when it gave up as
@@ -513,6 +530,11 @@ class OsarBatch:
 
     def synchronize(self):
         self._check(self._lib.osar_batch_synchronize(self._h))
+
+    def check_guards(self) -> int:
+        n = C.c_int32(0)
+        self._check(self._lib.osar_batch_check_guards(self._h, C.byref(n)))
+        return int(n.value)
 
 
 def version() -> str:

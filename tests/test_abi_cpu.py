@@ -49,7 +49,7 @@ def test_config_defaults_and_layout(lib):
     assert cfg.overlap_synthesis == 1 and cfg.synth_ctas == 0
     assert cfg.tc_pairs == 3 and cfg.fuse_first_step == 1
     assert cfg.n_lambdas == 1 and cfg.lambda_list is None
-    assert cfg.defer_gram == 0
+    assert cfg.defer_gram == 0 and cfg.guard_bytes == 0
 
 
 @pytest.mark.parametrize("changes", [
@@ -78,6 +78,7 @@ def test_create_rejects_unsupported_deferred_update(lib, changes):
     ("overlap_synthesis", 2), ("synth_ctas", -1), ("tc_pairs", 4),
     ("fuse_first_step", 2), ("n_lambdas", 0), ("n_lambdas", 9),
     ("n_lambdas", 2),  # > 1 without a lambda_list
+    ("guard_bytes", -256), ("guard_bytes", 100), ("guard_bytes", 2 << 20),
 ])
 def test_create_rejects_invalid_config_before_any_device_work(lib, field, value):
     cfg = osar.default_config()
