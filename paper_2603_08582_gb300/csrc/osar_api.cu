@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "trace.h"
 
 using namespace osar;
 
@@ -747,6 +748,7 @@ void osar_config_default(osar_config* c) {
 }
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
+  osar::TraceRange trace_("osar_create");
   if (!out) return fail(nullptr, OSAR_E_INVALID, "out is NULL");
   *out = nullptr;
   return create_impl(cfg, out);
@@ -764,6 +766,7 @@ osar_status osar_destroy(osar_ctx* ctx) {
 
 osar_status osar_push_pulse(osar_ctx* ctx, const double gamma_xyz[3],
                             const double* d_c128) {
+  osar::TraceRange trace_("osar_push_pulse");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!gamma_xyz || !d_c128)
@@ -785,6 +788,7 @@ osar_status osar_push_pulse(osar_ctx* ctx, const double gamma_xyz[3],
 
 osar_status osar_push_pulse_dev(osar_ctx* ctx, const double gamma_xyz[3],
                                 const void* d_dev_c128) {
+  osar::TraceRange trace_("osar_push_pulse_dev");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!gamma_xyz || !d_dev_c128)
@@ -800,6 +804,7 @@ osar_status osar_push_pulse_dev(osar_ctx* ctx, const double gamma_xyz[3],
 
 osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
                          int32_t* iters_done) {
+  osar::TraceRange trace_("osar_iterate");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (max_iters < 0 || !is_finite(tol) || tol < 0)
@@ -835,6 +840,7 @@ osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
 }
 
 osar_status osar_get_coeffs(osar_ctx* ctx, double* out_c128) {
+  osar::TraceRange trace_("osar_get_coeffs");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!out_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_coeffs: NULL");
@@ -855,6 +861,7 @@ osar_status osar_get_coeffs_dev(osar_ctx* ctx, void* out_dev_c128) {
 
 osar_status osar_get_coeffs_async(osar_ctx* ctx, double* out_c128,
                                   int32_t slot) {
+  osar::TraceRange trace_("osar_get_coeffs_async");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!out_c128 || slot < 0 || slot >= OSAR_COPY_SLOTS)
@@ -918,6 +925,7 @@ osar_status osar_get_dims(const osar_ctx* ctx, int32_t* m_atoms,
 }
 
 osar_status osar_get_gram(osar_ctx* ctx, double* out_c128) {
+  osar::TraceRange trace_("osar_get_gram");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!out_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_gram: NULL");
@@ -947,6 +955,7 @@ osar_status osar_get_gram(osar_ctx* ctx, double* out_c128) {
 osar_status osar_get_gram_entries(osar_ctx* ctx, const int32_t* rows,
                                   const int32_t* cols, int32_t count,
                                   double* out_c128) {
+  osar::TraceRange trace_("osar_get_gram_entries");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (count < 0 || (count > 0 && (!rows || !cols || !out_c128)))
@@ -989,6 +998,7 @@ osar_status osar_get_b(osar_ctx* ctx, double* out_c128) {
 
 osar_status osar_gram_apply(osar_ctx* ctx, const double* x_c128,
                             double* y_c128) {
+  osar::TraceRange trace_("osar_gram_apply");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!x_c128 || !y_c128) return fail(ctx, OSAR_E_INVALID, "osar_gram_apply: NULL");
@@ -1005,6 +1015,7 @@ osar_status osar_gram_apply(osar_ctx* ctx, const double* x_c128,
 
 osar_status osar_simulate_pulse(osar_ctx* ctx, const double gamma_xyz[3],
                                 const double* coeffs_c128, double* d_c128) {
+  osar::TraceRange trace_("osar_simulate_pulse");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!gamma_xyz || !coeffs_c128 || !d_c128)
@@ -1038,6 +1049,7 @@ osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
                              const double* c0_c128, const double* c_true_c128,
                              double* loss, double* d_lambda, double* d_tau,
                              double* d_b_c128, double* c_T_c128) {
+  osar::TraceRange trace_("osar_unroll_grad");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (ctx->n == 0)
@@ -1055,6 +1067,7 @@ osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
 }
 
 osar_status osar_synchronize(osar_ctx* ctx) {
+  osar::TraceRange trace_("osar_synchronize");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1191,6 +1204,7 @@ osar_status read_dev(osar_ctx* ctx, FILE* f, void* dev, size_t bytes) {
 }  // namespace
 
 osar_status osar_save(osar_ctx* ctx, const char* path) {
+  osar::TraceRange trace_("osar_save");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!path) return fail(ctx, OSAR_E_INVALID, "osar_save: NULL path");
@@ -1232,6 +1246,7 @@ osar_status osar_save(osar_ctx* ctx, const char* path) {
 }
 
 osar_status osar_load(const char* path, const osar_config* cfg, osar_ctx** out) {
+  osar::TraceRange trace_("osar_load");
   if (!out) return fail(nullptr, OSAR_E_INVALID, "out is NULL");
   *out = nullptr;
   if (!path || !cfg) return fail(nullptr, OSAR_E_INVALID, "osar_load: NULL argument");

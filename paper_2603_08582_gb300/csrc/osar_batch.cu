@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "batch.h"
+#include "trace.h"
 
 using namespace osar;
 
@@ -163,6 +164,7 @@ extern "C" {
 
 osar_status osar_batch_create(const osar_config* cfgs, int32_t n_scenes,
                               void* cuda_stream, osar_batch** out) {
+  osar::TraceRange trace_("osar_batch_create");
   if (!out) return bfail(nullptr, OSAR_E_INVALID, "out is NULL");
   *out = nullptr;
   if (!cfgs || n_scenes < 1 || n_scenes > 4096)
@@ -375,6 +377,7 @@ osar_status osar_batch_destroy(osar_batch* B) {
 osar_status osar_batch_push(osar_batch* B, const int32_t* active,
                             const double* gammas_xyz, const double* d_c128,
                             int32_t d_stride) {
+  osar::TraceRange trace_("osar_batch_push");
   if (!B) return OSAR_E_INVALID;
   if (B->sticky != OSAR_OK) return B->sticky;
   if (!active || !gammas_xyz || !d_c128 || d_stride < 1)
@@ -433,6 +436,7 @@ osar_status osar_batch_push(osar_batch* B, const int32_t* active,
 
 osar_status osar_batch_iterate(osar_batch* B, int32_t max_iters, double tol,
                                int32_t* iters) {
+  osar::TraceRange trace_("osar_batch_iterate");
   if (!B) return OSAR_E_INVALID;
   if (B->sticky != OSAR_OK) return B->sticky;
   if (max_iters < 0 || !std::isfinite(tol) || tol < 0)
@@ -479,6 +483,7 @@ osar_status osar_batch_iterate(osar_batch* B, int32_t max_iters, double tol,
 }
 
 osar_status osar_batch_get_coeffs(osar_batch* B, int32_t scene, double* out_c128) {
+  osar::TraceRange trace_("osar_batch_get_coeffs");
   if (!B) return OSAR_E_INVALID;
   if (B->sticky != OSAR_OK) return B->sticky;
   if (scene < 0 || scene >= B->S || !out_c128)
