@@ -67,8 +67,10 @@ typedef enum {
 typedef enum {
   OSAR_DICT_IDENTITY = 0,  /* H = I, M = N (pixel basis) */
   OSAR_DICT_HOST = 1,      /* H given as an N x M complex matrix */
-  OSAR_DICT_GAUSSIAN = 2   /* H = unit-norm complex Gaussian columns drawn by
+  OSAR_DICT_GAUSSIAN = 2,  /* H = unit-norm complex Gaussian columns drawn by
                               Philox4x32-10 (see osar_config.dict_seed) */
+  OSAR_DICT_EDGELET = 3    /* H = binary edgelets (Sec. III-A): see
+                              osar_config.edgelet_lengths / _angles_deg */
 } osar_dict_kind;
 
 typedef struct {
@@ -161,6 +163,20 @@ typedef struct {
      buffer the context (or a batch created with this config first) owns;
      osar_check_guards reports buffers whose guard a kernel overwrote. */
   int32_t guard_bytes;
+  /* OSAR_DICT_EDGELET (Sec. III-A, Dictionary Model): one binary atom per
+     (length l, rotation psi, centre pixel), M = n_lengths x n_angles x N
+     (n_atoms must be 0 or that number).  The edgelet steps by
+     (round(cos psi), round(sin psi)) pixels, psi a multiple of 45 degrees in
+     [0, 360), and covers the centre plus j - (l - 1) / 2 (integer division)
+     steps for j = 0 .. l - 1; pixels off the grid are dropped.  Atom
+     m = (length index x n_angles + angle index) x N + y x nx + x.  Lengths
+     in [1, 64], at most 16 of each list; the lists are copied at create.
+     The forward block A_s = F_s H is then a sum of l phase rows per atom
+     (no GEMM, no dictionary in device memory). */
+  int32_t n_edgelet_lengths;
+  const int32_t* edgelet_lengths;
+  int32_t n_edgelet_angles;
+  const double* edgelet_angles_deg;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over

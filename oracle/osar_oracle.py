@@ -32,6 +32,10 @@ Readings taken where the paper is silent, ambiguous or garbled:
   t = 1 at every pulse instead;
 * an optional stop rule ends a burst once ||c^(k) - z^(k)||_2 <=
   tol ||c^(k)||_2 (tol = 0 means exactly m steps, as in the paper);
+* edgelet atoms (§III-A) step by (round(cos psi), round(sin psi)) for psi
+  a multiple of 45 degrees, cover j - (l - 1) // 2 steps from their centre
+  (j = 0 .. l - 1), drop pixels off the grid, and run over (length,
+  rotation, y, x) with x fastest;
 * repeated bursts without a new pulse continue the same run of Algorithm 1
   (z, c^(k-1) and t are kept), so two bursts of a and b steps equal one burst
   of a + b steps.
@@ -84,6 +88,43 @@ def phase_matrix(gamma: np.ndarray, x: np.ndarray,
     r = ranges(gamma, x)
     k = 2.0 * np.pi * freqs / C_LIGHT
     return np.exp(-1j * 2.0 * np.outer(k, r))
+
+
+def edgelet_atoms(nx: int, ny: int, lengths, angles_deg) -> list:
+    """Pixel sets of the edgelet dictionary (§III-A, Dictionary Model): each
+    atom is a binary edgelet of length l and rotation psi centred at pixel
+    (x, y), for every length, rotation and centre x < nx, y < ny.
+
+    Readings (the paper gives no rasterisation): psi is a multiple of 45
+    degrees and the edgelet steps by (round(cos psi), round(sin psi)) pixels;
+    it covers the centre plus j - (l - 1) // 2 steps for j = 0 .. l - 1 (for
+    even l one more pixel ahead of the centre than behind); pixels outside
+    the grid are dropped; atoms run over (length, rotation, y, x) with x
+    fastest; pixel (x, y) is index y * nx + x."""
+    atoms = []
+    for l in lengths:
+        for a in angles_deg:
+            dx = int(round(np.cos(np.radians(a))))
+            dy = int(round(np.sin(np.radians(a))))
+            for y in range(ny):
+                for x in range(nx):
+                    pix = []
+                    for j in range(l):
+                        o = j - (l - 1) // 2
+                        px, py = x + o * dx, y + o * dy
+                        if 0 <= px < nx and 0 <= py < ny:
+                            pix.append(py * nx + px)
+                    atoms.append(pix)
+    return atoms
+
+
+def edgelet_dictionary(nx: int, ny: int, lengths, angles_deg) -> np.ndarray:
+    """The binary dictionary H (N x M, 1 on an atom's pixels, §III-A)."""
+    atoms = edgelet_atoms(nx, ny, lengths, angles_deg)
+    h = np.zeros((nx * ny, len(atoms)))
+    for m, pix in enumerate(atoms):
+        h[pix, m] = 1.0
+    return h
 
 
 def forward_block(f: np.ndarray, dictionary: Optional[np.ndarray]) -> np.ndarray:

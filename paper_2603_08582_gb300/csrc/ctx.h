@@ -74,6 +74,7 @@ struct osar_ctx {
   osar_config cfg;
   int prec = OSAR_FP64;
   bool dict = false;  // overcomplete / explicit dictionary present
+  bool edgelet = false;  // binary edgelet dictionary (atom pixel lists)
   int M = 0, N = 0, K = 0;
   int Mp = 0, Np = 0, Kp = 0;
   int nb = 0;          // Mp / BLK
@@ -135,6 +136,8 @@ struct osar_ctx {
   __nv_bfloat16* Apl = nullptr;  // split: 6 planes x Mp x Kp
   __nv_bfloat16* Fpl = nullptr;  // split + dictionary: 6 planes x Kp x Np
   __nv_bfloat16* Dpl = nullptr;  // split + dictionary: 4 planes x Mp x Np
+  int* atom_ptr = nullptr;       // edgelets: first entry of atom m (M + 1)
+  int* atom_pix = nullptr;       // edgelets: pixels of the atoms, in order
   CUtensorMap map_a_rows1;     // Apl, box (KC, 128, 1)
   CUtensorMap map_a_rows2;     // Apl, box (KC, 128, 2)
   CUtensorMap map_d_rows1;     // Dpl, box (KC, 128, 1)
@@ -209,6 +212,12 @@ cudaError_t settle_gram(osar_ctx* ctx);
 // ---- launch bracketing for the per-kernel profile -------------------------
 void prof_begin(osar_ctx* ctx, int kind, ProfEvent* ev);
 void prof_end(osar_ctx* ctx, ProfEvent* ev);
+
+// ---- k_edgelet.cu -----------------------------------------------------------
+// A_s = F_s H for the binary edgelet dictionary (sums of pixel phase rows)
+cudaError_t launch_edgelet(osar_ctx* ctx, int grid_cap);
+// the image H c of the simulation's sparse coefficients (sim_idx / sim_nz)
+cudaError_t launch_sim_rho_edgelet(osar_ctx* ctx, int nnz);
 
 // ---- k_defer.cu -------------------------------------------------------------
 // corr[set] = A_n^H (A_n x) for the pending forward block (nothing when no

@@ -759,7 +759,7 @@ bool make_tensor_maps(osar_ctx* ctx, std::string* err) {
       (!encode_planes(&ctx->map_alt_rows1, ctx->Apl_alt, ctx->Kp, ctx->Mp, 6, 1, err) ||
        !encode_planes(&ctx->map_alt_rows2, ctx->Apl_alt, ctx->Kp, ctx->Mp, 6, 2, err)))
     return false;
-  if (ctx->dict) {
+  if (ctx->dict && !ctx->edgelet) {
     if (!encode_planes(&ctx->map_d_rows1, ctx->Dpl, ctx->Np, ctx->Mp, 4, 1, err))
       return false;
     if (!encode_planes(&ctx->map_f_rows1, ctx->Fpl, ctx->Np, ctx->Kp, 6, 1, err))

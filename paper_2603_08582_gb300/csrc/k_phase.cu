@@ -347,8 +347,11 @@ cudaError_t launch_pixel_turns(osar_ctx* ctx, const double gamma[3]) {
 cudaError_t launch_phase(osar_ctx* ctx, int grid_cap) {
   ProfEvent ev;
   prof_begin(ctx, KCL_PHASE, &ev);
-  const bool pix = !ctx->dict;
-  const int rows = pix ? ctx->Mp : ctx->Kp;
+  // pixel-major rows (p, k) for the pixel basis (they are the block itself)
+  // and for edgelets (whose atoms sum pixel rows); frequency-major for the
+  // dictionary GEMM
+  const bool pix = !ctx->dict || ctx->edgelet;
+  const int rows = !ctx->dict ? ctx->Mp : ctx->edgelet ? ctx->Np : ctx->Kp;
   const int ld = pix ? ctx->Kp : ctx->Np;
   const int64_t work = (int64_t)rows * (ld / 8);
   unsigned g = blocks_for(work, 256);
@@ -356,7 +359,16 @@ cudaError_t launch_phase(osar_ctx* ctx, int grid_cap) {
   // split-BF16 kernel strides over its rows)
   if (grid_cap > 0 && ctx->prec == OSAR_SPLIT_BF16 && g > (unsigned)(4 * grid_cap))
     g = (unsigned)(4 * grid_cap);
-  if (ctx->prec == OSAR_SPLIT_BF16) {
+  if (ctx->edgelet) {
+    // FP32 phases for the split and FP32 paths, FP64 on the plain path
+    const unsigned gc = blocks_for(work, 256);  // one thread per 8 entries
+    if (ctx->prec == OSAR_FP64)
+      k_phase_complex<double2, true><<<gc, 256, 0, ctx->stream>>>(
+          ctx->turns, ctx->N, ctx->K, rows, ld, (double2*)ctx->F);
+    else
+      k_phase_complex<float2, true><<<gc, 256, 0, ctx->stream>>>(
+          ctx->turns, ctx->N, ctx->K, rows, ld, (float2*)ctx->F);
+  } else if (ctx->prec == OSAR_SPLIT_BF16) {
     __nv_bfloat16* out = pix ? ctx->Apl : ctx->Fpl;
     if (pix)
       k_phase_planes<true><<<g, 256, 0, ctx->stream>>>(ctx->turns, ctx->N,
@@ -429,7 +441,10 @@ cudaError_t launch_dictionary_build(osar_ctx* ctx, const double* host_dict) {
 
 cudaError_t launch_simulate(osar_ctx* ctx, int nnz, double2* d_out) {
   const int Np = ctx->Np;
-  if (!ctx->dict) {
+  if (ctx->edgelet) {
+    cudaError_t e = launch_sim_rho_edgelet(ctx, nnz);
+    if (e != cudaSuccess) return e;
+  } else if (!ctx->dict) {
     cudaMemsetAsync(ctx->sim_rho, 0, sizeof(double2) * Np, ctx->stream);
     if (nnz > 0)
       k_sim_scatter<<<blocks_for(nnz, 256), 256, 0, ctx->stream>>>(

@@ -67,7 +67,8 @@ void free_all(osar_ctx* ctx) {
                   ctx->sim_idx, ctx->sim_d, ctx->dict_part, ctx->gram_pairs,
                   ctx->dict_pairs, ctx->segpart2, ctx->tilepart2,
                   ctx->segpart_x, ctx->tilepart_x, ctx->gn_hi, ctx->gn_lo,
-                  ctx->Apl_alt, ctx->corr, ctx->corr_u, ctx->corr_tick};
+                  ctx->Apl_alt, ctx->corr, ctx->corr_u, ctx->corr_tick,
+                  ctx->atom_ptr, ctx->atom_pix};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
@@ -110,9 +111,30 @@ osar_status validate(const osar_config* c, std::string* why) {
     return *why = "need 0 < f_lo_hz <= f_hi_hz", OSAR_E_INVALID;
   if (c->precision < OSAR_FP64 || c->precision > OSAR_SPLIT_BF16)
     return *why = "unknown precision", OSAR_E_INVALID;
-  if (c->dict_kind < OSAR_DICT_IDENTITY || c->dict_kind > OSAR_DICT_GAUSSIAN)
+  if (c->dict_kind < OSAR_DICT_IDENTITY || c->dict_kind > OSAR_DICT_EDGELET)
     return *why = "unknown dict_kind", OSAR_E_INVALID;
-  if (c->dict_kind != OSAR_DICT_IDENTITY) {
+  if (c->dict_kind == OSAR_DICT_EDGELET) {
+    const int nl = c->n_edgelet_lengths, na = c->n_edgelet_angles;
+    if (nl < 1 || nl > 16 || na < 1 || na > 16 || !c->edgelet_lengths ||
+        !c->edgelet_angles_deg)
+      return *why = "edgelets need 1..16 lengths and 1..16 angles", OSAR_E_INVALID;
+    for (int i = 0; i < nl; ++i)
+      if (c->edgelet_lengths[i] < 1 || c->edgelet_lengths[i] > 64)
+        return *why = "edgelet lengths must be in [1, 64]", OSAR_E_INVALID;
+    for (int i = 0; i < na; ++i) {
+      const double a = c->edgelet_angles_deg[i];
+      if (!is_finite(a) || a < 0 || a >= 360 || std::fmod(a, 45.0) != 0.0)
+        return *why = "edgelet angles must be multiples of 45 in [0, 360)",
+               OSAR_E_INVALID;
+    }
+    const int64_t m = (int64_t)nl * na * c->nx * c->ny;
+    if ((int64_t)c->nx * c->ny > 131072 || m > 262144)
+      return *why = "edgelet dictionaries are limited to 131072 pixels and "
+                    "262144 atoms", OSAR_E_INVALID;
+    if (c->n_atoms != 0 && c->n_atoms != m)
+      return *why = "edgelets: n_atoms must be 0 or lengths x angles x pixels",
+             OSAR_E_INVALID;
+  } else if (c->dict_kind != OSAR_DICT_IDENTITY) {
     if (c->n_atoms < 1 || c->n_atoms > 131072)
       return *why = "n_atoms must be in [1, 131072]", OSAR_E_INVALID;
     if (c->dict_kind == OSAR_DICT_HOST && !c->dict_c128)
@@ -212,6 +234,34 @@ void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
   }
 }
 
+// Pixel lists of the edgelet atoms (§III-A): atom m = (length index x
+// angles + angle index) x N + y x nx + x covers the centre (x, y) plus
+// j - (l - 1) / 2 steps of (dx, dy) for j = 0 .. l - 1, pixels off the grid
+// dropped; (dx, dy) = (round(cos psi), round(sin psi)) for psi = 45 s.
+void build_edgelets(const osar_config& c, std::vector<int>& ptr,
+                    std::vector<int>& pix) {
+  static const int DX[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+  static const int DY[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+  ptr.assign(1, 0);
+  pix.clear();
+  for (int li = 0; li < c.n_edgelet_lengths; ++li) {
+    const int l = c.edgelet_lengths[li];
+    for (int ai = 0; ai < c.n_edgelet_angles; ++ai) {
+      const int s = (int)std::lround(c.edgelet_angles_deg[ai] / 45.0) % 8;
+      for (int y = 0; y < c.ny; ++y)
+        for (int x = 0; x < c.nx; ++x) {
+          for (int j = 0; j < l; ++j) {
+            const int o = j - (l - 1) / 2;
+            const int px = x + o * DX[s], py = y + o * DY[s];
+            if (px >= 0 && px < c.nx && py >= 0 && py < c.ny)
+              pix.push_back(py * c.nx + px);
+          }
+          ptr.push_back((int)pix.size());
+        }
+    }
+  }
+}
+
 osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   std::string why;
   osar_status st = validate(cfg, &why);
@@ -227,8 +277,14 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
                                                      : cfg->lambda;
   ctx->prec = cfg->precision;
   ctx->dict = cfg->dict_kind != OSAR_DICT_IDENTITY;
+  ctx->edgelet = cfg->dict_kind == OSAR_DICT_EDGELET;
   ctx->N = cfg->nx * cfg->ny;
-  ctx->M = ctx->dict ? cfg->n_atoms : ctx->N;
+  ctx->M = ctx->edgelet ? cfg->n_edgelet_lengths * cfg->n_edgelet_angles * ctx->N
+           : ctx->dict  ? cfg->n_atoms
+                        : ctx->N;
+  ctx->cfg.n_atoms = ctx->dict ? ctx->M : cfg->n_atoms;
+  ctx->cfg.edgelet_lengths = nullptr;     // the atom lists are built below
+  ctx->cfg.edgelet_angles_deg = nullptr;
   ctx->K = cfg->n_freq;
   ctx->Mp = (int)roundup(ctx->M, BLK);
   ctx->Np = (int)roundup(ctx->N, BLK);
@@ -311,7 +367,19 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   if (ctx->dict) AL(ctx->dict_tiles, sizeof(int4) * (dtiles.size() ? dtiles.size() : 1));
   AL(ctx->gram_pairs, sizeof(int4) * gpairs.size());
   if (ctx->dict) AL(ctx->dict_pairs, sizeof(int4) * (dpairs.size() ? dpairs.size() : 1));
-  if (ctx->prec == OSAR_SPLIT_BF16) {
+  std::vector<int> atom_ptr, atom_pix;
+  if (ctx->edgelet) {
+    // edgelets: pixel-major phases (FP32 for the split and FP32 paths) and
+    // the atoms' pixel lists instead of a dictionary in device memory
+    build_edgelets(*cfg, atom_ptr, atom_pix);
+    AL(ctx->F, (ctx->prec == OSAR_FP64 ? 16 : 8) * Np * Kp);
+    AL(ctx->atom_ptr, sizeof(int) * atom_ptr.size());
+    AL(ctx->atom_pix, sizeof(int) * (atom_pix.empty() ? 1 : atom_pix.size()));
+    if (ctx->prec == OSAR_SPLIT_BF16)
+      AL(ctx->Apl, 2 * 6 * Mp * Kp);
+    else
+      AL(ctx->A, cplx * Mp * Kp);
+  } else if (ctx->prec == OSAR_SPLIT_BF16) {
     AL(ctx->Apl, 2 * 6 * Mp * Kp);
     if (ctx->dict) {
       AL(ctx->Fpl, 2 * 6 * Kp * Np);
@@ -402,7 +470,17 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   if (e == cudaSuccess) e = launch_set_working(ctx);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "upload tables"));
 
-  if (ctx->dict) {
+  if (ctx->edgelet) {
+    e = cudaMemcpyAsync(ctx->atom_ptr, atom_ptr.data(), sizeof(int) * atom_ptr.size(),
+                        cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && !atom_pix.empty())
+      e = cudaMemcpyAsync(ctx->atom_pix, atom_pix.data(),
+                          sizeof(int) * atom_pix.size(), cudaMemcpyHostToDevice,
+                          ctx->stream);
+    // the host lists leave scope below: the copies complete first
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "edgelet atoms"));
+  } else if (ctx->dict) {
     e = launch_dictionary_build(
         ctx, cfg->dict_kind == OSAR_DICT_HOST ? cfg->dict_c128 : nullptr);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "dictionary build"));
@@ -451,6 +529,7 @@ cudaError_t synthesize_phase(osar_ctx* ctx, const double gamma[3], int grid_cap)
 }
 cudaError_t synthesize_dict(osar_ctx* ctx, int grid_cap) {
   if (!ctx->dict) return cudaSuccess;
+  if (ctx->edgelet) return launch_edgelet(ctx, grid_cap);
   return ctx->prec == OSAR_SPLIT_BF16 ? launch_dict_tc(ctx, grid_cap)
                                       : launch_dict_simt(ctx);
 }
@@ -497,6 +576,8 @@ void refresh_iters_estimate(osar_ctx* ctx) {
 // 1.23e13 f/s alone, about 1.2e13 beside the burst).
 int synth_grid(const osar_ctx* ctx, bool main_idle) {
   if (ctx->cfg.synth_ctas > 0) return std::min(ctx->cfg.synth_ctas, ctx->sm_count);
+  // an edgelet block is a gather of phase rows, too short to overlap
+  if (ctx->edgelet) return 0;
   // nothing in flight on the main stream (the caller waited for the last
   // burst): the product has the GPU to itself
   if (main_idle) return 0;

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libosar.so")
 OSAR_OK, OSAR_E_INVALID, OSAR_E_OOM, OSAR_E_CUDA, OSAR_E_STATE, \
     OSAR_E_TIMEOUT, OSAR_E_NUMERIC, OSAR_E_IO = range(8)
 OSAR_FP64, OSAR_FP32, OSAR_SPLIT_BF16 = 0, 1, 2
-OSAR_DICT_IDENTITY, OSAR_DICT_HOST, OSAR_DICT_GAUSSIAN = 0, 1, 2
+OSAR_DICT_IDENTITY, OSAR_DICT_HOST, OSAR_DICT_GAUSSIAN, OSAR_DICT_EDGELET = 0, 1, 2, 3
 COPY_SLOTS = 4  # OSAR_COPY_SLOTS: osar_get_coeffs_async completion slots
 
 PRECISIONS = {"fp64": OSAR_FP64, "fp32": OSAR_FP32, "split_bf16": OSAR_SPLIT_BF16}
@@ -68,6 +68,8 @@ class OsarConfig(C.Structure):
         ("tc_pairs", C.c_int32), ("fuse_first_step", C.c_int32),
         ("n_lambdas", C.c_int32), ("lambda_list", C.c_void_p),
         ("defer_gram", C.c_int32), ("guard_bytes", C.c_int32),
+        ("n_edgelet_lengths", C.c_int32), ("edgelet_lengths", C.c_void_p),
+        ("n_edgelet_angles", C.c_int32), ("edgelet_angles_deg", C.c_void_p),
     ]
 
 
@@ -170,9 +172,12 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
                 power_iters=4, lipschitz_margin=0.01, restart_momentum=False,
                 compensated=True, stream=None, overlap_synthesis=True,
                 synth_ctas=0, tc_pairs=3, fuse_first_step=True, lambdas=None,
-                defer_gram=False, guard_bytes=0):
+                defer_gram=False, guard_bytes=0, edgelet_lengths=None,
+                edgelet_angles=None):
     """Build an osar_config.  dictionary: None (identity), "gaussian"
-    (seeded Philox atoms, needs n_atoms) or an N x M complex array."""
+    (seeded Philox atoms, needs n_atoms), "edgelet" (binary edgelets of
+    edgelet_lengths x edgelet_angles degrees at every pixel) or an N x M
+    complex array."""
     cfg = default_config()
     cfg.nx, cfg.ny, cfg.pixel_m = int(nx), int(ny), float(pixel_m)
     cfg.n_freq, cfg.f_lo_hz, cfg.f_hi_hz = int(n_freq), float(f_lo_hz), float(f_hi_hz)
@@ -184,6 +189,14 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
         cfg.dict_kind = OSAR_DICT_GAUSSIAN
         cfg.n_atoms = int(n_atoms)
         cfg.dict_seed = int(dict_seed)
+    elif isinstance(dictionary, str) and dictionary == "edgelet":
+        lv = np.ascontiguousarray(np.asarray(edgelet_lengths, dtype=np.int32))
+        av = np.ascontiguousarray(np.asarray(edgelet_angles, dtype=np.float64))
+        cfg.dict_kind = OSAR_DICT_EDGELET
+        cfg.n_atoms = 0
+        cfg.n_edgelet_lengths, cfg.edgelet_lengths = int(lv.size), lv.ctypes.data
+        cfg.n_edgelet_angles, cfg.edgelet_angles_deg = int(av.size), av.ctypes.data
+        keep = (lv, av)
     else:
         d = np.asarray(dictionary, dtype=np.complex128)
         keep = np.asfortranarray(d)

@@ -58,8 +58,10 @@ class Workload:
     height_m: float = 500.0
     pixel_m: float = 1.0
     theta0_deg: float = 0.0
-    dictionary: str = "identity"     # "identity" | "gaussian"
+    dictionary: str = "identity"     # "identity" | "gaussian" | "edgelet"
     n_atoms: Optional[int] = None    # None => M = N
+    edgelet_lengths: tuple = ()      # edgelet atoms: lengths x angles x pixels
+    edgelet_angles: tuple = ()       # degrees, multiples of 45
     dict_seed: int = 0
     sparsity: float = 0.05
     clustered: bool = False
@@ -76,6 +78,8 @@ class Workload:
 
     @property
     def m_atoms(self) -> int:
+        if self.dictionary == "edgelet":
+            return len(self.edgelet_lengths) * len(self.edgelet_angles) * self.n_pixels
         return self.n_atoms if self.n_atoms is not None else self.n_pixels
 
     def as_dict(self) -> dict:
@@ -279,6 +283,9 @@ def gaussian_dictionary(n_pixels: int, n_atoms: int, seed: int,
 
 
 def workload_dictionary(w: Workload) -> Optional[np.ndarray]:
-    if w.dictionary == "identity":
+    """The random dictionary a workload draws (None for the pixel basis; the
+    edgelet dictionary is no draw but part of the model, built by each side
+    from its lengths and angles)."""
+    if w.dictionary in ("identity", "edgelet"):
         return None
     return gaussian_dictionary(w.n_pixels, w.m_atoms, w.dict_seed)

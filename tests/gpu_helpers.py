@@ -13,7 +13,12 @@ def gpu_config(w, precision, lam=0.05, lambda_relative=True,
                power_iters_first=30, power_iters=4, margin=0.01,
                restart_momentum=False, compensated=True, host_dictionary=None,
                defer_gram=False):
-    if w.dictionary == "gaussian" and host_dictionary is None:
+    extra = {}
+    if w.dictionary == "edgelet":
+        dictionary, n_atoms = "edgelet", None
+        extra = dict(edgelet_lengths=list(w.edgelet_lengths),
+                     edgelet_angles=list(w.edgelet_angles))
+    elif w.dictionary == "gaussian" and host_dictionary is None:
         dictionary, n_atoms = "gaussian", w.m_atoms
     elif host_dictionary is not None:
         dictionary, n_atoms = host_dictionary, host_dictionary.shape[1]
@@ -25,7 +30,7 @@ def gpu_config(w, precision, lam=0.05, lambda_relative=True,
         dict_seed=w.dict_seed, lam=lam, lambda_relative=lambda_relative,
         power_iters_first=power_iters_first, power_iters=power_iters,
         lipschitz_margin=margin, restart_momentum=restart_momentum,
-        compensated=compensated, defer_gram=defer_gram)
+        compensated=compensated, defer_gram=defer_gram, **extra)
 
 
 def run_pair(w, precision, steps, tol=0.0, pulses=None, lam=0.05,

@@ -90,6 +90,24 @@ def test_create_rejects_invalid_config_before_any_device_work(lib, field, value)
     assert len(lib.osar_last_error(None)) > 0
 
 
+@pytest.mark.parametrize("lengths,angles,n_atoms", [
+    ([], [0.0], 0), ([4], [], 0), ([0], [0.0], 0), ([65], [0.0], 0),
+    ([4], [30.0], 0), ([4], [360.0], 0), ([4], [-45.0], 0),
+    ([4], [0.0, 90.0], 7),          # n_atoms must be 0 or 2 x pixels
+])
+def test_create_rejects_invalid_edgelets(lib, lengths, angles, n_atoms):
+    cfg = osar.make_config(8, 8, 16, 9.9e9, 10.1e9, dictionary="edgelet",
+                           edgelet_lengths=lengths or [1], edgelet_angles=angles or [0.0])
+    if not lengths:
+        cfg.n_edgelet_lengths = 0
+    if not angles:
+        cfg.n_edgelet_angles = 0
+    cfg.n_atoms = n_atoms
+    h = C.c_void_p()
+    assert lib.osar_create(C.byref(cfg), C.byref(h)) == osar.OSAR_E_INVALID
+    assert h.value is None
+
+
 def test_create_rejects_missing_host_dictionary(lib):
     cfg = osar.default_config()
     cfg.dict_kind = osar.OSAR_DICT_HOST

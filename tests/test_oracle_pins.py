@@ -387,3 +387,61 @@ def test_gaussian_dictionary_statistics():
     assert abs(np.var(raw.real) - 0.5) < 0.02
     cols = synth.gaussian_dictionary_columns(256, np.array([7, 299]), seed=3)
     assert np.array_equal(cols, d[:, [7, 299]])
+
+
+# ------------------------------------------------------------ edgelets ---
+# §III-A: binary edgelets of length l and rotation psi centred at every pixel.
+# The pins restate the atoms in closed form (a clipped run of columns or rows,
+# or a hand-listed diagonal), not by the oracle's stepping rule.
+
+def test_edgelet_atoms_horizontal_and_vertical_are_clipped_runs():
+    nx, ny = 7, 5
+    for l in (1, 2, 3, 4, 6):
+        h = orc.edgelet_atoms(nx, ny, [l], [0.0])
+        v = orc.edgelet_atoms(nx, ny, [l], [90.0])
+        assert len(h) == len(v) == nx * ny
+        back = (l - 1) // 2                      # pixels behind the centre
+        for y in range(ny):
+            for x in range(nx):
+                lo, hi = max(0, x - back), min(nx - 1, x - back + l - 1)
+                assert sorted(h[y * nx + x]) == [y * nx + c for c in range(lo, hi + 1)]
+                lo, hi = max(0, y - back), min(ny - 1, y - back + l - 1)
+                assert sorted(v[y * nx + x]) == [r * nx + x for r in range(lo, hi + 1)]
+
+
+def test_edgelet_atoms_diagonals_by_hand():
+    # 4 x 4 grid, length 3: offsets -1, 0, 1 along (1, 1) and (-1, 1)
+    d45 = orc.edgelet_atoms(4, 4, [3], [45.0])
+    assert sorted(d45[1 * 4 + 1]) == [0, 5, 10]          # (0,0) (1,1) (2,2)
+    assert sorted(d45[0]) == [0, 5]                      # (-1,-1) dropped
+    d135 = orc.edgelet_atoms(4, 4, [3], [135.0])
+    assert sorted(d135[1 * 4 + 2]) == [3, 6, 9]          # (3,0) (2,1) (1,2)
+    # length 4 along (1, 1) from (1, 1): offsets -1 .. 2
+    assert sorted(orc.edgelet_atoms(4, 4, [4], [45.0])[5]) == [0, 5, 10, 15]
+
+
+def test_edgelet_dictionary_counts_order_and_paper_square():
+    nx = ny = 12
+    lengths, angles = [2, 4, 6], [0.0]
+    h = orc.edgelet_dictionary(nx, ny, lengths, angles)
+    assert h.shape == (nx * ny, 3 * nx * ny)
+    assert set(np.unique(h)) <= {0.0, 1.0}
+    # atom m = (length index * rotations + rotation index) * N + y * nx + x
+    m = (2 * 1 + 0) * nx * ny + 3 * nx + 5                 # length 6 at (5, 3)
+    assert np.flatnonzero(h[:, m]).tolist() == [3 * nx + c for c in range(3, 9)]
+    # dictionary 1 of the experiments (length 4, 0 and 90 degrees): a square
+    # outline of side 4 with top-left (x0, y0) is exactly four atoms
+    d1 = orc.edgelet_dictionary(nx, ny, [4], [0.0, 90.0])
+    x0, y0, n = 3, 2, nx * ny
+    c = np.zeros(2 * n)
+    c[y0 * nx + x0 + 1] = 1                 # top edge, centre (x0 + 1, y0)
+    c[(y0 + 3) * nx + x0 + 1] = 1           # bottom edge
+    c[n + (y0 + 1) * nx + x0] = 1           # left edge, centre (x0, y0 + 1)
+    c[n + (y0 + 1) * nx + x0 + 3] = 1       # right edge
+    img = (d1 @ c).reshape(ny, nx)
+    want = np.zeros((ny, nx))
+    want[y0, x0:x0 + 4] += 1
+    want[y0 + 3, x0:x0 + 4] += 1
+    want[y0:y0 + 4, x0] += 1
+    want[y0:y0 + 4, x0 + 3] += 1
+    assert np.array_equal(img, want)
