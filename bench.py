@@ -638,6 +638,89 @@ def run_forms(stream):
             "ms_per_pulse_one_lambda": round(res[1], 2),
             "solution_pulses_per_s": round(len(lams) / (res[len(lams)] / 1e3), 1),
             "speedup_vs_separate": round(len(lams) * res[1] / res[len(lams)], 2)}
+        out.update(run_edgelet_forms(stream))
+    return out
+
+
+def run_edgelet_forms(stream):
+    """The edgelet dictionary (§III-A): the 128 x 128 geometry with the
+    square scenes' dictionary (M = 2N = 32768 atoms, as the Gaussian
+    workload), and a scene like the experiments' Scene 1 run until the
+    number of large coefficients (|c| > 0.02) reaches its ideal 4."""
+    from paper_2603_08582_gb300 import osar, synth
+    out = {}
+    w0 = synth.workloads()["c2_128x128_split_bf16"]
+    w = synth.Workload(**{**w0.as_dict(), "name": "c2_128x128_edgelet",
+                          "dictionary": "edgelet", "n_atoms": None,
+                          "edgelet_lengths": (4,), "edgelet_angles": (0.0, 90.0)})
+    cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
+                           pixel_m=w.pixel_m, precision="split_bf16",
+                           dictionary="edgelet", edgelet_lengths=[4],
+                           edgelet_angles=[0.0, 90.0], lam=w.lambda_rel,
+                           stream=stream.cuda_stream)
+    ctx = osar.Osar(cfg)
+    W, P = 4, 32
+    track, data, _ = _sim_pulses(ctx, w, W + P)
+    for s in range(W):
+        ctx.push_pulse(track[s], data[s])
+        ctx.iterate(INNER_STEPS, TOL, want_count=False)
+    ctx.synchronize()
+    ctx.profile_reset()
+    ctx.profile_enable(True)
+    steps = []
+
+    def rune():
+        for s in range(W, W + P):
+            ctx.push_pulse(track[s], data[s])
+            steps.append(ctx.iterate(INNER_STEPS, TOL))
+    ms = _time(rune, stream) / P
+    ph = ctx.profile_read("phase")[1] / P
+    dg = ctx.profile_read("dict_gemm")[1] / P
+    gr = ctx.profile_read("gram_gemm")[1] / P
+    ctx.profile_enable(False)
+    out["c2_128x128_edgelet_split_bf16"] = {
+        "pulses": P, "ms_per_pulse": round(ms, 2),
+        "pulses_per_s": round(1e3 / ms, 1), "mean_iters": round(float(np.mean(steps)), 2),
+        "synthesis_ms_per_pulse": {"phases": round(ph, 3), "edgelet_block": round(dg, 3)},
+        "gram_ms_per_pulse": round(gr, 3), "device_gb": round(ctx.device_bytes() / 1e9, 1)}
+    ctx.close()
+    # Scene 1 of the experiments (a square, 4 atoms): 4 km radius, 1 km up,
+    # 1000 positions over 2 degrees, pulses kept with p = 0.3, m = 20
+    lengths, angles, c_true = synth.paper_scene("square", 32, 32)
+    sw = synth.Workload(name="paper_scene1_32x32", nx=32, ny=32, n_freq=128,
+                        f_lo_hz=9.9e9, f_hi_hz=10.1e9, n_pulses=1000, span_deg=2.0,
+                        radius_m=4000.0, height_m=1000.0, dictionary="edgelet",
+                        edgelet_lengths=lengths, edgelet_angles=angles,
+                        snr_db=20.0, seed=7)
+    track = synth.sampled_track(1000, 4000.0, 1000.0, 2.0, 0.3, sw.seed)
+    cfg = osar.make_config(sw.nx, sw.ny, sw.n_freq, sw.f_lo_hz, sw.f_hi_hz,
+                           precision="split_bf16", dictionary="edgelet",
+                           edgelet_lengths=list(lengths), edgelet_angles=list(angles),
+                           lam=0.05, stream=stream.cuda_stream)
+    ctx = osar.Osar(cfg)
+    clean = np.stack([ctx.simulate_pulse(g, c_true) for g in track])
+    noise = synth.unit_noise(len(track), sw.n_freq, sw.seed)
+    data = clean + synth.scale_noise(clean, noise, sw.snr_db)
+    counts, reached = [], None
+    e0 = time.perf_counter()
+    for s in range(len(track)):
+        ctx.push_pulse(track[s], data[s])
+        ctx.iterate(20, 0.0, want_count=False)
+        cnt = int(np.count_nonzero(np.abs(ctx.coeffs()) > 2e-2))
+        counts.append(cnt)
+        if cnt == 4:
+            reached = s + 1
+            break
+    wall = time.perf_counter() - e0
+    big = np.flatnonzero(np.abs(ctx.coeffs()) > 2e-2)
+    out["paper_scene1_32x32_split_bf16"] = {
+        "positions": 1000, "pulses_available": int(len(track)),
+        "pulses_to_ideal_count": reached, "final_count": counts[-1],
+        "large_are_the_true_atoms": bool(set(big) == set(np.flatnonzero(c_true))),
+        "count_after_pulses": {str(k): counts[k - 1] for k in (1, 5, 10, 20, 50, 100)
+                               if k <= len(counts)},
+        "ms_per_pulse_with_readback": round(1e3 * wall / len(counts), 3)}
+    ctx.close()
     return out
 
 

@@ -158,6 +158,61 @@ def workload_track(w: Workload) -> np.ndarray:
                           w.theta0_deg)
 
 
+def sampled_track(n_positions: int, radius_m: float, height_m: float,
+                  span_deg: float, p: float, seed: int,
+                  theta0_deg: float = 0.0) -> np.ndarray:
+    """The pulses of the experiments' pulse selection: n_positions evenly
+    spaced along the arc, each kept by its own Bernoulli(p) draw (the paper
+    gives no p; it is an input here)."""
+    full = circular_track(n_positions, radius_m, height_m, span_deg, theta0_deg)
+    keep = np.random.default_rng(seed + 104729).random(n_positions) < p
+    return full[keep]
+
+
+def edgelet_atom_index(nx: int, ny: int, n_angles: int, length_idx: int,
+                       angle_idx: int, x: int, y: int) -> int:
+    """Atom number of the edgelet dictionary's documented order: (length,
+    rotation, y, x) with x fastest."""
+    return (length_idx * n_angles + angle_idx) * nx * ny + y * nx + x
+
+
+def paper_scene(kind: str, nx: int, ny: int):
+    """Coefficient vectors for scenes like the experiments' four (§IV-A:
+    a square; two squares; lines of varying intensities, spaced; the same
+    lines adjoined), rebuilt from the text (the images are not available):
+    returns (lengths, angles_deg, c).  Squares use length-4 edgelets at 0 and
+    90 degrees (4 atoms each), lines lengths 2, 4 and 6 at 0 degrees (5
+    atoms).  An edgelet of length l covering columns xs .. xs + l - 1 is
+    centred at xs + (l - 1) // 2."""
+    n = nx * ny
+    if kind in ("square", "two_squares"):
+        lengths, angles = (4,), (0.0, 90.0)
+        c = np.zeros(2 * n, dtype=np.complex128)
+        corners = [(nx // 2 - 2, ny // 2 - 2)]
+        if kind == "two_squares":
+            corners = [(nx // 4 - 2, ny // 4 - 2), (3 * nx // 4 - 2, 3 * ny // 4 - 2)]
+        for x0, y0 in corners:
+            for (ai, x, y) in ((0, x0 + 1, y0), (0, x0 + 1, y0 + 3),
+                               (1, x0, y0 + 1), (1, x0 + 3, y0 + 1)):
+                c[edgelet_atom_index(nx, ny, 2, 0, ai, x, y)] = 1.0
+        return lengths, angles, c
+    if kind in ("lines_spaced", "lines_adjoined"):
+        lengths, angles = (2, 4, 6), (0.0,)
+        c = np.zeros(3 * n, dtype=np.complex128)
+        # (length index, first column, row, intensity)
+        if kind == "lines_spaced":
+            lines = [(2, 2, 3, 1.0), (1, 12, 5, 0.8), (0, 20, 9, 0.6),
+                     (2, 4, 15, 0.9), (1, 18, 21, 0.7)]
+        else:  # end to end on two rows
+            lines = [(2, 4, 10, 1.0), (1, 10, 10, 0.8), (0, 14, 10, 0.6),
+                     (2, 6, 16, 0.9), (1, 12, 16, 0.7)]
+        for li, xs, y, a in lines:
+            l = lengths[li]
+            c[edgelet_atom_index(nx, ny, 1, li, 0, xs + (l - 1) // 2, y)] = a
+        return lengths, angles, c
+    raise ValueError(kind)
+
+
 def sparse_coefficients(m: int, frac: float, rng: np.random.Generator,
                         k: Optional[int] = None) -> np.ndarray:
     """k-sparse complex vector: |a| ~ U(0.5, 1), arg a ~ U[0, 2pi)."""

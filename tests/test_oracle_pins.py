@@ -445,3 +445,17 @@ def test_edgelet_dictionary_counts_order_and_paper_square():
     want[y0:y0 + 4, x0] += 1
     want[y0:y0 + 4, x0 + 3] += 1
     assert np.array_equal(img, want)
+
+
+def test_paper_scenes_have_the_ideal_atom_counts():
+    # §IV-A: the ideal numbers of coefficients are 4, 8, 5 and 5
+    for kind, ideal, pixels in (("square", 4, 12), ("two_squares", 8, 24),
+                                ("lines_spaced", 5, 22), ("lines_adjoined", 5, 22)):
+        lengths, angles, c = synth.paper_scene(kind, 32, 32)
+        assert np.count_nonzero(c) == ideal
+        img = orc.edgelet_dictionary(32, 32, lengths, angles) @ c.real
+        assert np.count_nonzero(img) == pixels
+    # the pulse selection keeps about p of the positions, within the arc
+    t = synth.sampled_track(1000, 4000.0, 1000.0, 2.0, 0.3, 7)
+    assert 250 <= len(t) <= 350
+    assert np.allclose(np.hypot(t[:, 0], t[:, 1]), 4000.0) and np.allclose(t[:, 2], 1000.0)
