@@ -209,6 +209,17 @@ osar_status osar_push_pulse(osar_ctx* ctx, const double gamma_xyz[3],
 osar_status osar_push_pulse_dev(osar_ctx* ctx, const double gamma_xyz[3],
                                 const void* d_dev_c128);
 
+/* A pulse with non-white noise (Eq. 12 with R_n = diag(noise_var)):
+   noise_var holds the K (n_freq) noise variances of this pulse's
+   frequencies, finite and > 0 (host, copied).  Its update is
+   G_n^H R_n^{-1} G_n and G_n^H R_n^{-1} d_n: the library scales the data and
+   the rows of the pulse's phase block by 1 / sqrt(noise_var[k]), so the
+   dictionary products, Gram update and data update run unchanged.
+   noise_var = NULL is osar_push_pulse (R_n = I).  Otherwise as
+   osar_push_pulse. */
+osar_status osar_push_pulse_var(osar_ctx* ctx, const double gamma_xyz[3],
+                                const double* d_c128, const double* noise_var);
+
 /* Run up to max_iters steps of Algorithm 1's inner loop.  The first call
    after a pulse starts the burst (c^(0) = c_hat_{n-1}, z^(1) = c^(0),
    t_1 = t_{n-1}, or 1 at the first pulse); later calls continue it, so

@@ -17,7 +17,9 @@ Readings taken where the paper is silent, ambiguous or garbled:
   simulation and inversion);
 * frequencies f_m = linspace(f_lo, f_hi, K), both ends inclusive (the N_r
   fast-time samples of §II read as K frequency samples); amplitude A = 1;
-* R_n = I (white noise), so Eq. 12 becomes dA = G^H G, db = G^H d;
+* R_n = I (white noise), so Eq. 12 becomes dA = G^H G, db = G^H d, unless
+  a pulse gives its K noise variances (R_n diagonal: frequencies with
+  independent noise; a full covariance is not taken);
 * the threshold of Algorithm 1 is S_{lambda tau} (the printed "t tau" is read
   as a typo) and the shrinkage is the complex one,
   S_a(u) = u max(0, 1 - a / |u|), which is 0 whenever |u| <= a;
@@ -144,14 +146,20 @@ def simulate_pulse(a_s: np.ndarray, c_true: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 
-def gram_increment(a_s: np.ndarray) -> np.ndarray:
-    """dA_n = G_n^H R_n^{-1} G_n with R_n = I (Eq. 12)."""
-    return a_s.conj().T @ a_s
+def gram_increment(a_s: np.ndarray, noise_var=None) -> np.ndarray:
+    """dA_n = G_n^H R_n^{-1} G_n (Eq. 12); R_n = diag(noise_var), or I."""
+    if noise_var is None:
+        return a_s.conj().T @ a_s
+    r_inv = np.diag(1.0 / np.asarray(noise_var, dtype=np.float64))
+    return a_s.conj().T @ r_inv @ a_s
 
 
-def data_increment(a_s: np.ndarray, d_s: np.ndarray) -> np.ndarray:
-    """db_n = G_n^H R_n^{-1} d_n with R_n = I (Eq. 12)."""
-    return a_s.conj().T @ d_s
+def data_increment(a_s: np.ndarray, d_s: np.ndarray, noise_var=None) -> np.ndarray:
+    """db_n = G_n^H R_n^{-1} d_n (Eq. 12); R_n = diag(noise_var), or I."""
+    if noise_var is None:
+        return a_s.conj().T @ d_s
+    r_inv = np.diag(1.0 / np.asarray(noise_var, dtype=np.float64))
+    return a_s.conj().T @ r_inv @ d_s
 
 
 def smooth_part(blocks, data, c) -> float:
@@ -347,11 +355,13 @@ class OnlineFista:
         return forward_block(phase_matrix(gamma, self.x, self.f),
                              self.cfg.dictionary)
 
-    def push_pulse(self, gamma, d_s) -> None:
+    def push_pulse(self, gamma, d_s, noise_var=None) -> None:
+        """One pulse; noise_var: the K variances of a non-white pulse
+        (R_n = diag(noise_var)), None for R_n = I."""
         s, cfg = self.s, self.cfg
         a_s = self.block(gamma)
-        s.gram = s.gram + gram_increment(a_s)            # Eq. 13
-        s.b = s.b + data_increment(a_s, d_s)             # Eq. 13
+        s.gram = s.gram + gram_increment(a_s, noise_var)         # Eq. 13
+        s.b = s.b + data_increment(a_s, d_s, noise_var)          # Eq. 13
         s.n += 1
         if cfg.lambda_relative:
             s.lam = cfg.lam * float(np.max(np.abs(s.b)))

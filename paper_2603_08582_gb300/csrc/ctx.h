@@ -169,6 +169,16 @@ struct osar_ctx {
   float2* corr = nullptr;              // A_n^H A_n x per partial set (2 x Mp)
   float2* corr_u = nullptr;            // A_n x: nb block partials, then the sum
   unsigned* corr_tick = nullptr;       // last-CTA ticket of the A_n x sums
+  // non-white pulses (osar_push_pulse_var): weights 1 / sigma_k in a pinned
+  // host ring, copied on the synthesis stream into a device slot by pulse
+  // parity; synth_w is the slot the phase kernels of the synthesis being
+  // queued scale their rows by (nullptr: white)
+  double* h_wring = nullptr;          // RING x Kp pinned
+  cudaEvent_t w_ev[8] = {};
+  int w_pos = 0;
+  int w_slot = -1;                    // host slot of the push in progress
+  double* wk_dev = nullptr;           // 2 x Kp device
+  const double* synth_w = nullptr;
   // osar_get_coeffs_async completion events (OSAR_COPY_SLOTS)
   cudaEvent_t copy_ev[4] = {};
   // pinned staging ring for pulse data (slots of Kp complex)

@@ -76,9 +76,12 @@ __device__ __forceinline__ float2 phase_entry<float2>(uint64_t turn) {
 // dictionary is the identity so that the block is written in the K-contiguous
 // layout the Gram update reads.  Otherwise out[m][p] (ld = Np, rows Kp).
 // Each thread writes 8 consecutive entries along the contiguous axis.
+// wk (nullable): per-frequency weights 1 / sigma_k of a non-white pulse, the
+// rows of R_n^{-1/2} F (Eq. 12 with R_n = diag(sigma_k^2)).
 template <typename T2, bool PIXEL_MAJOR>
 __global__ void k_phase_complex(const ulonglong2* __restrict__ turns, int N,
-                                int K, int rows, int ld, T2* __restrict__ out) {
+                                int K, int rows, int ld, T2* __restrict__ out,
+                                const double* __restrict__ wk) {
   const int groups = ld / 8;
   int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= (int64_t)rows * groups) return;
@@ -94,6 +97,10 @@ __global__ void k_phase_complex(const ulonglong2* __restrict__ turns, int N,
       T2 v;
       if (p < N && m < K) {
         v = phase_entry<T2>(tp.x + (uint64_t)m * tp.y);
+        if (wk) {
+          v.x *= wk[m];
+          v.y *= wk[m];
+        }
       } else {
         v.x = 0; v.y = 0;
       }
@@ -101,6 +108,7 @@ __global__ void k_phase_complex(const ulonglong2* __restrict__ turns, int N,
     }
   } else {
     const int m = row;
+    const double w = wk && m < K ? wk[m] : 1.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       int p = col0 + q;
@@ -108,6 +116,10 @@ __global__ void k_phase_complex(const ulonglong2* __restrict__ turns, int N,
       if (p < N && m < K) {
         ulonglong2 tp = turns[p];
         v = phase_entry<T2>(tp.x + (uint64_t)m * tp.y);
+        if (wk) {
+          v.x *= w;
+          v.y *= w;
+        }
       } else {
         v.x = 0; v.y = 0;
       }
@@ -120,7 +132,8 @@ __global__ void k_phase_complex(const ulonglong2* __restrict__ turns, int N,
 template <bool PIXEL_MAJOR>
 __global__ void k_phase_planes(const ulonglong2* __restrict__ turns, int N,
                                int K, int rows, int ld,
-                               __nv_bfloat16* __restrict__ planes) {
+                               __nv_bfloat16* __restrict__ planes,
+                               const double* __restrict__ wk) {
   const int groups = ld / 8;
   const int64_t plane = (int64_t)rows * ld;
   // grid-stride: a capped grid leaves SMs to the burst running beside it
@@ -139,6 +152,11 @@ __global__ void k_phase_planes(const ulonglong2* __restrict__ turns, int N,
       if (p < N && m < K) {
         ulonglong2 tp = PIXEL_MAJOR ? tp_row : turns[p];
         e = unit_phase_f32(tp.x + (uint64_t)m * tp.y);
+        if (wk) {
+          const float w = (float)wk[m];
+          e.x *= w;
+          e.y *= w;
+        }
       }
       split_bf16(e.x, v[0][q], v[3][q]);
       split_bf16(e.y, v[1][q], v[4][q]);
@@ -364,34 +382,36 @@ cudaError_t launch_phase(osar_ctx* ctx, int grid_cap) {
     const unsigned gc = blocks_for(work, 256);  // one thread per 8 entries
     if (ctx->prec == OSAR_FP64)
       k_phase_complex<double2, true><<<gc, 256, 0, ctx->stream>>>(
-          ctx->turns, ctx->N, ctx->K, rows, ld, (double2*)ctx->F);
+          ctx->turns, ctx->N, ctx->K, rows, ld, (double2*)ctx->F, ctx->synth_w);
     else
       k_phase_complex<float2, true><<<gc, 256, 0, ctx->stream>>>(
-          ctx->turns, ctx->N, ctx->K, rows, ld, (float2*)ctx->F);
+          ctx->turns, ctx->N, ctx->K, rows, ld, (float2*)ctx->F, ctx->synth_w);
   } else if (ctx->prec == OSAR_SPLIT_BF16) {
     __nv_bfloat16* out = pix ? ctx->Apl : ctx->Fpl;
     if (pix)
       k_phase_planes<true><<<g, 256, 0, ctx->stream>>>(ctx->turns, ctx->N,
-                                                       ctx->K, rows, ld, out);
+                                                       ctx->K, rows, ld, out,
+                                                       ctx->synth_w);
     else
       k_phase_planes<false><<<g, 256, 0, ctx->stream>>>(ctx->turns, ctx->N,
-                                                        ctx->K, rows, ld, out);
+                                                        ctx->K, rows, ld, out,
+                                                        ctx->synth_w);
   } else if (ctx->prec == OSAR_FP64) {
     double2* out = (double2*)(pix ? ctx->A : ctx->F);
     if (pix)
       k_phase_complex<double2, true><<<g, 256, 0, ctx->stream>>>(
-          ctx->turns, ctx->N, ctx->K, rows, ld, out);
+          ctx->turns, ctx->N, ctx->K, rows, ld, out, ctx->synth_w);
     else
       k_phase_complex<double2, false><<<g, 256, 0, ctx->stream>>>(
-          ctx->turns, ctx->N, ctx->K, rows, ld, out);
+          ctx->turns, ctx->N, ctx->K, rows, ld, out, ctx->synth_w);
   } else {
     float2* out = (float2*)(pix ? ctx->A : ctx->F);
     if (pix)
       k_phase_complex<float2, true><<<g, 256, 0, ctx->stream>>>(
-          ctx->turns, ctx->N, ctx->K, rows, ld, out);
+          ctx->turns, ctx->N, ctx->K, rows, ld, out, ctx->synth_w);
     else
       k_phase_complex<float2, false><<<g, 256, 0, ctx->stream>>>(
-          ctx->turns, ctx->N, ctx->K, rows, ld, out);
+          ctx->turns, ctx->N, ctx->K, rows, ld, out, ctx->synth_w);
   }
   prof_end(ctx, &ev);
   ctx->launches++;

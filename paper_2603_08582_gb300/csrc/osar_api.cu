@@ -68,10 +68,13 @@ void free_all(osar_ctx* ctx) {
                   ctx->dict_pairs, ctx->segpart2, ctx->tilepart2,
                   ctx->segpart_x, ctx->tilepart_x, ctx->gn_hi, ctx->gn_lo,
                   ctx->Apl_alt, ctx->corr, ctx->corr_u, ctx->corr_tick,
-                  ctx->atom_ptr, ctx->atom_pix};
+                  ctx->atom_ptr, ctx->atom_pix, ctx->wk_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+  if (ctx->h_wring) cudaFreeHost(ctx->h_wring);
+  for (cudaEvent_t ev : ctx->w_ev)
+    if (ev) cudaEventDestroy(ev);
   if (ctx->adj_buf) cudaFree(ctx->adj_buf);
   for (int i = 0; i < RING; ++i)
     if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);
@@ -402,12 +405,17 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     AL(ctx->corr_u, 8 * ((int64_t)ctx->nb + 1) * Kp);
     AL(ctx->corr_tick, sizeof(unsigned));
   }
+  AL(ctx->wk_dev, 8 * 2 * Kp);
   AL(ctx->sim_rho, 16 * Np);
   AL(ctx->sim_nz, 16 * Mp);
   AL(ctx->sim_idx, 4 * Mp);
   AL(ctx->sim_d, 16 * Kp);
 #undef AL
   e = cudaMallocHost((void**)&ctx->h_ring, sizeof(double2) * RING * Kp);
+  if (e == cudaSuccess)
+    e = cudaMallocHost((void**)&ctx->h_wring, sizeof(double) * RING * Kp);
+  for (int i = 0; i < RING && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&ctx->w_ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaMallocHost"));
   for (int i = 0; i < RING; ++i) {
     e = cudaEventCreateWithFlags(&ctx->ring_ev[i], cudaEventDisableTiming);
@@ -523,8 +531,20 @@ bool capturing(cudaStream_t s) {
 // Forward block of a pulse (Eq. 4 with the dictionary of Eq. 5): per-pixel
 // phase terms, phase matrix, then A_s = F_s D for dictionary models.
 cudaError_t synthesize_phase(osar_ctx* ctx, const double gamma[3], int grid_cap) {
-  cudaError_t e = launch_pixel_turns(ctx, gamma);
+  cudaError_t e = cudaSuccess;
+  ctx->synth_w = nullptr;
+  if (ctx->w_slot >= 0) {
+    // a non-white pulse: its weights, on the stream of its phases
+    double* dev = ctx->wk_dev + (int64_t)(ctx->n & 1) * ctx->Kp;
+    e = cudaMemcpyAsync(dev, ctx->h_wring + (int64_t)ctx->w_slot * ctx->Kp,
+                        sizeof(double) * ctx->Kp, cudaMemcpyHostToDevice,
+                        ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->w_ev[ctx->w_slot], ctx->stream);
+    ctx->synth_w = dev;
+  }
+  if (e == cudaSuccess) e = launch_pixel_turns(ctx, gamma);
   if (e == cudaSuccess) e = launch_phase(ctx, grid_cap);
+  ctx->synth_w = nullptr;
   return e;
 }
 cudaError_t synthesize_dict(osar_ctx* ctx, int grid_cap) {
@@ -865,6 +885,45 @@ osar_status osar_push_pulse(osar_ctx* ctx, const double gamma_xyz[3],
                           cudaMemcpyHostToDevice, ctx->stream));
   CK(ctx, cudaEventRecord(ctx->ring_ev[slot], ctx->stream));
   return push_impl(ctx, gamma_xyz, idle);
+}
+
+osar_status osar_push_pulse_var(osar_ctx* ctx, const double gamma_xyz[3],
+                                const double* d_c128, const double* noise_var) {
+  osar::TraceRange trace_("osar_push_pulse_var");
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (!gamma_xyz || !d_c128)
+    return fail(ctx, OSAR_E_INVALID, "osar_push_pulse_var: NULL argument");
+  if (!noise_var) return osar_push_pulse(ctx, gamma_xyz, d_c128);
+  for (int i = 0; i < 3; ++i)
+    if (!is_finite(gamma_xyz[i]))
+      return fail(ctx, OSAR_E_INVALID, "osar_push_pulse_var: non-finite gamma");
+  for (int k = 0; k < ctx->K; ++k)
+    if (!is_finite(noise_var[k]) || !(noise_var[k] > 0.0))
+      return fail(ctx, OSAR_E_INVALID,
+                  "osar_push_pulse_var: noise variances must be finite and > 0");
+  const bool idle = main_idle(ctx);
+  // weights 1 / sigma_k for the phases (host ring slot)
+  const int ws = ctx->w_pos;
+  ctx->w_pos = (ctx->w_pos + 1) % RING;
+  CK(ctx, cudaEventSynchronize(ctx->w_ev[ws]));
+  double* w = ctx->h_wring + (size_t)ws * ctx->Kp;
+  for (int k = 0; k < ctx->Kp; ++k)
+    w[k] = k < ctx->K ? 1.0 / std::sqrt(noise_var[k]) : 0.0;
+  // the whitened data R_n^{-1/2} d
+  const int slot = ctx->ring_pos;
+  ctx->ring_pos = (ctx->ring_pos + 1) % RING;
+  CK(ctx, cudaEventSynchronize(ctx->ring_ev[slot]));
+  double2* h = ctx->h_ring + (size_t)slot * ctx->Kp;
+  for (int k = 0; k < ctx->K; ++k)
+    h[k] = make_double2(d_c128[2 * k] * w[k], d_c128[2 * k + 1] * w[k]);
+  CK(ctx, cudaMemcpyAsync(ctx->d_dev, h, sizeof(double2) * ctx->K,
+                          cudaMemcpyHostToDevice, ctx->stream));
+  CK(ctx, cudaEventRecord(ctx->ring_ev[slot], ctx->stream));
+  ctx->w_slot = ws;
+  st = push_impl(ctx, gamma_xyz, idle);
+  ctx->w_slot = -1;
+  return st;
 }
 
 osar_status osar_push_pulse_dev(osar_ctx* ctx, const double gamma_xyz[3],

@@ -31,6 +31,7 @@ KERNEL_CLASSES = {"phase": 0, "dict_gemm": 1, "gram_gemm": 2, "data_update": 3,
 # Symbols declared in include/osar.h (checked by the CPU test suite).
 EXPORTS = [
     "osar_config_default", "osar_create", "osar_destroy", "osar_push_pulse",
+    "osar_push_pulse_var",
     "osar_push_pulse_dev", "osar_iterate", "osar_get_coeffs",
     "osar_get_coeffs_dev", "osar_get_coeffs_async", "osar_wait_coeffs",
     "osar_get_lambda_state",
@@ -101,6 +102,7 @@ def load_library(path: str = LIB_PATH):
         "osar_destroy": (I32, [P]),
         "osar_push_pulse": (I32, [P, D, D]),
         "osar_push_pulse_dev": (I32, [P, D, P]),
+        "osar_push_pulse_var": (I32, [P, D, D, D]),
         "osar_iterate": (I32, [P, I32, C.c_double, C.POINTER(I32)]),
         "osar_get_coeffs": (I32, [P, D]),
         "osar_get_coeffs_dev": (I32, [P, P]),
@@ -276,12 +278,22 @@ class Osar:
         return self._h
 
     # -- Eqs. 12-13 and Algorithm 1 ---------------------------------------
-    def push_pulse(self, gamma, d):
+    def push_pulse(self, gamma, d, noise_var=None):
+        """One pulse; noise_var: its n_freq noise variances (R_n diagonal),
+        None for white noise."""
         g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))
         dv = _c128(d)
         if dv.size != self.n_freq or g.size != 3:
             raise ValueError("gamma must have 3 entries and d n_freq entries")
-        self._check(self._lib.osar_push_pulse(self._h, _dptr(g), _dptr(dv.view(np.float64))))
+        if noise_var is None:
+            self._check(self._lib.osar_push_pulse(self._h, _dptr(g),
+                                                  _dptr(dv.view(np.float64))))
+            return
+        vv = np.ascontiguousarray(np.asarray(noise_var, dtype=np.float64))
+        if vv.size != self.n_freq:
+            raise ValueError("noise_var needs n_freq entries")
+        self._check(self._lib.osar_push_pulse_var(self._h, _dptr(g),
+                                                  _dptr(dv.view(np.float64)), _dptr(vv)))
 
     def push_pulse_dev(self, gamma, d_dev_ptr: int):
         g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))

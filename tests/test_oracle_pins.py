@@ -459,3 +459,22 @@ def test_paper_scenes_have_the_ideal_atom_counts():
     t = synth.sampled_track(1000, 4000.0, 1000.0, 2.0, 0.3, 7)
     assert 250 <= len(t) <= 350
     assert np.allclose(np.hypot(t[:, 0], t[:, 1]), 4000.0) and np.allclose(t[:, 2], 1000.0)
+
+
+def test_non_white_increments_are_the_weighted_sums():
+    # Eq. 12 with R_n = diag(var): entrywise sums with weights 1 / var_k, and
+    # a constant variance scales the white increments
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((6, 4)) + 1j * rng.standard_normal((6, 4))
+    d = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    var = rng.uniform(0.5, 3.0, 6)
+    g = orc.gram_increment(a, var)
+    for i in range(4):
+        for j in range(4):
+            want = sum(np.conj(a[k, i]) * a[k, j] / var[k] for k in range(6))
+            assert abs(g[i, j] - want) <= 1e-12 * max(1.0, abs(want))
+    b = orc.data_increment(a, d, var)
+    assert np.allclose(b, [sum(np.conj(a[k, i]) * d[k] / var[k] for k in range(6))
+                           for i in range(4)], rtol=1e-13, atol=0)
+    assert np.allclose(orc.gram_increment(a, np.full(6, 4.0)),
+                       orc.gram_increment(a) / 4.0, rtol=1e-13, atol=0)
