@@ -712,11 +712,20 @@ def run_edgelet_forms(stream):
             reached = s + 1
             break
     wall = time.perf_counter() - e0
-    big = np.flatnonzero(np.abs(ctx.coeffs()) > 2e-2)
+    c_hat = ctx.coeffs()
+    big = np.flatnonzero(np.abs(c_hat) > 2e-2)
+    sup = np.abs(c_true) > 0
+    # the SNR of the experiments (20 log10 of signal over noise amplitude),
+    # read in the coefficient domain: the estimate on the scene's atoms
+    # against the rest (RMS)
+    rms_s = float(np.sqrt(np.mean(np.abs(c_hat[sup]) ** 2)))
+    rms_n = float(np.sqrt(np.mean(np.abs(c_hat[~sup]) ** 2)))
+    snr_db = 20.0 * np.log10(rms_s / rms_n) if rms_n > 0 else float("inf")
     out["paper_scene1_32x32_split_bf16"] = {
         "positions": 1000, "pulses_available": int(len(track)),
         "pulses_to_ideal_count": reached, "final_count": counts[-1],
         "large_are_the_true_atoms": bool(set(big) == set(np.flatnonzero(c_true))),
+        "coefficient_snr_db": round(snr_db, 1),
         "count_after_pulses": {str(k): counts[k - 1] for k in (1, 5, 10, 20, 50, 100)
                                if k <= len(counts)},
         "ms_per_pulse_with_readback": round(1e3 * wall / len(counts), 3)}
