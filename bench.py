@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-fuse", action="store_true",
                     help="separate Gram passes for the last power step and "
                          "the first FISTA step of a pulse")
+    ap.add_argument("--fuse-power-gram", type=int, choices=[0, 1], default=1,
+                    help="1: the Gram update's epilogue also forms the "
+                         "pulse's first power step (one Gram pass fewer)")
     ap.add_argument("--tc-pairs", type=int, default=3,
                     help="tensor-core products on SM pairs: bit 0 dictionary "
                          "product, bit 1 Gram update (0: one SM per tile)")
@@ -211,7 +214,7 @@ def workload(name="c2"):
 
 
 def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
-             fuse=True, defer=False):
+             fuse=True, defer=False, power_gram=True):
     from paper_2603_08582_gb300 import osar
     gauss = w.dictionary == "gaussian"
     cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
@@ -223,7 +226,8 @@ def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
                            synth_ctas=synth_ctas, tc_pairs=tc_pairs,
                            fuse_first_step=fuse,
                            defer_gram=(defer and overlap and gauss
-                                       and precision == "split_bf16"))
+                                       and precision == "split_bf16"),
+                           fuse_power_gram=power_gram)
     return osar.Osar(cfg)
 
 
@@ -259,8 +263,11 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     ov = dict(overlap=not args.no_overlap, synth_ctas=args.synth_ctas,
               tc_pairs=args.tc_pairs, fuse=not args.no_fuse,
-              defer=bool(args.defer_gram) and not args.no_overlap)
+              defer=bool(args.defer_gram) and not args.no_overlap,
+              power_gram=bool(args.fuse_power_gram))
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
+    # power steps per pulse that are Gram passes of their own
+    power_passes = POWER_ITERS - (1 if ov["power_gram"] and not ov["defer"] else 0)
     total = W + K + 1
     track, data = pulse_data(ctx, w, total)
     d_dev = torch.from_numpy(data).to(f"cuda:{local_rank}")
@@ -346,7 +353,7 @@ def run_ours(args):
                 ctx_e.wait_coeffs((q - 1) % 2)
         ctx_e.wait_coeffs((K - 1) % 2)
         e2e_s = time.perf_counter() - t0
-        fista_steps = (ctx_e.profile_passes() - K * POWER_ITERS
+        fista_steps = (ctx_e.profile_passes() - K * power_passes
                        + (0 if args.no_fuse else K))
         ctx_e.close()
 
@@ -432,6 +439,7 @@ def run_ours(args):
                    "tc_pairs": {0: "off", 1: "dictionary product", 2: "Gram update",
                                 3: "dictionary product and Gram update"}[args.tc_pairs & 3],
                    "fused_first_step": not args.no_fuse,
+                   "power_step_in_gram_update": bool(args.fuse_power_gram) and not ov["defer"],
                    "deferred_gram_update": bool(ov["defer"]),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (packed Gram 4.3 GB streamed per step)"},
@@ -441,9 +449,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": w.m_atoms * 16 + 4,
                 "mean_iters_per_pulse": round(fista_steps / K, 2),
                 "pipelined": "image of pulse s read while pulse s+1 is queued"},
-        # Gram passes per pulse: the power steps, plus the FISTA steps less
-        # the first one when it shares the last power step's pass
-        "mean_iters_per_pulse": round((passes - K * POWER_ITERS) / K
+        # Gram passes per pulse: the power steps (less the first one when
+        # the Gram update forms it), plus the FISTA steps less the first one
+        # when it shares the last power step's pass
+        "mean_iters_per_pulse": round((passes - K * power_passes) / K
                                       + (0 if args.no_fuse else 1), 2),
         "time_to_tol": ttt,
         "gpu_launches": int(launches),

@@ -177,6 +177,16 @@ typedef struct {
   const int32_t* edgelet_lengths;
   int32_t n_edgelet_angles;
   const double* edgelet_angles_deg;
+  /* SPLIT_BF16 with the Gram update on SM pairs (tc_pairs bit 1), defer_gram
+     = 0.  1: the Gram update's epilogue, which holds each updated 128 x 128
+     block of G_n, also applies it to the power vector v (Eq. 11: the first
+     power step of the pulse), so that step reads no Gram: one Gram pass fewer
+     per pulse.  The partial sums are combined in a fixed order (results do
+     not depend on the grid) but in another order than a separate pass, so
+     mu_n, L_n and the iterates agree with 0 to rounding, not bitwise.  0:
+     every power step is a separate pass.  Ignored on the other paths.
+     Default 1. */
+  int32_t fuse_power_gram;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
@@ -184,7 +194,7 @@ typedef struct {
    30 / 4 power steps, margin 0.01, carried momentum, compensated = 1,
    overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
    (both tensor-core products on SM pairs), fuse_first_step = 1,
-   n_lambdas = 1, defer_gram = 0, guard_bytes = 0. */
+   n_lambdas = 1, defer_gram = 0, guard_bytes = 0, fuse_power_gram = 1. */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128

@@ -112,6 +112,10 @@ struct osar_ctx {
   void* segpart_x = nullptr;   // lambda path: partials of solutions 2..
   void* tilepart_x = nullptr;
   bool first_ready = false;    // segpart2 / tilepart2 hold G z_1 for the burst
+  float2* gp_col = nullptr;    // Gram update's fused power step: column
+  float2* gp_row = nullptr;    // partials (nblk x BLK), half-row partials
+                               // (nblk x 2 x BLK)
+  bool gp_ready = false;       // gp_col / gp_row hold G_n v for the first power step
   int4* segs = nullptr;        // matvec work items (J, I0, I1, slot)
   int* seg_begin = nullptr;    // first segment of block column J (nb + 1)
   double* bmax = nullptr;      // per-block max |b_j|^2 (data update)
@@ -255,9 +259,12 @@ bool make_tensor_maps(osar_ctx* ctx, std::string* err);
 cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap);
 int dict_slices(int np);
 // G += A^H A in place, or, with dst_hi set, dst = G + A^H A (G unchanged);
-// grid_cap > 0: at most that many SMs
+// grid_cap > 0: at most that many SMs.  power: where the context holds the
+// buffers (gp_col), the update also forms the partials of G_n v for the
+// pulse's first power step and sets gp_ready.
 cudaError_t launch_gram_tc(osar_ctx* ctx, void* dst_hi = nullptr,
-                           __nv_bfloat162* dst_lo = nullptr, int grid_cap = 0);
+                           __nv_bfloat162* dst_lo = nullptr, int grid_cap = 0,
+                           bool power = false);
 
 // ---- k_fista.cu ------------------------------------------------------------
 cudaError_t launch_data_update(osar_ctx* ctx);

@@ -115,8 +115,10 @@ __global__ void __launch_bounds__(FIN_THREADS)
 
 // Power step: w = A v; the last CTA forms mu = Re(v^H A v) (v has unit
 // norm) and 1/|w|, and on the last step of a pulse sets
-// L_n = max(L_{n-1}, (1 + margin) mu) and tau = 1/L_n.
-template <typename T2, typename Acc>
+// L_n = max(L_{n-1}, (1 + margin) mu) and tau = 1/L_n.  FROM_GRAM: A v
+// comes from the Gram update's fused power step (segpart / tilepart are
+// its column / half-row partials; no Gram pass is counted).
+template <typename T2, typename Acc, bool FROM_GRAM = false>
 __global__ void __launch_bounds__(FIN_THREADS)
     k_power_finalize(const T2* __restrict__ segpart,
                      const T2* __restrict__ tilepart,
@@ -125,7 +127,11 @@ __global__ void __launch_bounds__(FIN_THREADS)
                      double2* __restrict__ part, DevScalars* sc, int last_step,
                      double margin, const float2* __restrict__ corr) {
   const int K = blockIdx.x, i = threadIdx.x, idx = K * BLK + i;
-  const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K, corr);
+  double2 y;
+  if constexpr (FROM_GRAM)
+    y = gather_gram_row(segpart, tilepart, nb, K);
+  else
+    y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K, corr);
   double p0 = 0.0, p1 = 0.0;
   if (i < BLK) {
     w[idx] = y;
@@ -146,7 +152,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
       if (l > sc->lip) sc->lip = l;
       sc->tau = sc->lip > 0.0 ? 1.0 / sc->lip : 0.0;
     }
-    sc->passes += 1;
+    if (!FROM_GRAM) sc->passes += 1;
     sc->done = 0;
   }
 }
@@ -548,9 +554,26 @@ cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
   // the FP64 path keeps separate passes: two FP64 vectors' partial sums do
   // not fit the matvec's registers; a lambda path pairs its own solutions
   fuse = fuse && ctx->prec != OSAR_FP64 && ctx->n_lam == 1;
+  // the Gram update just formed G_n v (first step, no pass of its own)
+  const bool from_gram = ctx->gp_ready;
+  ctx->gp_ready = false;
+  bool fused_last = false;
   for (int s = 0; s < steps; ++s) {
     const int last = s == steps - 1 ? 1 : 0;
+    if (s == 0 && from_gram) {
+      ProfEvent ev;
+      prof_begin(ctx, KCL_POWFIN, &ev);
+      k_power_finalize<float2, float, true><<<nb, FIN_THREADS, 0, ctx->stream>>>(
+          ctx->gp_col, ctx->gp_row, nullptr, ctx->nb, ctx->v, ctx->w,
+          ctx->part, ctx->scal, last, ctx->cfg.lipschitz_margin, nullptr);
+      k_power_normalize<float2><<<nb, BLK, 0, ctx->stream>>>(
+          ctx->w, ctx->v, (float2*)ctx->vt, ctx->Mp, ctx->scal);
+      prof_end(ctx, &ev);
+      ctx->launches += 2;
+      continue;
+    }
     if (last && fuse) {
+      fused_last = true;
       // the burst that follows starts from z = c_hat: apply the Gram to it
       // in the same pass as the last power step
       cudaError_t e = launch_burst_begin(ctx);
@@ -593,7 +616,7 @@ cudaError_t launch_power_steps(osar_ctx* ctx, int steps, bool fuse) {
     prof_end(ctx, &ev);
     ctx->launches += 2;
   }
-  if (fuse && steps > 0) {
+  if (fused_last) {
     ctx->first_ready = true;
     ctx->fresh = false;
   }
@@ -630,6 +653,7 @@ cudaError_t prepare_burst_kernels() {
   set((const void*)k_fista_finalize<float2, float>);
   set((const void*)k_fista_finalize<double2, double>);
   set((const void*)k_power_finalize<float2, float>);
+  set((const void*)k_power_finalize<float2, float, true>);
   set((const void*)k_power_finalize<double2, double>);
   set((const void*)k_power_normalize<float2>);
   set((const void*)k_power_normalize<double2>);

@@ -36,7 +36,10 @@
 // rows and one of the two B planes (32 KB per ring slot instead of 48 KB, 7
 // slots); in Gram mode the ring keeps 5 slots and the Gram read-modify-write
 // is staged through the rest of the shared memory by bulk copies in
-// 8-column pieces; see k_tc_cgemm<true>.
+// 8-column pieces; see k_tc_cgemm<true>.  There the epilogue can also apply
+// each updated block of G_n to the power vector (the pulse's first power
+// step, Eq. 11): row partials T x_J and column partials T^H x_I per block,
+// which a finalize kernel sums per output block, so that step reads no Gram.
 //
 // Accumulation in the tensor pipe rounds its FP32 partial sums toward zero,
 // which biases long reductions (|A| shrinks by ~(steps) 2^-24).  The
@@ -86,9 +89,16 @@ struct TcCfg {
 };
 static_assert(TcCfg<true>::SMEM <= 227 * 1024 && TcCfg<false>::SMEM <= 227 * 1024,
               "tcgen05 ring exceeds shared memory");
-static_assert(PAIR_GRAM_STAGES * TcCfg<true>::STAGE_BYTES + 4 * G_SLOT <=
+// Fused power step (TcParams::pv): per tile parity and half, the 4 warps'
+// column sums of their 32 rows (128 floats each), combined after the tile,
+// and the half's 64 entries of x_J.
+constexpr int PW_RED_BYTES = 2 * 2 * 4 * BLK * 4;  // 8 KB
+constexpr int PW_X_BYTES = 2 * 2 * 64 * 8;         // 2 KB
+static_assert(PAIR_GRAM_STAGES * TcCfg<true>::STAGE_BYTES + 4 * G_SLOT +
+                      PW_RED_BYTES + PW_X_BYTES <=
                   TcCfg<true>::STAGES * TcCfg<true>::STAGE_BYTES,
               "staged Gram epilogue does not fit beside the operand ring");
+static_assert(G_COLS == 8, "the fused power step reduces 8-column pieces");
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 struct TcParams {
@@ -110,6 +120,15 @@ struct TcParams {
   __nv_bfloat162* g_lo;  // compensation word, bf16 (re, im), or NULL
   const float2* gs_hi;   // the Gram read (g_hi for an update in place)
   const __nv_bfloat162* gs_lo;
+  // Fused power step on the updated Gram (pair kernel, Gram mode), or NULL:
+  // w = G x for x = pv (FP32, Mp entries).  Per stored block (I, J):
+  //   pcol[blk][c]        = sum_r conj(T[r][c]) x_I[r]   (all 128 columns;
+  //                         on a diagonal block the block's whole product)
+  //   prow[blk][h][r]     = sum over the 64 columns c of half h of T[r][c] x_J[c]
+  //                         (off-diagonal blocks only)
+  const float2* pv;
+  float2* pcol;
+  float2* prow;
   int nb;
   int* err;
 };
@@ -121,9 +140,9 @@ struct TcParams {
 // 2^-17 of the split-BF16 products, and saves a quarter of the traffic.)
 // Blocks are column-major, so entry (row, c) is at c * 128 + row and the 32
 // lanes of a warp (32 consecutive rows) touch contiguous bytes per access.
-template <int W>
+template <int W, bool KEEP = false>
 __device__ __forceinline__ void gram_piece(float2* gh, __nv_bfloat162* gl,
-                                           const float2 (&h)[W],
+                                           float2 (&h)[W],
                                            const __nv_bfloat162 (&l)[W],
                                            const float* re, const float* im,
                                            bool comp) {
@@ -142,7 +161,50 @@ __device__ __forceinline__ void gram_piece(float2* gh, __nv_bfloat162* gl,
       hv.y += im[q];
     }
     gh[q * BLK] = hv;
+    if (KEEP) h[q] = hv;  // the updated entry, for a fused power step
   }
+}
+
+// One 8-column piece of the fused power step for this thread's row r of
+// block (I, J), h = the updated entries T[r][c0 .. c0+7]:
+//   racc += sum_c T[r][c] x_J[c]                        (row partial)
+//   red[j] = sum over the warp's 32 rows of conj(T[r][c]) x_I[r]
+// for the piece's 16 floats j = 2 c + (0: re, 1: im).  The column sums are
+// a butterfly reduce-scatter: after halving over lane bits 4..1 and a final
+// exchange over bit 0, lanes 2j and 2j + 1 both hold float j.
+__device__ __forceinline__ void power_piece(const float2 (&h)[8], float2 xi,
+                                            const float2* xj_src, int lane,
+                                            float2& racc, float* red) {
+  float2 xj[8];  // x_J[c0 .. c0+7], from shared memory (one broadcast each)
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = reinterpret_cast<const float4*>(xj_src)[k];
+    xj[2 * k] = make_float2(v.x, v.y);
+    xj[2 * k + 1] = make_float2(v.z, v.w);
+  }
+  float v[16];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    racc.x = fmaf(h[c].x, xj[c].x, racc.x);
+    racc.x = fmaf(-h[c].y, xj[c].y, racc.x);
+    racc.y = fmaf(h[c].x, xj[c].y, racc.y);
+    racc.y = fmaf(h[c].y, xj[c].x, racc.y);
+    v[2 * c] = fmaf(h[c].x, xi.x, h[c].y * xi.y);
+    v[2 * c + 1] = fmaf(h[c].x, xi.y, -(h[c].y * xi.x));
+  }
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1) {
+    const int bit = w * 2;  // lane bit 4, 3, 2, 1
+    const bool up = (lane & bit) != 0;
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const float send = up ? v[k] : v[k + w];
+      const float keep = up ? v[k + w] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  if ((lane & 1) == 0) red[lane >> 1] = v[0];
 }
 
 __device__ __forceinline__ void load_piece(const float2* gh,
@@ -404,6 +466,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bulk_load(dst, p.gs_hi + off, G_PIECE_HI, &gf[b]);
       if (comp) bulk_load(dst + G_PIECE_HI, p.gs_lo + off, G_PIECE_LO, &gf[b]);
     };
+    // fused power step: this half's column-sum buffers (one per tile parity)
+    const bool pw = p.pv != nullptr;
+    float* pw_red = reinterpret_cast<float*>(
+        smem + PAIR_GRAM_STAGES * C::STAGE_BYTES + 4 * G_SLOT);
+    float2* pw_x = reinterpret_cast<float2*>(
+        smem + PAIR_GRAM_STAGES * C::STAGE_BYTES + 4 * G_SLOT + PW_RED_BYTES);
+    int tcount = 0;
     uint32_t issued[2] = {0, 0};
     if (loader && unit < p.n_tiles) {
       issue(unit, 0, 0);
@@ -417,8 +486,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // The 4 warps of a half pass the same barriers: every tile they enter
     // has G_PIECES barriers, and whether to stop is the OR over the half, taken at
     // a barrier, so all of them leave together.
-    for (int t = unit; t < p.n_tiles; t += units) {
-      const bool store = !(rank && (p.tiles[t].w & 1));
+    for (int t = unit; t < p.n_tiles; t += units, ++tcount) {
+      const int4 tl = p.tiles[t];
+      const bool store = !(rank && (tl.w & 1));
+      const int ti = rank ? tl.z : tl.x, tj = tl.y & 0xFFFF;
+      float* red = pw_red + ((tcount & 1) * 2 + colh) * 4 * BLK;
+      float2* xs = pw_x + ((tcount & 1) * 2 + colh) * 64;
+      float2 xi = make_float2(0.f, 0.f), racc = make_float2(0.f, 0.f);
+      if (pw && store) {
+        // x_I for this row; the half's x_J to shared memory, seen by its
+        // 4 warps after the first piece's barrier
+        xi = p.pv[ti * BLK + row];
+        if (row < 64) xs[row] = p.pv[tj * BLK + colh * 64 + row];
+      }
       if (!mbar_wait_bounded(&tfull[acc], aph, abort_flag, p.err,
                              WAIT_LIMIT_NS))
         fail = true;
@@ -427,6 +507,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_fence_after();
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) +
                             (uint32_t)acc * 256u + (uint32_t)colh * 64u;
+      float2 h[G_COLS];  // the piece's updated entries of this thread's row
       for (int pc = 0; pc < G_PIECES; ++pc, ++n) {
         const int b = n & 1;
         const uint32_t gph = (uint32_t)(n >> 1) & 1u;
@@ -453,7 +534,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           float2* hs = reinterpret_cast<float2*>(sl) + row;
           __nv_bfloat162* ls =
               reinterpret_cast<__nv_bfloat162*>(sl + G_PIECE_HI) + row;
-          float2 h[G_COLS];
           __nv_bfloat162 l[G_COLS];
 #pragma unroll
           for (int c = 0; c < G_COLS; ++c) h[c] = hs[c * BLK];
@@ -461,7 +541,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int c = 0; c < G_COLS; ++c) l[c] = ls[c * BLK];
           }
-          gram_piece<G_COLS>(hs, comp ? ls : nullptr, h, l, re, im, comp);
+          gram_piece<G_COLS, true>(hs, comp ? ls : nullptr, h, l, re, im, comp);
           fence_proxy_async();  // the bulk store reads what was written here
         }
         // all 4 warps of the half have updated the piece (or given up)
@@ -486,8 +566,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
         __syncwarp();
+        // the power step's share of the piece, after the copies are issued
+        if (pw && store)
+          power_piece(h, xi, xs + pc * G_COLS, lane, racc,
+                      red + q * BLK + pc * 2 * G_COLS);
       }
       if (fail) break;
+      if (pw && store) {
+        // every warp's column sums are in; the buffers of this parity are
+        // next written two tiles on, after this half's barriers of the tile
+        // between
+        named_barrier(1 + colh, EPI_THREADS / 2);
+        const int64_t blk = packed_block(ti, tj, p.nb);
+        const float s = ((red[row] + red[BLK + row]) + red[2 * BLK + row]) +
+                        red[3 * BLK + row];
+        reinterpret_cast<float*>(p.pcol + blk * BLK + colh * 64)[row] = s;
+        if (ti != tj) p.prow[(blk * 2 + colh) * BLK + row] = racc;
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(&tempty[acc], 0u);
@@ -811,7 +906,7 @@ cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap) {
 }
 
 cudaError_t launch_gram_tc(osar_ctx* ctx, void* dst_hi, __nv_bfloat162* dst_lo,
-                           int grid_cap) {
+                           int grid_cap, bool power) {
   const bool pairs = (ctx->cfg.tc_pairs & 2) != 0;
   TcParams p = {};
   p.tiles = pairs ? ctx->gram_pairs : ctx->gram_tiles;
@@ -828,6 +923,13 @@ cudaError_t launch_gram_tc(osar_ctx* ctx, void* dst_hi, __nv_bfloat162* dst_lo,
   p.g_lo = dst_hi ? dst_lo : ctx->g_lo;
   p.nb = ctx->nb;
   p.err = &ctx->scal->error;
+  ctx->gp_ready = false;
+  if (power && pairs && ctx->gp_col) {
+    p.pv = (const float2*)ctx->vt;
+    p.pcol = ctx->gp_col;
+    p.prow = ctx->gp_row;
+    ctx->gp_ready = true;
+  }
   return launch_tc(ctx, ctx->map_a_rows1,
                    pairs ? ctx->map_a_rows1 : ctx->map_a_rows2, p, KCL_GRAM,
                    pairs, grid_cap);

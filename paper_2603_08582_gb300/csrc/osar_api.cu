@@ -68,7 +68,8 @@ void free_all(osar_ctx* ctx) {
                   ctx->dict_pairs, ctx->segpart2, ctx->tilepart2,
                   ctx->segpart_x, ctx->tilepart_x, ctx->gn_hi, ctx->gn_lo,
                   ctx->Apl_alt, ctx->corr, ctx->corr_u, ctx->corr_tick,
-                  ctx->atom_ptr, ctx->atom_pix, ctx->wk_dev};
+                  ctx->atom_ptr, ctx->atom_pix, ctx->wk_dev, ctx->gp_col,
+                  ctx->gp_row};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
@@ -158,6 +159,8 @@ osar_status validate(const osar_config* c, std::string* why) {
     return *why = "tc_pairs must be in [0, 3]", OSAR_E_INVALID;
   if (c->fuse_first_step != 0 && c->fuse_first_step != 1)
     return *why = "fuse_first_step must be 0 or 1", OSAR_E_INVALID;
+  if (c->fuse_power_gram != 0 && c->fuse_power_gram != 1)
+    return *why = "fuse_power_gram must be 0 or 1", OSAR_E_INVALID;
   if (c->n_lambdas < 1 || c->n_lambdas > MAX_LAMBDAS)
     return *why = "n_lambdas must be in [1, 8]", OSAR_E_INVALID;
   if (c->n_lambdas > 1) {
@@ -351,6 +354,11 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     AL(ctx->g_lo, 4 * bb * ctx->nblk);
   AL(ctx->segpart, cplx * BLK * (int64_t)ctx->nseg);
   AL(ctx->tilepart, cplx * BLK * ctx->nblk);
+  if (ctx->prec == OSAR_SPLIT_BF16 && (cfg->tc_pairs & 2) &&
+      cfg->fuse_power_gram && !cfg->defer_gram) {
+    AL(ctx->gp_col, 8 * BLK * ctx->nblk);
+    AL(ctx->gp_row, 16 * BLK * ctx->nblk);
+  }
   if (cfg->fuse_first_step || L > 1) {
     AL(ctx->segpart2, cplx * BLK * (int64_t)ctx->nseg);
     AL(ctx->tilepart2, cplx * BLK * ctx->nblk);
@@ -607,7 +615,8 @@ int synth_grid(const osar_ctx* ctx, bool main_idle) {
   const double bytes = (double)ctx->nblk * BLK * BLK * 8.0;
   const double pass = bytes / kHbm;
   const int power = ctx->n <= 1 ? ctx->cfg.power_iters_first : ctx->cfg.power_iters;
-  const double passes = power + ctx->iters_est;
+  // the first power step rides on the Gram update when fuse_power_gram holds
+  const double passes = power - (ctx->gp_col && power > 0 ? 1 : 0) + ctx->iters_est;
   const int S = ctx->sm_count;
   double best = flops / (kSmRateAlone * S) + passes * pass;
   int best_g = 0;
@@ -758,7 +767,8 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
   }
   if (e == cudaSuccess) e = launch_data_update(ctx);
   if (e == cudaSuccess)
-    e = ctx->prec == OSAR_SPLIT_BF16 ? launch_gram_tc(ctx) : launch_gram_simt(ctx);
+    e = ctx->prec == OSAR_SPLIT_BF16 ? launch_gram_tc(ctx, nullptr, nullptr, 0, true)
+                                     : launch_gram_simt(ctx);
   if (e == cudaSuccess && ctx->side && !ctx->free_stale)
     e = cudaEventRecord(ctx->ev_free, ctx->stream);
   ctx->n += 1;
@@ -846,6 +856,7 @@ void osar_config_default(osar_config* c) {
   c->lambda_list = nullptr;
   c->defer_gram = 0;
   c->guard_bytes = 0;
+  c->fuse_power_gram = 1;
 }
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {

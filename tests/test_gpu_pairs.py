@@ -16,6 +16,9 @@ pytestmark = pytest.mark.gpu
 def _run(w, problem, pairs, synth_ctas=0, steps=10):
     cfg = gpu_config(w, "split_bf16")
     cfg.tc_pairs = 3 if pairs else 0  # both products on SM pairs, or neither
+    # the power step fused into the pair kernel's Gram update sums in another
+    # order than a separate pass; compare like with like
+    cfg.fuse_power_gram = 0
     cfg.synth_ctas = int(synth_ctas)
     g = osar.Osar(cfg)
     track, _, _, data = problem
