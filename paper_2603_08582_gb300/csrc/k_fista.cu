@@ -113,6 +113,42 @@ __global__ void __launch_bounds__(FIN_THREADS)
   }
 }
 
+// y_K from the partials a Gram update's fused power step wrote: the column
+// partials of the stored blocks (I, K), I <= K, then the two half-row
+// partials of each block (K, J), J > K (contiguous in the packed order),
+// split over FIN_GROUPS thread groups and combined in a fixed order.
+__device__ __forceinline__ double2 gather_gram_row(const float2* __restrict__ pcol,
+                                                   const float2* __restrict__ prow,
+                                                   int nb, int K) {
+  __shared__ float red_r[FIN_GROUPS][BLK], red_i[FIN_GROUPS][BLK];
+  const int g = threadIdx.x / BLK, i = threadIdx.x % BLK;
+  const int ncol = K + 1;
+  const int total = ncol + 2 * (nb - 1 - K);
+  const int64_t r0 = 2 * (packed_block(K, K, nb) + 1);  // block (K, K+1), half 0
+  float yr = 0.f, yi = 0.f;
+#pragma unroll 4
+  for (int q = g; q < total; q += FIN_GROUPS) {
+    const float2 v = q < ncol ? pcol[packed_block(q, K, nb) * BLK + i]
+                              : prow[(r0 + (q - ncol)) * BLK + i];
+    yr += v.x;
+    yi += v.y;
+  }
+  red_r[g][i] = yr;
+  red_i[g][i] = yi;
+  __syncthreads();
+  double2 y = make_double2(0.0, 0.0);
+  if (threadIdx.x < BLK) {
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int k = 0; k < FIN_GROUPS; ++k) {
+      sr += red_r[k][i];
+      si += red_i[k][i];
+    }
+    y = make_double2((double)sr, (double)si);
+  }
+  return y;
+}
+
 // Power step: w = A v; the last CTA forms mu = Re(v^H A v) (v has unit
 // norm) and 1/|w|, and on the last step of a pulse sets
 // L_n = max(L_{n-1}, (1 + margin) mu) and tau = 1/L_n.  FROM_GRAM: A v
