@@ -654,8 +654,9 @@ def run_forms(stream):
 def run_edgelet_forms(stream):
     """The edgelet dictionary (§III-A): the 128 x 128 geometry with the
     square scenes' dictionary (M = 2N = 32768 atoms, as the Gaussian
-    workload), and a scene like the experiments' Scene 1 run until the
-    number of large coefficients (|c| > 0.02) reaches its ideal 4."""
+    workload), and scenes like the experiments' four, each run until the
+    number of large coefficients (|c| > 0.02) reaches its true atom count
+    (4, 8, 5, 5)."""
     from paper_2603_08582_gb300 import osar, synth
     out = {}
     w0 = synth.workloads()["c2_128x128_split_bf16"]
@@ -693,10 +694,25 @@ def run_edgelet_forms(stream):
         "synthesis_ms_per_pulse": {"phases": round(ph, 3), "edgelet_block": round(dg, 3)},
         "gram_ms_per_pulse": round(gr, 3), "device_gb": round(ctx.device_bytes() / 1e9, 1)}
     ctx.close()
-    # Scene 1 of the experiments (a square, 4 atoms): 4 km radius, 1 km up,
-    # 1000 positions over 2 degrees, pulses kept with p = 0.3, m = 20
-    lengths, angles, c_true = synth.paper_scene("square", 32, 32)
-    sw = synth.Workload(name="paper_scene1_32x32", nx=32, ny=32, n_freq=128,
+    # the experiments' four scenes (a square: 4 atoms; two squares: 8; lines
+    # of varying intensity, spaced or adjoined: 5 each): 4 km radius, 1 km
+    # up, 1000 positions over 2 degrees, pulses kept with p = 0.3, m = 20
+    scenes = [("paper_scene1_32x32_split_bf16", "square"),
+              ("paper_scene2_32x32_split_bf16", "two_squares"),
+              ("paper_scene3_32x32_split_bf16", "lines_spaced"),
+              ("paper_scene4_32x32_split_bf16", "lines_adjoined")]
+    for key, kind in scenes:
+        out[key] = paper_scene_form(kind, stream)
+    return out
+
+
+def paper_scene_form(kind, stream):
+    """Run one of the experiments' scenes until its large-coefficient count
+    (|c| > 0.02) equals the number of true atoms, or to the last pulse."""
+    from paper_2603_08582_gb300 import osar, synth
+    lengths, angles, c_true = synth.paper_scene(kind, 32, 32)
+    ideal = int(np.count_nonzero(c_true))
+    sw = synth.Workload(name=f"paper_{kind}_32x32", nx=32, ny=32, n_freq=128,
                         f_lo_hz=9.9e9, f_hi_hz=10.1e9, n_pulses=1000, span_deg=2.0,
                         radius_m=4000.0, height_m=1000.0, dictionary="edgelet",
                         edgelet_lengths=lengths, edgelet_angles=angles,
@@ -717,11 +733,12 @@ def run_edgelet_forms(stream):
         ctx.iterate(20, 0.0, want_count=False)
         cnt = int(np.count_nonzero(np.abs(ctx.coeffs()) > 2e-2))
         counts.append(cnt)
-        if cnt == 4:
+        if cnt == ideal:
             reached = s + 1
             break
     wall = time.perf_counter() - e0
     c_hat = ctx.coeffs()
+    ctx.close()
     big = np.flatnonzero(np.abs(c_hat) > 2e-2)
     sup = np.abs(c_true) > 0
     # the SNR of the experiments (20 log10 of signal over noise amplitude),
@@ -730,16 +747,15 @@ def run_edgelet_forms(stream):
     rms_s = float(np.sqrt(np.mean(np.abs(c_hat[sup]) ** 2)))
     rms_n = float(np.sqrt(np.mean(np.abs(c_hat[~sup]) ** 2)))
     snr_db = 20.0 * np.log10(rms_s / rms_n) if rms_n > 0 else float("inf")
-    out["paper_scene1_32x32_split_bf16"] = {
-        "positions": 1000, "pulses_available": int(len(track)),
+    return {
+        "scene": kind, "true_atoms": ideal, "positions": 1000,
+        "pulses_available": int(len(track)),
         "pulses_to_ideal_count": reached, "final_count": counts[-1],
         "large_are_the_true_atoms": bool(set(big) == set(np.flatnonzero(c_true))),
         "coefficient_snr_db": round(snr_db, 1),
         "count_after_pulses": {str(k): counts[k - 1] for k in (1, 5, 10, 20, 50, 100)
                                if k <= len(counts)},
         "ms_per_pulse_with_readback": round(1e3 * wall / len(counts), 3)}
-    ctx.close()
-    return out
 
 
 # ------------------------------------------------------------ CPU oracle ---
