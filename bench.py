@@ -663,37 +663,50 @@ def run_edgelet_forms(stream):
     w = synth.Workload(**{**w0.as_dict(), "name": "c2_128x128_edgelet",
                           "dictionary": "edgelet", "n_atoms": None,
                           "edgelet_lengths": (4,), "edgelet_angles": (0.0, 90.0)})
-    cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
-                           pixel_m=w.pixel_m, precision="split_bf16",
-                           dictionary="edgelet", edgelet_lengths=[4],
-                           edgelet_angles=[0.0, 90.0], lam=w.lambda_rel,
-                           stream=stream.cuda_stream)
-    ctx = osar.Osar(cfg)
-    W, P = 4, 32
-    track, data, _ = _sim_pulses(ctx, w, W + P)
-    for s in range(W):
-        ctx.push_pulse(track[s], data[s])
-        ctx.iterate(INNER_STEPS, TOL, want_count=False)
-    ctx.synchronize()
-    ctx.profile_reset()
-    ctx.profile_enable(True)
-    steps = []
-
-    def rune():
-        for s in range(W, W + P):
+    # the stored-Gram form (G_n, M x M), then the pixel-space Gram form
+    # (P_n, N x N, G_n applied as H^H P_n H) on the same pulses
+    c_stored = None
+    for pixel in (False, True):
+        cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
+                               pixel_m=w.pixel_m, precision="split_bf16",
+                               dictionary="edgelet", edgelet_lengths=[4],
+                               edgelet_angles=[0.0, 90.0], lam=w.lambda_rel,
+                               stream=stream.cuda_stream, pixel_gram=pixel)
+        ctx = osar.Osar(cfg)
+        W, P = 4, 32
+        track, data, _ = _sim_pulses(ctx, w, W + P)
+        for s in range(W):
             ctx.push_pulse(track[s], data[s])
-            steps.append(ctx.iterate(INNER_STEPS, TOL))
-    ms = _time(rune, stream) / P
-    ph = ctx.profile_read("phase")[1] / P
-    dg = ctx.profile_read("dict_gemm")[1] / P
-    gr = ctx.profile_read("gram_gemm")[1] / P
-    ctx.profile_enable(False)
-    out["c2_128x128_edgelet_split_bf16"] = {
-        "pulses": P, "ms_per_pulse": round(ms, 2),
-        "pulses_per_s": round(1e3 / ms, 1), "mean_iters": round(float(np.mean(steps)), 2),
-        "synthesis_ms_per_pulse": {"phases": round(ph, 3), "edgelet_block": round(dg, 3)},
-        "gram_ms_per_pulse": round(gr, 3), "device_gb": round(ctx.device_bytes() / 1e9, 1)}
-    ctx.close()
+            ctx.iterate(INNER_STEPS, TOL, want_count=False)
+        ctx.synchronize()
+        ctx.profile_reset()
+        ctx.profile_enable(True)
+        steps = []
+
+        def rune():
+            for s in range(W, W + P):
+                ctx.push_pulse(track[s], data[s])
+                steps.append(ctx.iterate(INNER_STEPS, TOL))
+        ms = _time(rune, stream) / P
+        ph = ctx.profile_read("phase")[1] / P
+        dg = ctx.profile_read("dict_gemm")[1] / P
+        gr = ctx.profile_read("gram_gemm")[1] / P
+        ctx.profile_enable(False)
+        res = {
+            "pulses": P, "ms_per_pulse": round(ms, 2),
+            "pulses_per_s": round(1e3 / ms, 1), "mean_iters": round(float(np.mean(steps)), 2),
+            "synthesis_ms_per_pulse": {"phases": round(ph, 3), "edgelet_block": round(dg, 3)},
+            "gram_ms_per_pulse": round(gr, 3), "device_gb": round(ctx.device_bytes() / 1e9, 1)}
+        c_hat = ctx.coeffs()
+        if not pixel:
+            c_stored = c_hat
+            out["c2_128x128_edgelet_split_bf16"] = res
+        else:
+            res["gram_order"] = {"stored_form": w.m_atoms, "pixel_form": w.n_pixels}
+            res["coeffs_rel_diff_vs_stored_gram_form"] = float(
+                np.linalg.norm(c_hat - c_stored) / max(np.linalg.norm(c_stored), 1e-300))
+            out["c2_128x128_edgelet_pixel_gram_split_bf16"] = res
+        ctx.close()
     # the experiments' four scenes (a square: 4 atoms; two squares: 8; lines
     # of varying intensity, spaced or adjoined: 5 each): 4 km radius, 1 km
     # up, 1000 positions over 2 degrees, pulses kept with p = 0.3, m = 20

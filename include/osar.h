@@ -187,6 +187,20 @@ typedef struct {
      every power step is a separate pass.  Ignored on the other paths.
      Default 1. */
   int32_t fuse_power_gram;
+  /* OSAR_DICT_EDGELET only, one lambda, defer_gram = 0.  1: the pixel-space
+     Gram form.  Since A_s = F_s H, G_n = H^H P_n H and b_n = H^H b_pix with
+     P_n = sum_s F_s^H F_s (N x N) and b_pix = sum_s F_s^H d_s; the context
+     accumulates P_n and b_pix with its pixel-basis kernels and applies G_n
+     to a coefficient vector x as H^H (P_n (H x)) (sums over H's pixel and
+     atom lists around one pass over the packed P_n), in Algorithm 1 and in
+     the power iteration.  P_n has N^2 entries where G_n has M^2, and no
+     forward block A_s is formed.  Coefficients, b (osar_get_b returns
+     H^H b_pix), lambda_n, L_n and t are those of the stored-Gram form to
+     rounding.  In this form osar_get_gram, osar_get_gram_entries and
+     osar_gram_apply work on P_n (N x N, pixel vectors); osar_save,
+     osar_load, osar_unroll_grad and osar_get_lambda_state return
+     OSAR_E_STATE.  Default 0. */
+  int32_t pixel_gram;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
@@ -194,7 +208,8 @@ typedef struct {
    30 / 4 power steps, margin 0.01, carried momentum, compensated = 1,
    overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
    (both tensor-core products on SM pairs), fuse_first_step = 1,
-   n_lambdas = 1, defer_gram = 0, guard_bytes = 0, fuse_power_gram = 1. */
+   n_lambdas = 1, defer_gram = 0, guard_bytes = 0, fuse_power_gram = 1,
+   pixel_gram = 0. */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128

@@ -68,10 +68,31 @@ struct ProfEvent {
   cudaEvent_t a, b;
 };
 
+// Pixel-space Gram form (config pixel_gram, binary edgelet dictionary H):
+// the context runs as a pixel-basis one (its Gram is P_n = sum_s F_s^H F_s,
+// N x N, its data vector b_pix = sum_s F_s^H d_s) and this holds the
+// coefficient side: G_n = H^H P_n H and b_n = H^H b_pix are applied, never
+// stored.
+struct PixGram {
+  int M = 0;                  // atoms
+  int Mp = 0;                 // atoms padded to BLK
+  int nb = 0;                 // Mp / BLK
+  int* pix_ptr = nullptr;     // first entry of pixel p in pix_atom (N + 1)
+  int* pix_atom = nullptr;    // atoms covering each pixel, ascending
+  double2* c = nullptr;       // c_hat (Mp)
+  double2* z = nullptr;       // z of Algorithm 1 (Mp)
+  double2* b = nullptr;       // H^H b_pix (Mp)
+  double2* v = nullptr;       // power vector (Mp)
+  double2* w = nullptr;       // G v (Mp)
+  double2* part = nullptr;    // per-block partial sums (nb)
+  double* bmax = nullptr;     // per-block max |b_m|^2 (blocks of the b grid)
+};
+
 }  // namespace osar
 
 struct osar_ctx {
   osar_config cfg;
+  osar::PixGram* pg = nullptr;  // pixel-space Gram form, or NULL
   int prec = OSAR_FP64;
   bool dict = false;  // overcomplete / explicit dictionary present
   bool edgelet = false;  // binary edgelet dictionary (atom pixel lists)
@@ -233,6 +254,12 @@ cudaError_t launch_edgelet(osar_ctx* ctx, int grid_cap);
 // the image H c of the simulation's sparse coefficients (sim_idx / sim_nz)
 cudaError_t launch_sim_rho_edgelet(osar_ctx* ctx, int nnz);
 
+// ---- k_pixgram.cu ------------------------------------------------------------
+// b_n = H^H b_pix, lambda_n and the pulse's power steps on G_n = H^H P_n H
+cudaError_t pg_after_push(osar_ctx* ctx);
+cudaError_t pg_burst_begin(osar_ctx* ctx);
+cudaError_t pg_fista_step(osar_ctx* ctx);
+
 // ---- k_defer.cu -------------------------------------------------------------
 // corr[set] = A_n^H (A_n x) for the pending forward block (nothing when no
 // Gram update is pending); gate: skip when that flag is set
@@ -282,6 +309,11 @@ cudaError_t launch_gram_entries(osar_ctx* ctx, const int2* rc, int count,
                                 double2* out);
 size_t gram_apply_scratch_bytes(const osar_ctx* ctx);
 cudaError_t launch_matvec(osar_ctx* ctx, const void* xt);
+// One Gram pass y = G x over the working-precision vector xt (Mp), into the
+// FP64 vector y; gated: the pass and its finalize skip once solution 0 has
+// met the stop rule.  kind: the profile class of the finalize.
+cudaError_t launch_gram_pass(osar_ctx* ctx, const void* xt, int gated,
+                             double2* y, int kind);
 
 // ---- k_adjoint.cu ----------------------------------------------------------
 cudaError_t run_unroll_grad(osar_ctx* ctx, int T, int C, double lambda,

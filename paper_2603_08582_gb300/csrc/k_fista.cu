@@ -32,6 +32,7 @@
 #include "ctx.h"
 
 #include "matvec.cuh"
+#include "step.cuh"
 
 namespace osar {
 namespace {
@@ -41,21 +42,7 @@ namespace {
 //   t' = (1 + sqrt(1 + 4 t^2)) / 2,  z' = c + (t - 1)/t' (c - c_prev).
 // The last CTA then sets t <- t', counts the step and applies the stop rule
 // |c - z|_2 <= tol |c|_2 to the whole vector.
-// Shrink factor max(0, 1 - alpha/|u|): FP64 on the FP64 path; on the
-// FP32-Gram paths (whose matvec is FP32 anyway) an FP32 reciprocal square
-// root, since GB300's FP64 pipes are ~1/64 of its FP32 rate.
-template <typename T2>
-__device__ __forceinline__ double shrink_keep(double mag2, double alpha);
-template <>
-__device__ __forceinline__ double shrink_keep<double2>(double mag2, double alpha) {
-  const double mag = sqrt(mag2);
-  return mag > alpha ? 1.0 - alpha / mag : 0.0;
-}
-template <>
-__device__ __forceinline__ double shrink_keep<float2>(double mag2, double alpha) {
-  if (!(mag2 > alpha * alpha)) return 0.0;
-  return (double)(1.0f - (float)alpha * rsqrtf((float)mag2));
-}
+// The complex shrinkage factor is shrink_keep (step.cuh).
 
 template <typename T2, typename Acc>
 __global__ void __launch_bounds__(FIN_THREADS)
@@ -217,6 +204,20 @@ __global__ void __launch_bounds__(FIN_THREADS)
                      const T2* __restrict__ tilepart,
                      const int* __restrict__ seg_begin, int nb,
                      double2* __restrict__ y) {
+  const int K = blockIdx.x, i = threadIdx.x;
+  const double2 v = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
+  if (i < BLK) y[K * BLK + i] = v;
+}
+
+// y = A x of a pass whose result is needed as a vector (the pixel-space Gram
+// form); gated: nothing once solution 0 has met the stop rule.
+template <typename T2, typename Acc>
+__global__ void __launch_bounds__(FIN_THREADS)
+    k_pass_finalize(const T2* __restrict__ segpart,
+                    const T2* __restrict__ tilepart,
+                    const int* __restrict__ seg_begin, int nb,
+                    double2* __restrict__ y, const DevScalars* sc, int gated) {
+  if (gated && sc->converged) return;
   const int K = blockIdx.x, i = threadIdx.x;
   const double2 v = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K);
   if (i < BLK) y[K * BLK + i] = v;
@@ -691,6 +692,8 @@ cudaError_t prepare_burst_kernels() {
   set((const void*)k_power_finalize<float2, float>);
   set((const void*)k_power_finalize<float2, float, true>);
   set((const void*)k_power_finalize<double2, double>);
+  set((const void*)k_pass_finalize<float2, float>);
+  set((const void*)k_pass_finalize<double2, double>);
   set((const void*)k_power_normalize<float2>);
   set((const void*)k_power_normalize<double2>);
   set((const void*)k_burst_begin<float2>);
@@ -871,6 +874,24 @@ cudaError_t launch_gram_apply_scratch(osar_ctx* ctx, const double2* x,
 
 cudaError_t launch_matvec(osar_ctx* ctx, const void* xt) {
   matvec(ctx, xt, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_pass(osar_ctx* ctx, const void* xt, int gated,
+                             double2* y, int kind) {
+  matvec(ctx, xt, gated);
+  ProfEvent ev;
+  prof_begin(ctx, kind, &ev);
+  if (ctx->prec == OSAR_FP64)
+    k_pass_finalize<double2, double><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
+        (const double2*)ctx->segpart, (const double2*)ctx->tilepart,
+        ctx->seg_begin, ctx->nb, y, ctx->scal, gated);
+  else
+    k_pass_finalize<float2, float><<<(unsigned)ctx->nb, FIN_THREADS, 0, ctx->stream>>>(
+        (const float2*)ctx->segpart, (const float2*)ctx->tilepart,
+        ctx->seg_begin, ctx->nb, y, ctx->scal, gated);
+  prof_end(ctx, &ev);
+  ctx->launches++;
   return cudaGetLastError();
 }
 

@@ -461,7 +461,8 @@ cudaError_t launch_dictionary_build(osar_ctx* ctx, const double* host_dict) {
 
 cudaError_t launch_simulate(osar_ctx* ctx, int nnz, double2* d_out) {
   const int Np = ctx->Np;
-  if (ctx->edgelet) {
+  if (ctx->edgelet || ctx->pg) {
+    // the image H c (the pixel-space Gram form keeps H's lists too)
     cudaError_t e = launch_sim_rho_edgelet(ctx, nnz);
     if (e != cudaSuccess) return e;
   } else if (!ctx->dict) {

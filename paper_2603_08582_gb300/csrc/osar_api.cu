@@ -72,6 +72,15 @@ void free_all(osar_ctx* ctx) {
                   ctx->gp_row};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (ctx->pg) {
+    const PixGram& g = *ctx->pg;
+    for (void* p : {(void*)g.pix_ptr, (void*)g.pix_atom, (void*)g.c, (void*)g.z,
+                    (void*)g.b, (void*)g.v, (void*)g.w, (void*)g.part,
+                    (void*)g.bmax})
+      if (p) cudaFree(p);
+    delete ctx->pg;
+    ctx->pg = nullptr;
+  }
   if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
   if (ctx->h_wring) cudaFreeHost(ctx->h_wring);
   for (cudaEvent_t ev : ctx->w_ev)
@@ -161,6 +170,12 @@ osar_status validate(const osar_config* c, std::string* why) {
     return *why = "fuse_first_step must be 0 or 1", OSAR_E_INVALID;
   if (c->fuse_power_gram != 0 && c->fuse_power_gram != 1)
     return *why = "fuse_power_gram must be 0 or 1", OSAR_E_INVALID;
+  if (c->pixel_gram != 0 && c->pixel_gram != 1)
+    return *why = "pixel_gram must be 0 or 1", OSAR_E_INVALID;
+  if (c->pixel_gram &&
+      (c->dict_kind != OSAR_DICT_EDGELET || c->n_lambdas != 1 || c->defer_gram))
+    return *why = "pixel_gram needs the edgelet dictionary, one lambda and "
+                  "defer_gram = 0", OSAR_E_INVALID;
   if (c->n_lambdas < 1 || c->n_lambdas > MAX_LAMBDAS)
     return *why = "n_lambdas must be in [1, 8]", OSAR_E_INVALID;
   if (c->n_lambdas > 1) {
@@ -282,13 +297,22 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     ctx->lam.v[l] = l < ctx->n_lam && ctx->n_lam > 1 ? cfg->lambda_list[l]
                                                      : cfg->lambda;
   ctx->prec = cfg->precision;
-  ctx->dict = cfg->dict_kind != OSAR_DICT_IDENTITY;
-  ctx->edgelet = cfg->dict_kind == OSAR_DICT_EDGELET;
+  // the pixel-space Gram form runs the context as a pixel-basis one and
+  // keeps the edgelet coefficients beside it (PixGram)
+  const bool pixgram = cfg->pixel_gram != 0;
+  ctx->dict = cfg->dict_kind != OSAR_DICT_IDENTITY && !pixgram;
+  ctx->edgelet = cfg->dict_kind == OSAR_DICT_EDGELET && !pixgram;
   ctx->N = cfg->nx * cfg->ny;
   ctx->M = ctx->edgelet ? cfg->n_edgelet_lengths * cfg->n_edgelet_angles * ctx->N
            : ctx->dict  ? cfg->n_atoms
                         : ctx->N;
-  ctx->cfg.n_atoms = ctx->dict ? ctx->M : cfg->n_atoms;
+  if (pixgram) {
+    ctx->pg = new PixGram();
+    ctx->pg->M = cfg->n_edgelet_lengths * cfg->n_edgelet_angles * ctx->N;
+    ctx->pg->Mp = (int)roundup(ctx->pg->M, BLK);
+    ctx->pg->nb = ctx->pg->Mp / BLK;
+  }
+  ctx->cfg.n_atoms = ctx->dict ? ctx->M : pixgram ? ctx->pg->M : cfg->n_atoms;
   ctx->cfg.edgelet_lengths = nullptr;     // the atom lists are built below
   ctx->cfg.edgelet_angles_deg = nullptr;
   ctx->K = cfg->n_freq;
@@ -355,7 +379,7 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   AL(ctx->segpart, cplx * BLK * (int64_t)ctx->nseg);
   AL(ctx->tilepart, cplx * BLK * ctx->nblk);
   if (ctx->prec == OSAR_SPLIT_BF16 && (cfg->tc_pairs & 2) &&
-      cfg->fuse_power_gram && !cfg->defer_gram) {
+      cfg->fuse_power_gram && !cfg->defer_gram && !ctx->pg) {
     AL(ctx->gp_col, 8 * BLK * ctx->nblk);
     AL(ctx->gp_row, 16 * BLK * ctx->nblk);
   }
@@ -413,10 +437,37 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     AL(ctx->corr_u, 8 * ((int64_t)ctx->nb + 1) * Kp);
     AL(ctx->corr_tick, sizeof(unsigned));
   }
+  std::vector<int> pix_ptr, pix_atom;
+  if (ctx->pg) {
+    // H both ways: the atoms' pixel lists and, per pixel, its atoms
+    PixGram& g = *ctx->pg;
+    build_edgelets(*cfg, atom_ptr, atom_pix);
+    pix_ptr.assign((size_t)ctx->N + 1, 0);
+    for (int p : atom_pix) pix_ptr[p + 1]++;
+    for (int p = 0; p < ctx->N; ++p) pix_ptr[p + 1] += pix_ptr[p];
+    pix_atom.resize(atom_pix.size());
+    std::vector<int> fill(pix_ptr.begin(), pix_ptr.end() - 1);
+    for (int m = 0; m < g.M; ++m)
+      for (int t = atom_ptr[m]; t < atom_ptr[m + 1]; ++t)
+        pix_atom[fill[atom_pix[t]]++] = m;
+    const size_t lists = atom_pix.empty() ? 1 : atom_pix.size();
+    AL(ctx->atom_ptr, sizeof(int) * atom_ptr.size());
+    AL(ctx->atom_pix, sizeof(int) * lists);
+    AL(g.pix_ptr, sizeof(int) * pix_ptr.size());
+    AL(g.pix_atom, sizeof(int) * lists);
+    AL(g.c, 16 * (int64_t)g.Mp);
+    AL(g.z, 16 * (int64_t)g.Mp);
+    AL(g.b, 16 * (int64_t)g.Mp);
+    AL(g.v, 16 * (int64_t)g.Mp);
+    AL(g.w, 16 * (int64_t)g.Mp);
+    AL(g.part, 16 * (int64_t)g.nb);
+    AL(g.bmax, 8 * (int64_t)((g.M + 255) / 256));
+  }
+  const int64_t coef_p = ctx->pg ? std::max<int64_t>(Mp, ctx->pg->Mp) : Mp;
   AL(ctx->wk_dev, 8 * 2 * Kp);
   AL(ctx->sim_rho, 16 * Np);
-  AL(ctx->sim_nz, 16 * Mp);
-  AL(ctx->sim_idx, 4 * Mp);
+  AL(ctx->sim_nz, 16 * coef_p);
+  AL(ctx->sim_idx, 4 * coef_p);
   AL(ctx->sim_d, 16 * Kp);
 #undef AL
   e = cudaMallocHost((void**)&ctx->h_ring, sizeof(double2) * RING * Kp);
@@ -494,6 +545,30 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
                           sizeof(int) * atom_pix.size(), cudaMemcpyHostToDevice,
                           ctx->stream);
     // the host lists leave scope below: the copies complete first
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "edgelet atoms"));
+  } else if (ctx->pg) {
+    // both lists, and the coefficient power vector v = 1/sqrt(M) on the
+    // M atoms (the stored-Gram form's start)
+    const PixGram& g = *ctx->pg;
+    std::vector<double2> vc((size_t)g.Mp, make_double2(0.0, 0.0));
+    for (int i = 0; i < g.M; ++i) vc[i].x = 1.0 / std::sqrt((double)g.M);
+    e = cudaMemcpyAsync(ctx->atom_ptr, atom_ptr.data(), sizeof(int) * atom_ptr.size(),
+                        cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g.pix_ptr, pix_ptr.data(), sizeof(int) * pix_ptr.size(),
+                          cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && !atom_pix.empty())
+      e = cudaMemcpyAsync(ctx->atom_pix, atom_pix.data(),
+                          sizeof(int) * atom_pix.size(), cudaMemcpyHostToDevice,
+                          ctx->stream);
+    if (e == cudaSuccess && !pix_atom.empty())
+      e = cudaMemcpyAsync(g.pix_atom, pix_atom.data(),
+                          sizeof(int) * pix_atom.size(), cudaMemcpyHostToDevice,
+                          ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g.v, vc.data(), 16 * (size_t)g.Mp, cudaMemcpyHostToDevice,
+                          ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "edgelet atoms"));
   } else if (ctx->dict) {
@@ -699,10 +774,11 @@ osar_status push_deferred(osar_ctx* ctx, const double gamma[3]) {
   ctx->fresh = true;
   ctx->first_ready = false;
   if (e == cudaSuccess)
-    e = launch_power_steps(ctx,
-                           ctx->n == 1 ? ctx->cfg.power_iters_first
-                                       : ctx->cfg.power_iters,
-                           ctx->cfg.fuse_first_step != 0);
+    e = ctx->pg ? pg_after_push(ctx)
+                : launch_power_steps(ctx,
+                                     ctx->n == 1 ? ctx->cfg.power_iters_first
+                                                 : ctx->cfg.power_iters,
+                                     ctx->cfg.fuse_first_step != 0);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_push_pulse");
   return OSAR_OK;
 }
@@ -775,10 +851,11 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
   ctx->fresh = true;
   ctx->first_ready = false;
   if (e == cudaSuccess)
-    e = launch_power_steps(ctx,
-                           ctx->n == 1 ? ctx->cfg.power_iters_first
-                                       : ctx->cfg.power_iters,
-                           ctx->cfg.fuse_first_step != 0);
+    e = ctx->pg ? pg_after_push(ctx)
+                : launch_power_steps(ctx,
+                                     ctx->n == 1 ? ctx->cfg.power_iters_first
+                                                 : ctx->cfg.power_iters,
+                                     ctx->cfg.fuse_first_step != 0);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_push_pulse");
   return OSAR_OK;
 }
@@ -857,7 +934,19 @@ void osar_config_default(osar_config* c) {
   c->defer_gram = 0;
   c->guard_bytes = 0;
   c->fuse_power_gram = 1;
+  c->pixel_gram = 0;
 }
+
+namespace {
+// The coefficient vector c_hat and its length (the atoms' side in the
+// pixel-space Gram form).
+const double2* coef_c(const osar_ctx* ctx) { return ctx->pg ? ctx->pg->c : ctx->c; }
+int coef_m(const osar_ctx* ctx) { return ctx->pg ? ctx->pg->M : ctx->M; }
+osar_status no_pixgram(osar_ctx* ctx, const char* what) {
+  return fail(ctx, OSAR_E_STATE,
+              std::string(what) + ": not available in the pixel-space Gram form");
+}
+}  // namespace
 
 osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
   osar::TraceRange trace_("osar_create");
@@ -964,12 +1053,12 @@ osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
     return fail(ctx, OSAR_E_STATE, "osar_iterate before the first pulse");
   cudaError_t e = cudaSuccess;
   if (ctx->fresh) {
-    e = launch_burst_begin(ctx);
+    e = ctx->pg ? pg_burst_begin(ctx) : launch_burst_begin(ctx);
     ctx->fresh = false;
   }
   if (e == cudaSuccess) e = launch_iter_begin(ctx, tol);
   for (int k = 0; e == cudaSuccess && k < max_iters; ++k)
-    e = launch_fista_step(ctx);
+    e = ctx->pg ? pg_fista_step(ctx) : launch_fista_step(ctx);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_iterate");
   if (iters_done) {
     DevScalars s;
@@ -995,7 +1084,7 @@ osar_status osar_get_coeffs(osar_ctx* ctx, double* out_c128) {
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!out_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_coeffs: NULL");
-  CK(ctx, cudaMemcpyAsync(out_c128, ctx->c, sizeof(double2) * ctx->M,
+  CK(ctx, cudaMemcpyAsync(out_c128, coef_c(ctx), sizeof(double2) * coef_m(ctx),
                           cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   return OSAR_OK;
@@ -1005,7 +1094,7 @@ osar_status osar_get_coeffs_dev(osar_ctx* ctx, void* out_dev_c128) {
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!out_dev_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_coeffs_dev: NULL");
-  CK(ctx, cudaMemcpyAsync(out_dev_c128, ctx->c, sizeof(double2) * ctx->M,
+  CK(ctx, cudaMemcpyAsync(out_dev_c128, coef_c(ctx), sizeof(double2) * coef_m(ctx),
                           cudaMemcpyDeviceToDevice, ctx->stream));
   return OSAR_OK;
 }
@@ -1017,7 +1106,7 @@ osar_status osar_get_coeffs_async(osar_ctx* ctx, double* out_c128,
   if (st != OSAR_OK) return st;
   if (!out_c128 || slot < 0 || slot >= OSAR_COPY_SLOTS)
     return fail(ctx, OSAR_E_INVALID, "osar_get_coeffs_async: bad buffer or slot");
-  CK(ctx, cudaMemcpyAsync(out_c128, ctx->c, sizeof(double2) * ctx->M,
+  CK(ctx, cudaMemcpyAsync(out_c128, coef_c(ctx), sizeof(double2) * coef_m(ctx),
                           cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaEventRecord(ctx->copy_ev[slot], ctx->stream));
   return OSAR_OK;
@@ -1050,6 +1139,7 @@ osar_status osar_get_lambda_state(osar_ctx* ctx, int32_t l, double* out_c128,
                                   double* lambda, double* t, int32_t* iters) {
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
+  if (ctx->pg) return no_pixgram(ctx, "osar_get_lambda_state");
   if (l < 0 || l >= ctx->n_lam)
     return fail(ctx, OSAR_E_INVALID, "osar_get_lambda_state: no such solution");
   DevScalars s;
@@ -1069,7 +1159,7 @@ osar_status osar_get_lambda_state(osar_ctx* ctx, int32_t l, double* out_c128,
 osar_status osar_get_dims(const osar_ctx* ctx, int32_t* m_atoms,
                           int32_t* n_pixels, int32_t* n_freq) {
   if (!ctx) return OSAR_E_INVALID;
-  if (m_atoms) *m_atoms = ctx->M;
+  if (m_atoms) *m_atoms = coef_m(ctx);
   if (n_pixels) *n_pixels = ctx->N;
   if (n_freq) *n_freq = ctx->K;
   return OSAR_OK;
@@ -1141,7 +1231,8 @@ osar_status osar_get_b(osar_ctx* ctx, double* out_c128) {
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!out_c128) return fail(ctx, OSAR_E_INVALID, "osar_get_b: NULL");
-  CK(ctx, cudaMemcpyAsync(out_c128, ctx->b, sizeof(double2) * ctx->M,
+  CK(ctx, cudaMemcpyAsync(out_c128, ctx->pg ? ctx->pg->b : ctx->b,
+                          sizeof(double2) * coef_m(ctx),
                           cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   return OSAR_OK;
@@ -1173,7 +1264,7 @@ osar_status osar_simulate_pulse(osar_ctx* ctx, const double gamma_xyz[3],
     return fail(ctx, OSAR_E_INVALID, "osar_simulate_pulse: NULL argument");
   std::vector<int> idx;
   std::vector<double2> val;
-  for (int j = 0; j < ctx->M; ++j) {
+  for (int j = 0; j < coef_m(ctx); ++j) {
     double re = coeffs_c128[2 * j], im = coeffs_c128[2 * j + 1];
     if (re != 0.0 || im != 0.0) {
       idx.push_back(j);
@@ -1203,6 +1294,7 @@ osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
   osar::TraceRange trace_("osar_unroll_grad");
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
+  if (ctx->pg) return no_pixgram(ctx, "osar_unroll_grad");
   if (ctx->n == 0)
     return fail(ctx, OSAR_E_STATE, "osar_unroll_grad before the first pulse");
   CK(ctx, settle_gram(ctx));
@@ -1359,6 +1451,7 @@ osar_status osar_save(osar_ctx* ctx, const char* path) {
   osar_status st = check_usable(ctx);
   if (st != OSAR_OK) return st;
   if (!path) return fail(ctx, OSAR_E_INVALID, "osar_save: NULL path");
+  if (ctx->pg) return no_pixgram(ctx, "osar_save");
   CK(ctx, settle_gram(ctx));
   FILE* f = fopen(path, "wb");
   if (!f) return fail(ctx, OSAR_E_IO, std::string("cannot open ") + path);
@@ -1401,6 +1494,9 @@ osar_status osar_load(const char* path, const osar_config* cfg, osar_ctx** out) 
   if (!out) return fail(nullptr, OSAR_E_INVALID, "out is NULL");
   *out = nullptr;
   if (!path || !cfg) return fail(nullptr, OSAR_E_INVALID, "osar_load: NULL argument");
+  if (cfg->pixel_gram)
+    return fail(nullptr, OSAR_E_STATE,
+                "osar_load: not available in the pixel-space Gram form");
   FILE* f = fopen(path, "rb");
   if (!f) return fail(nullptr, OSAR_E_IO, std::string("cannot open ") + path);
   CkptHeader h;

@@ -71,7 +71,7 @@ class OsarConfig(C.Structure):
         ("defer_gram", C.c_int32), ("guard_bytes", C.c_int32),
         ("n_edgelet_lengths", C.c_int32), ("edgelet_lengths", C.c_void_p),
         ("n_edgelet_angles", C.c_int32), ("edgelet_angles_deg", C.c_void_p),
-        ("fuse_power_gram", C.c_int32),
+        ("fuse_power_gram", C.c_int32), ("pixel_gram", C.c_int32),
     ]
 
 
@@ -176,7 +176,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
                 compensated=True, stream=None, overlap_synthesis=True,
                 synth_ctas=0, tc_pairs=3, fuse_first_step=True, lambdas=None,
                 defer_gram=False, guard_bytes=0, edgelet_lengths=None,
-                edgelet_angles=None, fuse_power_gram=True):
+                edgelet_angles=None, fuse_power_gram=True, pixel_gram=False):
     """Build an osar_config.  dictionary: None (identity), "gaussian"
     (seeded Philox atoms, needs n_atoms), "edgelet" (binary edgelets of
     edgelet_lengths x edgelet_angles degrees at every pixel) or an N x M
@@ -221,6 +221,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
     cfg.defer_gram = 1 if defer_gram else 0
     cfg.guard_bytes = int(guard_bytes)
     cfg.fuse_power_gram = 1 if fuse_power_gram else 0
+    cfg.pixel_gram = 1 if pixel_gram else 0
     if lambdas is not None and len(lambdas) > 1:
         # lambda path: one solution per value (relative or absolute like lam)
         lv = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
@@ -252,6 +253,9 @@ class Osar:
         m, n, k = C.c_int32(), C.c_int32(), C.c_int32()
         self._lib.osar_get_dims(self._h, C.byref(m), C.byref(n), C.byref(k))
         self.m_atoms, self.n_pixels, self.n_freq = m.value, n.value, k.value
+        # the stored Gram's order: M, or N in the pixel-space Gram form
+        pixel = self.cfg is not None and getattr(self.cfg, "pixel_gram", 0)
+        self.gram_dim = self.n_pixels if pixel else self.m_atoms
 
     # -- helpers --------------------------------------------------------
     def _check(self, st: int):
@@ -345,7 +349,7 @@ class Osar:
         return {"coeffs": out, "lambda": lam.value, "t": t.value, "iters": it.value}
 
     def gram(self) -> np.ndarray:
-        out = np.empty((self.m_atoms, self.m_atoms), dtype=np.complex128)
+        out = np.empty((self.gram_dim, self.gram_dim), dtype=np.complex128)
         self._check(self._lib.osar_get_gram(self._h, _dptr(out.view(np.float64))))
         return out
 
@@ -366,7 +370,7 @@ class Osar:
 
     def gram_apply(self, x) -> np.ndarray:
         xv = _c128(x)
-        out = np.empty(self.m_atoms, dtype=np.complex128)
+        out = np.empty(self.gram_dim, dtype=np.complex128)
         self._check(self._lib.osar_gram_apply(self._h, _dptr(xv.view(np.float64)),
                                               _dptr(out.view(np.float64))))
         return out

@@ -50,7 +50,7 @@ def test_config_defaults_and_layout(lib):
     assert cfg.tc_pairs == 3 and cfg.fuse_first_step == 1
     assert cfg.n_lambdas == 1 and cfg.lambda_list is None
     assert cfg.defer_gram == 0 and cfg.guard_bytes == 0
-    assert cfg.fuse_power_gram == 1
+    assert cfg.fuse_power_gram == 1 and cfg.pixel_gram == 0
 
 
 @pytest.mark.parametrize("changes", [
@@ -77,7 +77,9 @@ def test_create_rejects_unsupported_deferred_update(lib, changes):
     ("precision", 7), ("dict_kind", 9), ("power_iters_first", 0),
     ("lam", float("nan")), ("lipschitz_margin", -0.5),
     ("overlap_synthesis", 2), ("synth_ctas", -1), ("tc_pairs", 4),
-    ("fuse_first_step", 2), ("fuse_power_gram", 2), ("n_lambdas", 0),
+    ("fuse_first_step", 2), ("fuse_power_gram", 2), ("pixel_gram", 2),
+    ("pixel_gram", 1),  # the pixel-space Gram form needs edgelets
+    ("n_lambdas", 0),
     ("n_lambdas", 9),
     ("n_lambdas", 2),  # > 1 without a lambda_list
     ("guard_bytes", -256), ("guard_bytes", 100), ("guard_bytes", 2 << 20),

@@ -461,6 +461,38 @@ def test_paper_scenes_have_the_ideal_atom_counts():
     assert np.allclose(np.hypot(t[:, 0], t[:, 1]), 4000.0) and np.allclose(t[:, 2], 1000.0)
 
 
+def test_pixel_space_gram_factors_the_dictionary_gram():
+    # Eqs. 6 and 12-13 with A_s = F_s H: the pixel-basis statistics P_n =
+    # sum F_s^H F_s and b_pix = sum F_s^H d_s give the dictionary's Gram and
+    # data vector as H^H P_n H and H^H b_pix (the pixel-space Gram form)
+    nx, ny = 6, 5
+    h = orc.edgelet_dictionary(nx, ny, (2, 3), (0.0, 90.0, 45.0))
+    x = orc.pixel_positions(nx, ny, 1.0)
+    f = orc.frequencies(7, 9.9e9, 10.1e9)
+    rng = np.random.default_rng(9)
+    p_n = np.zeros((nx * ny, nx * ny), dtype=np.complex128)
+    b_pix = np.zeros(nx * ny, dtype=np.complex128)
+    g_n = np.zeros((h.shape[1], h.shape[1]), dtype=np.complex128)
+    b_n = np.zeros(h.shape[1], dtype=np.complex128)
+    for k in range(3):
+        gamma = np.array([900.0 * np.cos(0.1 * k), 900.0 * np.sin(0.1 * k), 400.0])
+        fs = orc.phase_matrix(gamma, x, f)
+        d = rng.standard_normal(7) + 1j * rng.standard_normal(7)
+        p_n += orc.gram_increment(orc.forward_block(fs, None))
+        b_pix += orc.data_increment(orc.forward_block(fs, None), d)
+        a_s = orc.forward_block(fs, h)
+        g_n += orc.gram_increment(a_s)
+        b_n += orc.data_increment(a_s, d)
+    assert np.allclose(h.conj().T @ p_n @ h, g_n, rtol=0, atol=1e-10 * np.abs(g_n).max())
+    assert np.allclose(h.conj().T @ b_pix, b_n, rtol=0, atol=1e-12 * np.abs(b_n).max())
+    # applied as three steps on a vector: u = H x, w = P u, H^H w
+    c = rng.standard_normal(h.shape[1]) + 1j * rng.standard_normal(h.shape[1])
+    u = np.array([c[h[p] != 0].sum() for p in range(nx * ny)])
+    w = p_n @ u
+    y = np.array([w[h[:, m] != 0].sum() for m in range(h.shape[1])])
+    assert np.allclose(y, g_n @ c, rtol=0, atol=1e-10 * np.abs(g_n @ c).max())
+
+
 def test_non_white_increments_are_the_weighted_sums():
     # Eq. 12 with R_n = diag(var): entrywise sums with weights 1 / var_k, and
     # a constant variance scales the white increments
