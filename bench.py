@@ -691,12 +691,21 @@ def run_edgelet_forms(stream):
         ph = ctx.profile_read("phase")[1] / P
         dg = ctx.profile_read("dict_gemm")[1] / P
         gr = ctx.profile_read("gram_gemm")[1] / P
+        mv_n, mv_ms = ctx.profile_read("matvec")
         ctx.profile_enable(False)
+        # the packed Gram one matvec pass reads (G_n, or P_n in the pixel form)
+        nbg = ((w.n_pixels if pixel else w.m_atoms) + 127) // 128
+        pass_bytes = nbg * (nbg + 1) // 2 * 128 * 128 * 8
+        mv_avg = mv_ms / max(mv_n, 1)
+        hbm = measured_peaks()[0]["hbm_gbs"]
         res = {
             "pulses": P, "ms_per_pulse": round(ms, 2),
             "pulses_per_s": round(1e3 / ms, 1), "mean_iters": round(float(np.mean(steps)), 2),
             "synthesis_ms_per_pulse": {"phases": round(ph, 3), "edgelet_block": round(dg, 3)},
-            "gram_ms_per_pulse": round(gr, 3), "device_gb": round(ctx.device_bytes() / 1e9, 1)}
+            "gram_ms_per_pulse": round(gr, 3), "device_gb": round(ctx.device_bytes() / 1e9, 1),
+            "matvec": {"bytes_per_pass": pass_bytes, "avg_launch_ms": round(mv_avg, 4),
+                       "achieved_gbs": round(pass_bytes / mv_avg / 1e6, 1),
+                       "frac_of_measured_hbm": round(pass_bytes / mv_avg / 1e6 / hbm, 3)}}
         c_hat = ctx.coeffs()
         if not pixel:
             c_stored = c_hat
