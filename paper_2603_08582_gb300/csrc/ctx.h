@@ -257,6 +257,7 @@ cudaError_t launch_sim_rho_edgelet(osar_ctx* ctx, int nnz);
 // ---- k_pixgram.cu ------------------------------------------------------------
 // b_n = H^H b_pix, lambda_n and the pulse's power steps on G_n = H^H P_n H
 cudaError_t pg_after_push(osar_ctx* ctx);
+cudaError_t prepare_pixgram_kernels();  // shared-memory carve-out, as the burst's
 cudaError_t pg_burst_begin(osar_ctx* ctx);
 cudaError_t pg_fista_step(osar_ctx* ctx);
 

@@ -227,6 +227,27 @@ cudaError_t scatter(osar_ctx* ctx, const double2* x, int gated) {
 
 }  // namespace
 
+cudaError_t prepare_pixgram_kernels() {
+  // the burst's matvec runs with the largest shared-memory carve-out; the
+  // kernels between its passes ask for the same one (no L1 / shared
+  // reconfiguration between launches)
+  const int v = cudaSharedmemCarveoutMaxShared;
+  const cudaFuncAttribute a = cudaFuncAttributePreferredSharedMemoryCarveout;
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, a, v);
+  };
+  set((const void*)k_pg_scatter<float2>);
+  set((const void*)k_pg_scatter<double2>);
+  set((const void*)k_pg_fista_finalize<float2>);
+  set((const void*)k_pg_fista_finalize<double2>);
+  set((const void*)k_pg_power_finalize);
+  set((const void*)k_pg_normalize);
+  set((const void*)k_pg_bvec);
+  set((const void*)k_pg_burst_begin);
+  return e;
+}
+
 cudaError_t pg_after_push(osar_ctx* ctx) {
   const PixGram& g = *ctx->pg;
   k_pg_bvec<<<blocks(g.M, PG_THREADS), PG_THREADS, 0, ctx->stream>>>(

@@ -335,6 +335,7 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = prepare_burst_kernels();
+  if (e == cudaSuccess && ctx->pg) e = prepare_pixgram_kernels();
   if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaGetDevice"));
   if (cfg->cuda_stream) {
     ctx->stream = (cudaStream_t)cfg->cuda_stream;
