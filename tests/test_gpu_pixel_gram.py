@@ -134,3 +134,26 @@ def test_pixel_gram_refuses_what_it_does_not_offer(tmp_path):
     # the context stays usable
     g.push_pulse(track[1], data[1])
     assert g.iterate(3) == 3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+def test_pixel_gram_non_white_pulses(prec):
+    # Eq. 12 with R_n = diag(variances): P_n = sum F^H R^-1 F and b_pix =
+    # sum F^H R^-1 d keep the factorisation, white and non-white pulses mixed
+    w = _w("squares", n_pulses=6, seed=21)
+    track, dic, _, data = build_problem(w)
+    of = orc.OnlineFista(oracle_config(w, dic))
+    g = _ctx(w, prec)
+    rng = np.random.default_rng(3)
+    t = TOL[prec]
+    for s in range(track.shape[0]):
+        var = None if s % 3 == 2 else rng.uniform(0.3, 3.0, w.n_freq)
+        of.push_pulse(track[s], data[s], var)
+        g.push_pulse(track[s], data[s], var)
+        of.iterate(10)
+        g.iterate(10, want_count=False)
+        assert rel_err(dic.conj().T @ g.gram() @ dic, of.s.gram) <= t["gram"]
+        assert rel_err(g.b(), of.s.b) <= t["b"]
+        assert rel_err(g.coeffs(), of.s.c_hat) <= t["c"]
+        st = g.state()
+        assert abs(st["lipschitz"] - of.s.lip) <= max(t["gram"], 1e-7) * of.s.lip * 10
