@@ -4,7 +4,7 @@ central finite differences (h = 1e-6).
 
 Tolerances: FP64 adjoint vs FP64 autograd <= 1e-8 relative; FP32-Gram
 adjoint vs FP64 <= 1e-4; finite differences vs the FP64 adjoint <= 1e-4
-(the spec bar).  Coordinates within 100 h of the shrinkage kink
+(the required bar).  Coordinates within 100 h of the shrinkage kink
 |u| = lambda tau would make differences meaningless, so the tests check the
 recorded margin first and nudge lambda until it is clear.
 

@@ -3,10 +3,10 @@ the same seeded inputs.
 
 Tolerances (relative 2-norm unless stated):
   FP64 path       Gram, b  <= 1e-9   (phase reductions agree to ~1e-10 rad)
-                  c        <= 1e-7   (spec bar 1e-5)
+                  c        <= 1e-7   (required: 1e-5)
   FP32 path       Gram     <= 2e-6,  c <= 1e-4
   split-BF16      Gram     <= 1e-4   (bf16 hi+lo keeps 2^-17 per factor),
-                  c        <= 1e-3   (spec bar)
+                  c        <= 1e-3   (required: 1e-3)
 """
 import os
 import tempfile
