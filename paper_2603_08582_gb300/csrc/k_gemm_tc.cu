@@ -484,8 +484,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool fail = false;
     int n = 0;  // pieces of this half processed so far
     // The 4 warps of a half pass the same barriers: every tile they enter
-    // has G_PIECES barriers, and whether to stop is the OR over the half, taken at
-    // a barrier, so all of them leave together.
+    // has G_PIECES barriers (one more with the power step), and whether to
+    // stop is the OR over the half, taken at a barrier, so all of them leave
+    // together.
     for (int t = unit; t < p.n_tiles; t += units, ++tcount) {
       const int4 tl = p.tiles[t];
       const bool store = !(rank && (tl.w & 1));
