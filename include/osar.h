@@ -252,6 +252,9 @@ osar_status osar_push_pulse_var(osar_ctx* ctx, const double gamma_xyz[3],
    once ||c^(k) - z^(k)||_2 <= tol ||c^(k)||_2 (decided on the device; the
    remaining launches return at once).  iters_done (nullable) receives the
    number of steps taken in this call, which synchronises the stream.
+   With iters_done = NULL a call only queues kernels on cuda_stream, so a
+   continuing call (not the first after a pulse) can be captured into a
+   CUDA graph and replayed, in order on that stream, for later pulses.
    Errors: OSAR_E_STATE before the first pulse, OSAR_E_INVALID for
    max_iters < 0. */
 osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
