@@ -180,7 +180,9 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
     """Build an osar_config.  dictionary: None (identity), "gaussian"
     (seeded Philox atoms, needs n_atoms), "edgelet" (binary edgelets of
     edgelet_lengths x edgelet_angles degrees at every pixel) or an N x M
-    complex array."""
+    complex array.  pixel_gram (edgelets only): keep the pixel-basis Gram
+    P_n = sum F^H F and apply G_n = H^H P_n H instead of storing G_n;
+    fuse_power_gram: form the pulse's first power step in the Gram update."""
     cfg = default_config()
     cfg.nx, cfg.ny, cfg.pixel_m = int(nx), int(ny), float(pixel_m)
     cfg.n_freq, cfg.f_lo_hz, cfg.f_hi_hz = int(n_freq), float(f_lo_hz), float(f_hi_hz)
