@@ -131,8 +131,8 @@ typedef struct {
      burst's first iterate z = c_hat (both vectors in one pass over the
      Gram), and that burst's first FISTA step uses the result; one Gram
      pass fewer per pulse, bitwise the same results.  0: separate passes.
-     (FP32 and split-BF16 matvecs; the FP64 path always uses separate
-     passes.) */
+     (FP32 and split-BF16 matvecs; the FP64 path and the pixel-space Gram
+     form always use separate passes.) */
   int32_t fuse_first_step;
   /* lambda path: 1..8 solutions of the same pulses that differ only in
      lambda.  n_lambdas > 1 takes lambda_list[l] (relative or absolute per
