@@ -212,9 +212,12 @@ typedef struct {
    pixel_gram = 0. */
 void osar_config_default(osar_config* cfg);
 
-/* Create a context: validates cfg, allocates the Gram (packed upper 128 x 128
-   blocks), data vector, coefficient state and per-pulse work buffers, builds
-   the dictionary on the device.  *out is NULL on failure.
+/* Create a context for the problem of Sec. III-C: the online reconstruction
+   starts from A_0 = 0, b_0 = 0 and c_hat_0 = 0 (Algorithm 1's input), over
+   the grid, frequencies and dictionary of Sec. II and III-A that cfg gives.
+   Validates cfg, allocates the Gram (packed upper 128 x 128 blocks), data
+   vector, coefficient state and per-pulse work buffers, and builds the
+   dictionary on the device.  *out is NULL on failure.
    Errors: OSAR_E_INVALID (sizes <= 0, unknown enums, M or N too large),
    OSAR_E_OOM, OSAR_E_CUDA. */
 osar_status osar_create(const osar_config* cfg, osar_ctx** out);
@@ -260,7 +263,8 @@ osar_status osar_push_pulse_var(osar_ctx* ctx, const double gamma_xyz[3],
 osar_status osar_iterate(osar_ctx* ctx, int32_t max_iters, double tol,
                          int32_t* iters_done);
 
-/* Copy c_hat (M complex) to host memory; synchronises. */
+/* Copy c_hat_n (M complex), the estimate Algorithm 1 returns after the
+   pulses pushed so far (Sec. III-C), to host memory; synchronises. */
 osar_status osar_get_coeffs(osar_ctx* ctx, double* out_c128);
 
 /* Copy c_hat (M complex128) into device memory out_dev; asynchronous. */
@@ -320,16 +324,23 @@ osar_status osar_gram_apply(osar_ctx* ctx, const double* x_c128,
                             double* y_c128);
 
 /* y = A_n x like osar_gram_apply, but without any allocation: x and y are
-   caller device buffers (M complex128 each, 16-byte aligned), the call is
-   asynchronous on the context's stream, and the matvec's scratch comes from
-   a 4 MiB static device array inside the library instead of cudaMalloc.
-   No counterpart in the paper: it exists for callers that may not allocate
-   device memory after start-up (fixed-budget embedded or flight pipelines,
-   hosts with their own memory pool).  Limit: contexts with M <= 4096 atoms
-   (larger ones return OSAR_E_INVALID).  The array is shared by all calls on
-   a device and keeps the last call's contents; calls that overlap on the GPU
-   race on it and must be ordered by the caller.  The first call on a device
-   looks up the array's address (make it before any stream capture). */
+   caller device buffers, the call is asynchronous on the context's stream,
+   and the matvec's scratch comes from a 4 MiB static device array inside the
+   library instead of cudaMalloc.  No counterpart in the paper: it exists for
+   callers that may not allocate device memory after start-up (fixed-budget
+   embedded or flight pipelines, hosts with their own memory pool).
+   Vectors: M complex128 each (interleaved doubles), device or managed memory
+   of the current device, 16-byte aligned; in the pixel-space Gram form the
+   apply works on P_n and the vectors have N (pixel) entries.
+   Limit: the Gram's dimension (M atoms, or N pixels in the pixel-space form)
+   at most 4096 always fits; larger ones return OSAR_E_INVALID, as do NULL,
+   host, other-device or unaligned vectors (checked before any launch).
+   The array is shared by all calls on a device and keeps the last call's
+   contents; calls that overlap on the GPU race on it and must be ordered by
+   the caller.  osar_create looks up the array's address on its device (under
+   CUDA's lazy module loading this is also when the array is placed in device
+   memory), so the apply itself allocates nothing; if that lookup failed the
+   first call repeats it (make that call before any stream capture). */
 osar_status osar_gram_apply_static(osar_ctx* ctx, const void* x_dev_c128,
                                    void* y_dev_c128);
 

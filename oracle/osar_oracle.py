@@ -331,6 +331,9 @@ class OnlineState:
     c_prev: Optional[np.ndarray] = None
     fresh: bool = True
     converged: bool = False
+    # u^(k) of the last step taken: kept so that a comparison can tell which
+    # coefficients sat within rounding of the threshold |u_i| = lambda tau
+    u: Optional[np.ndarray] = None
     history: list = field(default_factory=list)
 
 
@@ -399,7 +402,7 @@ class OnlineFista:
             if tol > 0.0:
                 cn = np.linalg.norm(c)
                 stop = np.linalg.norm(c - s.z) <= tol * cn
-            s.c_prev, s.z, s.t = c, z_next, t_next
+            s.c_prev, s.z, s.t, s.u = c, z_next, t_next, u
             done += 1
             if stop:
                 s.converged = True

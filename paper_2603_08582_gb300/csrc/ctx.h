@@ -309,6 +309,9 @@ cudaError_t launch_gram_expand(osar_ctx* ctx, int r0, int rows, double2* dense);
 cudaError_t launch_gram_entries(osar_ctx* ctx, const int2* rc, int count,
                                 double2* out);
 size_t gram_apply_scratch_bytes(const osar_ctx* ctx);
+// k_static.cu: look up the allocation-free apply's static array on the
+// current device (errors are left to that entry point to report)
+void prepare_static_scratch();
 cudaError_t launch_matvec(osar_ctx* ctx, const void* xt);
 // One Gram pass y = G x over the working-precision vector xt (Mp), into the
 // FP64 vector y; gated: the pass and its finalize skip once solution 0 has

@@ -10,9 +10,10 @@
 // copy of x and the segment / block partials) comes from one file-scope
 // device array instead of cudaMalloc.
 //
-// The array is GRAM_APPLY_STATIC_BYTES (4 MiB) on every GPU that loads the
-// library, held until the process exits.  It fits the scratch of any Gram
-// with M <= 4096 atoms in every precision; larger contexts are rejected with
+// The array is GRAM_APPLY_STATIC_BYTES (4 MiB) on every GPU where a context
+// is created, held until the process exits.  It fits the scratch of any Gram
+// with M <= 4096 rows in every precision (atoms; pixels N in the pixel-space
+// Gram form, whose apply works on P_n); larger contexts are rejected with
 // OSAR_E_INVALID.  All calls on a device share the array and it keeps the
 // last call's contents; every byte a call reads is written earlier in that
 // call, so nothing needs clearing.  Calls whose work overlaps on the GPU
@@ -20,9 +21,19 @@
 // ordered by the caller.
 //
 // Set-up: the array's device address is looked up once per device, with that
-// device current, by the first call made on it (cudaGetSymbolAddress); make
-// that first call before any stream capture on the device.
+// device current (cudaGetSymbolAddress).  osar_create does it for its device,
+// so that the lookup, and the module load that places the array in device
+// memory under CUDA's lazy loading, happen while the caller is still setting
+// up.  Should that lookup fail, the first osar_gram_apply_static call on the
+// device repeats it (then make that call before any stream capture).
+//
+// The caller's x and y are checked before any launch: both must be device
+// (or managed) memory that the current device can address and 16-byte
+// aligned.  A host pointer or a pointer into another GPU would otherwise make
+// the first kernel fault and leave the CUDA context unusable.
+#include <cstdint>
 #include <mutex>
+#include <string>
 
 #include "ctx.h"
 
@@ -53,7 +64,42 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
+// Device or managed memory usable by the current device, 16-byte aligned.
+bool device_vector_ok(const void* p, std::string* why) {
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0) {
+    *why = "not 16-byte aligned";
+    return false;
+  }
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the non-sticky error
+    *why = "not a CUDA pointer";
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) {
+    *why = a.type == cudaMemoryTypeHost ? "page-locked host memory, not device memory"
+                                        : "host memory, not device memory";
+    return false;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || a.device != dev) {
+    *why = "memory of another device";
+    return false;
+  }
+  return true;
+}
+
 }  // namespace
+
+namespace osar {
+// Called by osar_create with the context's device current: look the static
+// array up once per device now rather than inside the first apply.
+void prepare_static_scratch() {
+  void* p = nullptr;
+  if (scratch_address(&p) != cudaSuccess) cudaGetLastError();
+}
+}  // namespace osar
 
 extern "C" osar_status osar_gram_apply_static(osar_ctx* ctx,
                                               const void* x_dev_c128,
@@ -62,6 +108,15 @@ extern "C" osar_status osar_gram_apply_static(osar_ctx* ctx,
   if (ctx->sticky != OSAR_OK) return ctx->sticky;
   if (!x_dev_c128 || !y_dev_c128) {
     ctx->last_error = "osar_gram_apply_static: NULL vector";
+    return OSAR_E_INVALID;
+  }
+  std::string why;
+  if (!device_vector_ok(x_dev_c128, &why)) {
+    ctx->last_error = "osar_gram_apply_static: x is " + why;
+    return OSAR_E_INVALID;
+  }
+  if (!device_vector_ok(y_dev_c128, &why)) {
+    ctx->last_error = "osar_gram_apply_static: y is " + why;
     return OSAR_E_INVALID;
   }
   const size_t need = osar::gram_apply_scratch_bytes(ctx);

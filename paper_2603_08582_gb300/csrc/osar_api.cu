@@ -953,7 +953,11 @@ osar_status osar_create(const osar_config* cfg, osar_ctx** out) {
   osar::TraceRange trace_("osar_create");
   if (!out) return fail(nullptr, OSAR_E_INVALID, "out is NULL");
   *out = nullptr;
-  return create_impl(cfg, out);
+  const osar_status st = create_impl(cfg, out);
+  // the allocation-free Gram apply's static array: looked up now, on the
+  // context's device, so that its first call loads nothing
+  if (st == OSAR_OK) osar::prepare_static_scratch();
+  return st;
 }
 
 osar_status osar_destroy(osar_ctx* ctx) {

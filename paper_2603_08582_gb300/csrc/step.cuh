@@ -6,20 +6,16 @@
 namespace osar {
 namespace {
 
-// Shrink factor max(0, 1 - alpha/|u|) from |u|^2: FP64 on the FP64 path; on
-// the FP32-Gram paths (whose matvec is FP32 anyway) an FP32 reciprocal
-// square root, since GB300's FP64 pipes are ~1/64 of its FP32 rate.
+// Shrink factor max(0, 1 - alpha/|u|) from |u|^2, in FP64 on every path: near
+// the threshold 1 - alpha/|u| cancels, and an FP32 factor would leave a small
+// surviving coefficient with a large relative error.  It costs one FP64
+// square root and division per coefficient and step (the step's partial sums
+// stay in the matvec's precision).  The template parameter is the matvec's
+// working type and no longer changes the arithmetic.
 template <typename T2>
-__device__ __forceinline__ double shrink_keep(double mag2, double alpha);
-template <>
-__device__ __forceinline__ double shrink_keep<double2>(double mag2, double alpha) {
+__device__ __forceinline__ double shrink_keep(double mag2, double alpha) {
   const double mag = sqrt(mag2);
   return mag > alpha ? 1.0 - alpha / mag : 0.0;
-}
-template <>
-__device__ __forceinline__ double shrink_keep<float2>(double mag2, double alpha) {
-  if (!(mag2 > alpha * alpha)) return 0.0;
-  return (double)(1.0f - (float)alpha * rsqrtf((float)mag2));
 }
 
 }  // namespace

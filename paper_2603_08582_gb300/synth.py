@@ -14,7 +14,7 @@ the device so that a 16384 x 32768 dictionary never has to cross PCIe/C2C;
 this module implements it on the host so that the oracle sees identical atoms.
 
 Workload recipes (the paper's own scenes exist only as missing figures, so
-these stand in for them; see the workload table in the design notes):
+these stand in for them):
 
 * track: circular aperture centred on the scene centre, horizontal radius r,
   altitude h, P pulses evenly spaced (both ends inclusive) over `span_deg`

@@ -10,7 +10,8 @@ import pytest
 
 from oracle import osar_oracle as orc
 from paper_2603_08582_gb300 import osar
-from tests.helpers import small_workload, build_problem, oracle_config, rel_err
+from tests.helpers import (small_workload, build_problem, oracle_config, rel_err,
+                           assert_close, assert_coeffs, SUPPORT_DELTA)
 from tests.gpu_helpers import gpu_config
 
 pytestmark = pytest.mark.gpu
@@ -49,7 +50,8 @@ def test_path_solutions_equal_single_contexts_and_oracles(prec):
             assert np.array_equal(st["coeffs"], g.coeffs()), (prec, s, l)
             assert st["lambda"] == g.state()["lambda"]
             assert st["t"] == g.state()["t"]
-            assert rel_err(st["coeffs"], o.s.c_hat) <= TOL_C[prec], (prec, s, l)
+            assert_coeffs(st["coeffs"], o.s, TOL_C[prec], SUPPORT_DELTA[prec],
+                          f"c {prec} pulse {s} lambda {l}")
     assert np.array_equal(path.coeffs(), singles[0].coeffs())
 
 

@@ -9,7 +9,8 @@ import pytest
 
 from oracle import osar_oracle as orc
 from paper_2603_08582_gb300 import osar
-from tests.helpers import small_workload, build_problem, oracle_config, rel_err
+from tests.helpers import (small_workload, build_problem, oracle_config, rel_err,
+                           assert_close, assert_coeffs, SUPPORT_DELTA)
 from tests.gpu_helpers import gpu_config
 
 pytestmark = pytest.mark.gpu
@@ -33,9 +34,9 @@ def _run(w, prec, defer=False, steps=10):
         g.push_pulse(track[s], data[s], var)
         of.iterate(steps)
         g.iterate(steps, want_count=False)
-        assert rel_err(g.b(), of.s.b) <= t["b"], (prec, s)
-        assert rel_err(g.coeffs(), of.s.c_hat) <= t["c"], (prec, s)
-        assert rel_err(g.gram(), of.s.gram) <= t["gram"], (prec, s)
+        assert_close(g.b(), of.s.b, t["b"], f"b {prec} pulse {s}")
+        assert_coeffs(g.coeffs(), of.s, t["c"], SUPPORT_DELTA[prec], f"c {prec} pulse {s}")
+        assert_close(g.gram(), of.s.gram, t["gram"], f"gram {prec} pulse {s}")
         st = g.state()
         assert abs(st["lipschitz"] - of.s.lip) <= max(t["gram"], 1e-7) * of.s.lip * 10
 

@@ -13,7 +13,8 @@ import pytest
 
 from oracle import osar_oracle as orc
 from paper_2603_08582_gb300 import osar
-from tests.helpers import small_workload, build_problem, rel_err, oracle_config
+from tests.helpers import (small_workload, build_problem, rel_err, oracle_config,
+                           assert_close, assert_coeffs, SUPPORT_DELTA)
 from tests.gpu_helpers import gpu_config
 
 pytestmark = pytest.mark.gpu
@@ -68,9 +69,9 @@ def test_pixel_gram_parity_every_pulse(prec, name):
     def check(s, of, g, no, ng, h):
         p = g.gram()
         assert p.shape == (w.nx * w.ny, w.nx * w.ny)
-        assert rel_err(h.conj().T @ p @ h, of.s.gram) <= t["gram"]
-        assert rel_err(g.b(), of.s.b) <= t["b"]
-        assert rel_err(g.coeffs(), of.s.c_hat) <= t["c"]
+        assert_close(h.conj().T @ p @ h, of.s.gram, t["gram"], "H^H P H")
+        assert_close(g.b(), of.s.b, t["b"], "b")
+        assert_coeffs(g.coeffs(), of.s, t["c"], SUPPORT_DELTA[prec])
         st = g.state()
         assert st["n"] == of.s.n
         assert abs(st["lambda"] - of.s.lam) <= t["b"] * of.s.lam  # from b_n
@@ -85,7 +86,7 @@ def test_pixel_gram_stop_rule_counts():
 
     def check(s, of, g, no, ng, h):
         assert ng == no
-        assert rel_err(g.coeffs(), of.s.c_hat) <= TOL["fp64"]["c"]
+        assert_coeffs(g.coeffs(), of.s, TOL["fp64"]["c"], SUPPORT_DELTA["fp64"])
 
     _run(w, "fp64", steps=30, tol=1e-4, check=check)
 
@@ -152,8 +153,8 @@ def test_pixel_gram_non_white_pulses(prec):
         g.push_pulse(track[s], data[s], var)
         of.iterate(10)
         g.iterate(10, want_count=False)
-        assert rel_err(dic.conj().T @ g.gram() @ dic, of.s.gram) <= t["gram"]
-        assert rel_err(g.b(), of.s.b) <= t["b"]
-        assert rel_err(g.coeffs(), of.s.c_hat) <= t["c"]
+        assert_close(dic.conj().T @ g.gram() @ dic, of.s.gram, t["gram"], "H^H P H")
+        assert_close(g.b(), of.s.b, t["b"], "b")
+        assert_coeffs(g.coeffs(), of.s, t["c"], SUPPORT_DELTA[prec])
         st = g.state()
         assert abs(st["lipschitz"] - of.s.lip) <= max(t["gram"], 1e-7) * of.s.lip * 10

@@ -14,7 +14,8 @@ import numpy as np
 import pytest
 
 from paper_2603_08582_gb300 import osar
-from tests.helpers import small_workload, build_problem, rel_err
+from tests.helpers import (small_workload, build_problem, rel_err,
+                           assert_close, assert_coeffs, SUPPORT_DELTA)
 from tests.gpu_helpers import gpu_config, run_pair
 
 pytestmark = pytest.mark.gpu
@@ -85,9 +86,9 @@ def test_fused_power_step_meets_the_oracle_bar():
     w = _dictionary()
 
     def check(s, of, g, no, ng):
-        assert rel_err(g.b(), of.s.b) <= TOL_B
-        assert rel_err(g.gram(), of.s.gram) <= TOL_GRAM
-        assert rel_err(g.coeffs(), of.s.c_hat) <= TOL_C
+        assert_close(g.b(), of.s.b, TOL_B, "b")
+        assert_close(g.gram(), of.s.gram, TOL_GRAM, "gram")
+        assert_coeffs(g.coeffs(), of.s, TOL_C, SUPPORT_DELTA["split_bf16"])
         assert abs(g.state()["lipschitz"] - of.s.lip) <= 1e-5 * of.s.lip
 
     run_pair(w, "split_bf16", steps=12, per_pulse=check)

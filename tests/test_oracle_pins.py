@@ -340,17 +340,101 @@ def test_momentum_carried_vs_restart():
     assert abs(rest.s.t - t) < 1e-12
 
 
-def test_tolerance_stop_rule():
+def _hand_fista_2x2(g, b, lam, lip, t1, steps):
+    """Algorithm 1's inner loop on a 2 x 2 problem in scalar complex
+    arithmetic (no oracle function): returns per step the iterate c_k, the
+    point z_k where the gradient was taken, the momentum point z_{k+1} and the
+    previous iterate c_{k-1}."""
+    tau = 1.0 / lip
+    c_prev = [0j, 0j]
+    z = [0j, 0j]
+    t = t1
+    out = []
+    for _ in range(steps):
+        grad = [g[0][0] * z[0] + g[0][1] * z[1] - b[0],
+                g[1][0] * z[0] + g[1][1] * z[1] - b[1]]
+        u = [z[i] - tau * grad[i] for i in range(2)]
+        c = []
+        for ui in u:
+            a = abs(ui)
+            c.append(ui * (1.0 - lam * tau / a) if a > lam * tau else 0j)
+        t_next = (1.0 + (1.0 + 4.0 * t * t) ** 0.5) / 2.0
+        beta = (t - 1.0) / t_next
+        z_next = [c[i] + beta * (c[i] - c_prev[i]) for i in range(2)]
+        out.append({"c": c, "z": z, "z_next": z_next, "c_prev": c_prev})
+        c_prev, z, t = c, z_next, t_next
+    return out
+
+
+def _norm2(v):
+    return sum(abs(x) ** 2 for x in v) ** 0.5
+
+
+def test_tolerance_stop_rule_by_hand():
+    """The burst stops at the first step k with |c^(k) - z^(k)| <= tol |c^(k)|,
+    z^(k) the point where step k took its gradient.  The gaps are computed by
+    hand on a 2 x 2 Hermitian problem; tol is placed so that the two plausible
+    misreadings (|c^(k) - c^(k-1)|, or the post-momentum point z^(k+1)) stop
+    at other steps, so either would fail here."""
+    g = [[2.0 + 0j, 0.5 - 0.5j], [0.5 + 0.5j, 1.0 + 0j]]
+    b = [1.0 + 1.0j, -0.5 + 0.2j]
+    lam, lip = 0.1, 3.0
+    steps = _hand_fista_2x2(g, b, lam, lip, 1.0, 40)
+
+    def first_stop(gap, tol):
+        for k, st in enumerate(steps):
+            if gap(st) <= tol * _norm2(st["c"]):
+                return k + 1
+        return None
+
+    right = lambda st: _norm2([st["c"][i] - st["z"][i] for i in range(2)])
+    prev = lambda st: _norm2([st["c"][i] - st["c_prev"][i] for i in range(2)])
+    post = lambda st: _norm2([st["c"][i] - st["z_next"][i] for i in range(2)])
+    tol = None
+    for cand in np.geomspace(1e-1, 1e-8, 200):
+        k = first_stop(right, cand)
+        if k is not None and k > 2 and first_stop(prev, cand) != k \
+                and first_stop(post, cand) != k:
+            tol = float(cand)
+            break
+    assert tol is not None, "no tolerance separates the three readings"
+    k_star = first_stop(right, tol)
+
+    of = orc.OnlineFista(orc.OracleConfig(nx=1, ny=2, pixel_m=1.0, n_freq=1,
+                                          f_lo_hz=1e10, f_hi_hz=1e10,
+                                          lam=lam, lambda_relative=False))
+    of.s.gram = np.array(g, dtype=np.complex128)
+    of.s.b = np.array(b, dtype=np.complex128)
+    of.s.n, of.s.lip, of.s.lam = 1, lip, lam
+    n = of.iterate(40, tol=tol)
+    assert n == k_star
+    assert np.allclose(of.s.c_hat, steps[k_star - 1]["c"], rtol=0, atol=1e-15)
+    assert of.iterate(10, tol=tol) == 0            # a converged burst stays put
+    # the gap at the stop is below tol, the one before it above
+    assert right(steps[k_star - 1]) <= tol * _norm2(steps[k_star - 1]["c"])
+    assert right(steps[k_star - 2]) > tol * _norm2(steps[k_star - 2]["c"])
+
+
+def test_tolerance_stop_point_is_near_optimal():
+    """At the stop, c = prox(z - tau grad f(z)) gives (G - L I)(c - z) as an
+    element of grad f(c) + lambda d|c|_1, so the oracle's KKT residual (max
+    violation / lambda) is at most L |c - z| / lambda <= L tol |c| / lambda
+    when 0 <= G <= L I."""
     w = small_workload(nx=6, ny=6, n_freq=12, n_pulses=6)
     track, dic, c_true, data = build_problem(w)
     of = orc.OnlineFista(oracle_config(w, None))
     for s in range(w.n_pulses):
         of.push_pulse(track[s], data[s])
-    n = of.iterate(5000, tol=1e-5)
-    assert 0 < n < 5000
-    z_gap = np.linalg.norm(of.s.c_hat - of.s.c_prev)
-    assert z_gap == 0
-    assert of.iterate(10, tol=1e-5) == 0           # converged burst stays put
+    # the step size of the bound: L >= lambda_max(G)
+    of.s.lip = 1.01 * float(np.linalg.eigvalsh(of.s.gram).max())
+    tol = 1e-10
+    n = of.iterate(200000, tol=tol)
+    assert 0 < n < 200000
+    c = of.s.c_hat
+    bound = of.s.lip * tol * np.linalg.norm(c) / of.s.lam
+    kkt = orc.kkt_residual(of.s.gram, of.s.b, c, of.s.lam)
+    assert kkt <= bound * (1 + 1e-6) + 1e-12, (kkt, bound)
+    assert bound < 1e-6
 
 
 # ------------------------------------------------------------- Table I ---
