@@ -344,6 +344,37 @@ osar_status osar_gram_apply(osar_ctx* ctx, const double* x_c128,
 osar_status osar_gram_apply_static(osar_ctx* ctx, const void* x_dev_c128,
                                    void* y_dev_c128);
 
+/* Reconstruction quality of c_hat_n (Sec. IV-B).  The experiments count
+   the "large" coefficients, |c_m| > 2e-2, against slow time, and report the
+   SNR of Eq. 18, 20 log10(mu_signal / mu_noise).  This call reads mu as an
+   RMS amplitude in the coefficient domain: over a reference support (the
+   scene's true atoms, which only the caller knows) and over its complement.
+   Deterministic (one CTA reduces the vector in a fixed order), in FP64;
+   synchronises.  A lambda path reports solution 0; the pixel-space Gram form
+   its atom coefficients. */
+typedef struct {
+  int32_t n_large;                /* m with |c_m| > threshold */
+  int32_t n_nonzero;              /* m with c_m != 0 */
+  int32_t n_support;              /* distinct indices of the support given */
+  int32_t large_outside_support;  /* large coefficients off the support (all
+                                     of them without a support) */
+  double l1;                      /* sum_m |c_m| */
+  double max_abs;                 /* max_m |c_m| */
+  double rms_signal;              /* RMS of |c_m| on the support (0 without) */
+  double rms_noise;               /* RMS of |c_m| off the support */
+  double snr_db;                  /* 20 log10(rms_signal / rms_noise); NaN
+                                     without a support, +inf when rms_noise
+                                     is 0 and rms_signal is not */
+} osar_metrics;
+
+/* threshold >= 0 (finite); support: n_support atom indices in [0, M) (host,
+   duplicates allowed), or NULL with n_support = 0.  The first call allocates
+   a scratch of M + 256 bytes, kept until destroy.  Errors: OSAR_E_INVALID
+   (NULL out, bad threshold, index out of range), OSAR_E_OOM, OSAR_E_CUDA. */
+osar_status osar_get_metrics(osar_ctx* ctx, double threshold,
+                             const int32_t* support, int32_t n_support,
+                             osar_metrics* out);
+
 /* Noise-free pulse data d = G_n c for a platform at gamma_xyz (Eqs. 5-6),
    computed on the device in FP64: c (M complex, host) in, d (n_freq
    complex, host) out.  Does not touch the statistics; synchronises. */

@@ -42,6 +42,10 @@ Readings taken where the paper is silent, ambiguous or garbled:
   (z, c^(k-1) and t are kept), so two bursts of a and b steps equal one burst
   of a + b steps.
 
+* the SNR of Eq. 18 takes mu as an RMS amplitude (20 log10 of an amplitude
+  ratio) and, since the scenes' images are not given, is read in the
+  coefficient domain: the true atoms against the rest.
+
 Parity status: every function below is pinned by closed forms, invariants,
 brute force or an independent solver in tests/test_oracle_pins.py, except the
 online trajectory as a whole (lambda_n schedule, carried t, noise draw), whose
@@ -285,6 +289,26 @@ def fista_fixed(g: np.ndarray, b: np.ndarray, lam: float, lip: float,
         t = t_next
         hist.append(c)
     return c_prev, t, hist
+
+
+def large_coefficient_count(c: np.ndarray, threshold: float = 2e-2) -> int:
+    """Number of "large" coefficients, |c_m| > threshold (§IV-B counts them
+    with threshold 2e-2 against slow time)."""
+    return int(np.count_nonzero(np.abs(np.asarray(c)) > threshold))
+
+
+def coefficient_snr_db(c: np.ndarray, support) -> float:
+    """SNR of Eq. 18, 20 log10(mu_signal / mu_noise), with mu read as the RMS
+    amplitude of the coefficients over the reference support (signal) and
+    over the remaining coefficients (noise)."""
+    mag = np.abs(np.asarray(c))
+    on = np.zeros(mag.size, dtype=bool)
+    on[np.asarray(support, dtype=np.int64)] = True
+    mu_s = np.sqrt(np.mean(mag[on] ** 2))
+    mu_n = np.sqrt(np.mean(mag[~on] ** 2)) if np.any(~on) else 0.0
+    if mu_n == 0.0:
+        return float("inf") if mu_s > 0 else float("nan")
+    return float(20.0 * np.log10(mu_s / mu_n))
 
 
 def memory_values(m_atoms: int, n_pixels: int, n_r: int, n: int):

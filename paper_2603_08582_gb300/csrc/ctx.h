@@ -219,6 +219,9 @@ struct osar_ctx {
 
   osar::Guards guards;  // guard regions behind device buffers (guard_bytes)
 
+  // osar_get_metrics scratch (allocated by its first call): sums + mask
+  void* metrics_buf = nullptr;
+
   // differentiation-form scratch (allocated by the first unrolled gradient)
   void* adj_buf = nullptr;
   size_t adj_bytes = 0;

@@ -69,7 +69,7 @@ void free_all(osar_ctx* ctx) {
                   ctx->segpart_x, ctx->tilepart_x, ctx->gn_hi, ctx->gn_lo,
                   ctx->Apl_alt, ctx->corr, ctx->corr_u, ctx->corr_tick,
                   ctx->atom_ptr, ctx->atom_pix, ctx->wk_dev, ctx->gp_col,
-                  ctx->gp_row};
+                  ctx->gp_row, ctx->metrics_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->pg) {

@@ -39,6 +39,7 @@ EXPORTS = [
     "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
     "osar_gram_apply_static",
     "osar_simulate_pulse", "osar_unroll_grad", "osar_synchronize",
+    "osar_get_metrics",
     "osar_probe_bounded_wait", "osar_check_guards", "osar_poke_guard",
     "osar_batch_check_guards",
     "osar_profile_enable",
@@ -72,6 +73,16 @@ class OsarConfig(C.Structure):
         ("n_edgelet_lengths", C.c_int32), ("edgelet_lengths", C.c_void_p),
         ("n_edgelet_angles", C.c_int32), ("edgelet_angles_deg", C.c_void_p),
         ("fuse_power_gram", C.c_int32), ("pixel_gram", C.c_int32),
+    ]
+
+
+class OsarMetrics(C.Structure):
+    _fields_ = [
+        ("n_large", C.c_int32), ("n_nonzero", C.c_int32),
+        ("n_support", C.c_int32), ("large_outside_support", C.c_int32),
+        ("l1", C.c_double), ("max_abs", C.c_double),
+        ("rms_signal", C.c_double), ("rms_noise", C.c_double),
+        ("snr_db", C.c_double),
     ]
 
 
@@ -121,6 +132,8 @@ def load_library(path: str = LIB_PATH):
         "osar_unroll_grad": (I32, [P, I32, I32, C.c_double, C.c_double,
                                      C.c_double, D, D, D, D, D, D, D]),
         "osar_synchronize": (I32, [P]),
+        "osar_get_metrics": (I32, [P, C.c_double, C.POINTER(I32), I32,
+                                   C.POINTER(OsarMetrics)]),
         "osar_probe_bounded_wait": (I32, [P, C.c_int64]),
         "osar_check_guards": (I32, [P, C.POINTER(I32)]),
         "osar_poke_guard": (I32, [P, I32]),
@@ -382,6 +395,19 @@ class Osar:
         on the context's stream; see osar_gram_apply_static)."""
         self._check(self._lib.osar_gram_apply_static(
             self._h, C.c_void_p(x_dev_ptr), C.c_void_p(y_dev_ptr)))
+
+    def metrics(self, threshold: float = 2e-2, support=None) -> dict:
+        """Large-coefficient count and the coefficient-domain SNR of c_hat
+        against a reference support (osar_get_metrics)."""
+        out = OsarMetrics()
+        if support is None:
+            sp, n = None, 0
+        else:
+            sv = np.ascontiguousarray(np.asarray(support, dtype=np.int32))
+            sp, n = sv.ctypes.data_as(C.POINTER(C.c_int32)), int(sv.size)
+        self._check(self._lib.osar_get_metrics(self._h, float(threshold), sp, n,
+                                               C.byref(out)))
+        return {k: getattr(out, k) for k, _ in OsarMetrics._fields_}
 
     def simulate_pulse(self, gamma, coeffs) -> np.ndarray:
         g = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64))

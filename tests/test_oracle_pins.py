@@ -437,6 +437,29 @@ def test_tolerance_stop_point_is_near_optimal():
     assert bound < 1e-6
 
 
+# ------------------------------------------------------- quality (§IV-B) ---
+
+def test_large_coefficient_count_by_hand():
+    c = np.array([0.03, -0.02, 0.02 + 0.001j, 0.5j, 0.0, -0.0199 - 0.0001j])
+    # |c| = 0.03, 0.02, 0.020025, 0.5, 0, 0.01990025: strictly above 0.02
+    assert orc.large_coefficient_count(c) == 3
+    assert orc.large_coefficient_count(c, 0.0) == 5
+    assert orc.large_coefficient_count(np.zeros(7)) == 0
+
+
+def test_coefficient_snr_by_hand():
+    # support {0, 1}: RMS sqrt((9 + 16) / 2); rest: sqrt((9e-4 + 16e-4) / 2);
+    # ratio 100 -> exactly 40 dB
+    c = np.array([3.0, 4.0j, 0.03, -0.04j])
+    assert orc.coefficient_snr_db(c, [0, 1]) == pytest.approx(40.0, abs=1e-12)
+    # duplicates in the support change nothing; an empty complement is +inf
+    assert orc.coefficient_snr_db(c, [1, 0, 1]) == pytest.approx(40.0, abs=1e-12)
+    assert orc.coefficient_snr_db(c, [0, 1, 2, 3]) == float("inf")
+    # equal RMS on both sides: 0 dB
+    assert orc.coefficient_snr_db(np.array([1.0, 1j, -1.0, 0.6 + 0.8j]),
+                                  [0, 3]) == pytest.approx(0.0, abs=1e-12)
+
+
 # ------------------------------------------------------------- Table I ---
 
 def test_memory_table_golden():
