@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 256x256 leg (with and without online "
+                         "lambda tuning)")
     ap.add_argument("--fp64-pulses", type=int, default=2)
     ap.add_argument("--fp32-pulses", type=int, default=4)
     ap.add_argument("--forms", action="store_true",
@@ -484,12 +487,91 @@ def run_ours(args):
         line["cpu_baseline"] = cpu
     if accuracy is not None:
         line["accuracy_vs_fp64_oracle"] = accuracy
+    if rank == 0 and args.workload == "c2" and not args.no_large:
+        line["large_online_256x256"] = run_large_online(stream)
     if args.forms and rank == 0:
         line["forms"] = run_forms(stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_large_online(stream, warmup=4, pulses=24, tune_every=8):
+    """The 256 x 256 pixel-basis workload (N = M = 65536, K = 1024, 10 FISTA
+    steps per pulse, split-BF16), without and with online lambda tuning (the
+    burst's adjoint every `tune_every` pulses against the synthetic scene,
+    osar_set_lambda from the next pulse on)."""
+    import torch
+    from paper_2603_08582_gb300 import synth
+    from paper_2603_08582_gb300.tuning import OnlineLambdaTuner
+    w = synth.workloads()["c5_256x256_split_bf16"]
+    steps = w.inner_steps
+    c_true = synth.workload_scene(w)
+    peaks, src = measured_peaks()
+    out = {"workload": w.name, "n_atoms": w.m_atoms, "n_freq": w.n_freq,
+           "inner_steps": steps, "pulses_timed": pulses,
+           "pulses_warmup": warmup}
+    track = data = None
+    for tuned in (False, True):
+        ctx = make_ctx(w, "split_bf16", stream.cuda_stream)
+        if track is None:
+            track, data = pulse_data(ctx, w, warmup + pulses)
+        tuner = (OnlineLambdaTuner(ctx, c_true, rho=w.lambda_rel, steps=steps,
+                                   every=tune_every) if tuned else None)
+        for s in range(warmup):
+            ctx.push_pulse(track[s], data[s])
+            if tuner:
+                tuner.after_push(s)
+            ctx.iterate(steps, 0.0, want_count=False)
+        ctx.synchronize()
+        ctx.profile_reset()
+        ctx.profile_enable(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(warmup, warmup + pulses):
+            ctx.push_pulse(track[s], data[s])
+            if tuner:
+                tuner.after_push(s)
+            ctx.iterate(steps, 0.0, want_count=False)
+        ctx.synchronize()
+        wall = time.perf_counter() - t0
+        g_n, g_ms = ctx.profile_read("gram_gemm")
+        mv_n, mv_ms = ctx.profile_read("matvec")
+        passes = ctx.profile_passes()
+        ctx.profile_enable(False)
+        err = float(np.linalg.norm(ctx.coeffs() - c_true) / np.linalg.norm(c_true))
+        nblk = ctx_blocks(w.m_atoms)
+        kp = ((w.n_freq + 127) // 128) * 128
+        gram_flops = nblk * 3 * 2 * 128 * 256 * 2 * kp
+        gram_bytes = nblk * 128 * 128 * 8
+        mv_avg = mv_ms / max(passes, 1)
+        res = {"pulses_per_s": round(pulses / wall, 3),
+               "ms_per_pulse": round(1e3 * wall / pulses, 2),
+               "device_gb": round(ctx.device_bytes() / 1e9, 1),
+               "rel_err_vs_scene": round(err, 4),
+               "gram_update": {"avg_ms": round(g_ms / max(g_n, 1), 3),
+                               "tflops": round(gram_flops / (g_ms / max(g_n, 1) / 1e3) / 1e12, 1),
+                               "frac_of_sustained": round(gram_flops / (g_ms / max(g_n, 1) / 1e3) / 1e12
+                                                          / peaks["bf16_tflops_sustained"], 3)},
+               "matvec": {"avg_ms_per_pass": round(mv_avg, 4),
+                          "gbs": round(gram_bytes / mv_avg / 1e6, 1),
+                          "frac_of_hbm": round(gram_bytes / mv_avg / 1e6 / peaks["hbm_gbs"], 3)}}
+        if tuner:
+            hist = tuner.history
+            res["lambda_tuning"] = {
+                "rule": "log rho -= 0.25 clip(lambda dL/dlambda / L, -1, 1) every "
+                        f"{tune_every} pulses; L = |c_T - c_scene|^2 through the "
+                        f"{steps}-step burst (osar_unroll_grad)",
+                "updates": len(hist),
+                "rho_first_last": [round(hist[0]["rho"], 5), round(tuner.rho, 5)] if hist else None,
+                "loss_first_last": [hist[0]["loss"], hist[-1]["loss"]] if hist else None}
+            out["tuned"] = res
+        else:
+            out["untuned"] = res
+        ctx.close()
+    out["peak_source"] = src
+    return out
 
 
 def ctx_blocks(m):

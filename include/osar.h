@@ -405,6 +405,15 @@ osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
                              double* loss, double* d_lambda, double* d_tau,
                              double* d_b_c128, double* c_T_c128);
 
+/* Change the lambda setting of solution l (0 <= l < n_lambdas; 0 without a
+   lambda path): a factor rho (lambda_n = rho ||b_n||_inf) when the context
+   is relative, else the absolute lambda, finite and >= 0.  It takes effect
+   at the next pulse's lambda_n refresh (the current burst keeps its
+   lambda_n).  The paper leaves online parameter tuning to future work
+   (Sec. I, Sec. V); this call and osar_unroll_grad let a caller tune lambda
+   while the pulses arrive.  Errors: OSAR_E_INVALID. */
+osar_status osar_set_lambda(osar_ctx* ctx, int32_t l, double lambda);
+
 /* Wait for all work queued on the context's stream (and on its side
    stream, see overlap_synthesis). */
 osar_status osar_synchronize(osar_ctx* ctx);

@@ -361,18 +361,56 @@ class OnlineState:
     history: list = field(default_factory=list)
 
 
+class MatrixFreeGram:
+    """The accumulated Gram A_n kept as its pulses' blocks: A_n x is applied as
+    sum_k G_k^H R_k^{-1} (G_k x) (Eqs. 10, 12-13) without forming the M x M
+    matrix, for problems whose Gram does not fit in host memory.  Supports
+    `gram @ x`, so Algorithm 1 and the power iteration use it unchanged."""
+
+    def __init__(self):
+        self.blocks = []   # G_k (K x M)
+        self.weights = []  # diagonal of R_k^{-1} (K), or None for R_k = I
+
+    def add(self, a_s: np.ndarray, noise_var=None) -> None:
+        self.blocks.append(a_s)
+        self.weights.append(None if noise_var is None else
+                            1.0 / np.asarray(noise_var, dtype=np.float64))
+
+    def __matmul__(self, x: np.ndarray) -> np.ndarray:
+        out = np.zeros(self.blocks[0].shape[1], dtype=np.complex128)
+        for a, w in zip(self.blocks, self.weights):
+            r = a @ x
+            if w is not None:
+                r = w * r
+            out += (r.conj() @ a).conj()         # G_k^H r, without a copy of G_k^H
+        return out
+
+    def entries(self, rows, cols) -> np.ndarray:
+        """A_n[rows[q], cols[q]] = sum_k conj(G_k[:, i]) R_k^{-1} G_k[:, j]."""
+        rows = np.asarray(rows)
+        cols = np.asarray(cols)
+        out = np.zeros(rows.size, dtype=np.complex128)
+        for a, w in zip(self.blocks, self.weights):
+            wa = a[:, cols] if w is None else w[:, None] * a[:, cols]
+            out += np.sum(a[:, rows].conj() * wa, axis=0)
+        return out
+
+
 class OnlineFista:
     """Pulse-by-pulse reference: push_pulse applies Eqs. 12-13 and the L / lambda
-    updates, iterate runs Algorithm 1's inner loop."""
+    updates, iterate runs Algorithm 1's inner loop.  matrix_free=True keeps
+    the Gram as a MatrixFreeGram (the same arithmetic by Eq. 10, for sizes
+    whose M x M matrix does not fit in host memory)."""
 
-    def __init__(self, cfg: OracleConfig):
+    def __init__(self, cfg: OracleConfig, matrix_free: bool = False):
         self.cfg = cfg
         self.x = pixel_positions(cfg.nx, cfg.ny, cfg.pixel_m)
         self.f = frequencies(cfg.n_freq, cfg.f_lo_hz, cfg.f_hi_hz)
         m = self.x.shape[0] if cfg.dictionary is None else cfg.dictionary.shape[1]
         self.m = m
+        self.matrix_free = matrix_free
         self.s = OnlineState(
-            gram=np.zeros((m, m), dtype=np.complex128),
+            gram=MatrixFreeGram() if matrix_free else np.zeros((m, m), dtype=np.complex128),
             b=np.zeros(m, dtype=np.complex128),
             c_hat=np.zeros(m, dtype=np.complex128),
             v=np.full(m, 1.0 / np.sqrt(m), dtype=np.complex128))
@@ -387,7 +425,10 @@ class OnlineFista:
         (R_n = diag(noise_var)), None for R_n = I."""
         s, cfg = self.s, self.cfg
         a_s = self.block(gamma)
-        s.gram = s.gram + gram_increment(a_s, noise_var)         # Eq. 13
+        if self.matrix_free:
+            s.gram.add(a_s, noise_var)                           # Eq. 13, kept as blocks
+        else:
+            s.gram = s.gram + gram_increment(a_s, noise_var)     # Eq. 13
         s.b = s.b + data_increment(a_s, d_s, noise_var)          # Eq. 13
         s.n += 1
         if cfg.lambda_relative:

@@ -1314,6 +1314,17 @@ osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
   return OSAR_OK;
 }
 
+osar_status osar_set_lambda(osar_ctx* ctx, int32_t l, double lambda) {
+  osar::TraceRange trace_("osar_set_lambda");
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (l < 0 || l >= ctx->n_lam || !is_finite(lambda) || lambda < 0)
+    return fail(ctx, OSAR_E_INVALID, "osar_set_lambda: bad solution index or lambda");
+  ctx->lam.v[l] = lambda;
+  if (ctx->n_lam == 1) ctx->cfg.lambda = lambda;
+  return OSAR_OK;
+}
+
 osar_status osar_synchronize(osar_ctx* ctx) {
   osar::TraceRange trace_("osar_synchronize");
   osar_status st = check_usable(ctx);

@@ -39,7 +39,7 @@ EXPORTS = [
     "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
     "osar_gram_apply_static",
     "osar_simulate_pulse", "osar_unroll_grad", "osar_synchronize",
-    "osar_get_metrics",
+    "osar_get_metrics", "osar_set_lambda",
     "osar_probe_bounded_wait", "osar_check_guards", "osar_poke_guard",
     "osar_batch_check_guards",
     "osar_profile_enable",
@@ -132,6 +132,7 @@ def load_library(path: str = LIB_PATH):
         "osar_unroll_grad": (I32, [P, I32, I32, C.c_double, C.c_double,
                                      C.c_double, D, D, D, D, D, D, D]),
         "osar_synchronize": (I32, [P]),
+        "osar_set_lambda": (I32, [P, I32, C.c_double]),
         "osar_get_metrics": (I32, [P, C.c_double, C.POINTER(I32), I32,
                                    C.POINTER(OsarMetrics)]),
         "osar_probe_bounded_wait": (I32, [P, C.c_int64]),
@@ -434,6 +435,11 @@ class Osar:
             _dptr(ct.view(np.float64))))
         return {"loss": loss.value, "d_lambda": dl.value, "d_tau": dt.value,
                 "d_b": db, "c_T": ct}
+
+    def set_lambda(self, lam: float, l: int = 0):
+        """Lambda setting of solution l from the next pulse on (a factor of
+        ||b_n||_inf when the context is relative)."""
+        self._check(self._lib.osar_set_lambda(self._h, int(l), float(lam)))
 
     def data_grad(self, gamma, d_b) -> np.ndarray:
         """dL/dd_s = G_s dL/db for the pulse at gamma (the forward model

@@ -9,7 +9,11 @@ multi-tile path runs:
   so each SM pair of the Gram update handles many tiles (TMEM double buffer,
   the epilogue's prefetch across tile boundaries, the fused power step's
   tile-parity reduction buffers) and the matvec hands out segment tickets;
-* the 128 x 128 / M = 32768 / K = 512 workload itself (its first pulses).
+* the 128 x 128 / M = 32768 / K = 512 workload itself (its first pulses);
+* the 256 x 256 pixel-basis workload (M = 65536, K = 1024, 10 steps per
+  pulse; its first pulses), against the oracle in its matrix-free mode
+  (Eq. 10: A_n x = sum_k G_k^H G_k x), since the 69 GB FP64 Gram does not
+  fit in host memory.
 
 Bars (split-BF16, as in test_gpu_parity): b and sampled Gram entries <= 1e-4,
 coefficients <= 1e-3, each as a relative 2-norm and as a worst element
@@ -50,8 +54,9 @@ def _sampled_entries(m, rng, k=48):
 def _compare(of, gpu, rng, what):
     assert_close(gpu.b(), of.s.b, TOL_B, f"{what} b")
     rows, cols = _sampled_entries(of.m, rng)
-    assert_close(gpu.gram_entries(rows, cols), of.s.gram[rows, cols], TOL_GRAM,
-                 f"{what} gram entries")
+    ref = (of.s.gram.entries(rows, cols) if of.matrix_free
+           else of.s.gram[rows, cols])
+    assert_close(gpu.gram_entries(rows, cols), ref, TOL_GRAM, f"{what} gram entries")
     st = gpu.state()
     assert st["n"] == of.s.n
     assert abs(st["lambda"] - of.s.lam) <= 1e-3 * of.s.lam, (what, st, of.s.lam)
@@ -92,4 +97,31 @@ def test_headline_128x128_M32768_first_pulses():
     w = synth.workloads()["c2_128x128_split_bf16"]
     of, gpu, errs = _run(w, pulses=3, steps=20, rng=np.random.default_rng(2))
     print("128x128 M=32768 split-BF16 coefficient errors per pulse:",
+          " ".join(f"{e:.2e}" for e in errs))
+
+
+def test_large_online_256x256_first_pulses_matrix_free_oracle():
+    w = synth.workloads()["c5_256x256_split_bf16"]
+    P, steps = 2, w.inner_steps
+    track = synth.workload_track(w)[:P]
+    c_true = synth.workload_scene(w)
+    x = orc.pixel_positions(w.nx, w.ny, w.pixel_m)
+    f = orc.frequencies(w.n_freq, w.f_lo_hz, w.f_hi_hz)
+    clean = np.stack([orc.phase_matrix(g, x, f) @ c_true for g in track])
+    noise = synth.unit_noise(w.n_pulses, w.n_freq, w.seed)[:P]
+    data = clean + synth.scale_noise(clean, noise, w.snr_db)
+    of = orc.OnlineFista(oracle_config(w, None, lam=w.lambda_rel), matrix_free=True)
+    gpu = osar.Osar(gpu_config(w, "split_bf16", lam=w.lambda_rel))
+    rng = np.random.default_rng(3)
+    errs = []
+    for s in range(P):
+        of.push_pulse(track[s], data[s])
+        gpu.push_pulse(track[s], data[s])
+        assert of.iterate(steps) == steps
+        assert gpu.iterate(steps) == steps
+        errs.append(_compare(of, gpu, rng, f"pulse {s}"))
+    xv = rng.standard_normal(w.m_atoms) + 1j * rng.standard_normal(w.m_atoms)
+    assert_close(gpu.gram_apply(xv), of.s.gram @ xv, TOL_GRAM, "gram apply")
+    gpu.close()
+    print("256x256 M=65536 split-BF16 coefficient errors per pulse:",
           " ".join(f"{e:.2e}" for e in errs))

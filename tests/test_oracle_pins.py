@@ -437,6 +437,38 @@ def test_tolerance_stop_point_is_near_optimal():
     assert bound < 1e-6
 
 
+# ------------------------------------------------- matrix-free Gram form ---
+
+def test_matrix_free_online_fista_equals_the_stored_gram():
+    """The matrix-free mode applies A_n x as sum_k G_k^H R_k^-1 (G_k x) (Eq. 10
+    with Eqs. 12-13): its whole trajectory (L_n, lambda_n, t, c) equals the
+    stored-Gram run up to summation order, white and non-white pulses mixed,
+    and its entries equal the stored Gram's."""
+    w = small_workload(nx=8, ny=6, n_freq=20, n_pulses=6, dictionary="gaussian",
+                       n_atoms=70, seed=13, dict_seed=4)
+    track, dic, c_true, data = build_problem(w)
+    dense = orc.OnlineFista(oracle_config(w, dic))
+    free = orc.OnlineFista(oracle_config(w, dic), matrix_free=True)
+    rng = np.random.default_rng(2)
+    for s in range(w.n_pulses):
+        var = rng.uniform(0.5, 2.0, w.n_freq) if s % 2 else None
+        for of in (dense, free):
+            of.push_pulse(track[s], data[s], var)
+            of.iterate(15)
+        assert free.s.lip == pytest.approx(dense.s.lip, rel=1e-12)
+        assert free.s.lam == pytest.approx(dense.s.lam, rel=1e-13)
+        assert free.s.t == dense.s.t
+        assert np.linalg.norm(free.s.c_hat - dense.s.c_hat) <= \
+            1e-11 * np.linalg.norm(dense.s.c_hat)
+    rows = np.array([0, 5, 69, 33, 12])
+    cols = np.array([69, 5, 0, 7, 40])
+    assert np.allclose(free.s.gram.entries(rows, cols), dense.s.gram[rows, cols],
+                       rtol=0, atol=1e-12 * np.abs(dense.s.gram).max())
+    x = rng.standard_normal(70) + 1j * rng.standard_normal(70)
+    assert np.allclose(free.s.gram @ x, dense.s.gram @ x, rtol=0,
+                       atol=1e-12 * np.abs(dense.s.gram @ x).max())
+
+
 # ------------------------------------------------------- quality (§IV-B) ---
 
 def test_large_coefficient_count_by_hand():
