@@ -201,13 +201,6 @@ typedef struct {
      osar_load, osar_unroll_grad and osar_get_lambda_state return
      OSAR_E_STATE.  Default 0. */
   int32_t pixel_gram;
-  /* 1: each FISTA step after a burst's first is one launch: the Gram pass
-     also runs Algorithm 1's step for every 128-coefficient block as soon as
-     the block's last partial sum is written (a per-block completion counter;
-     the last block also updates t and the stop rule), instead of a pass
-     followed by a separate step launch.  Bitwise the same results as 0.
-     (One lambda, defer_gram = 0; otherwise the two launches.)  Default 1. */
-  int32_t fuse_step;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
@@ -216,7 +209,7 @@ typedef struct {
    overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
    (both tensor-core products on SM pairs), fuse_first_step = 1,
    n_lambdas = 1, defer_gram = 0, guard_bytes = 0, fuse_power_gram = 1,
-   pixel_gram = 0, fuse_step = 1. */
+   pixel_gram = 0. */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context for the problem of Sec. III-C: the online reconstruction

@@ -171,16 +171,6 @@ __device__ __forceinline__ uint64_t l2_policy_evict_last() {
 }
 
 // Barrier among `threads` threads of the CTA (a multiple of 32), id 1..15.
-// atomicAdd with acquire-release semantics at GPU scope: releases what the
-// calling CTA wrote before its last barrier, acquires what other CTAs
-// released through the same counter.
-__device__ __forceinline__ unsigned atomic_add_acq_rel_gpu(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
-               : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-
 __device__ __forceinline__ void named_barrier(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }

@@ -121,8 +121,6 @@ struct osar_ctx {
   void* vt = nullptr;          // v in the matvec's precision (Mp)
   void* xt = nullptr;          // osar_gram_apply input, matvec precision (Mp)
   double2* part = nullptr;     // per-block partial sums (nb)
-  unsigned* blk_cnt = nullptr; // fused FISTA pass: per output block
-                               // completion counters (nb), zero between passes
   double2* d_dev = nullptr;    // staged pulse data (Kp)
   ulonglong2* turns = nullptr; // per-pixel fixed-point phase terms (Np)
   void* g_hi = nullptr;        // packed Gram, float2 or double2 per entry

@@ -44,8 +44,10 @@ namespace {
 // |c - z|_2 <= tol |c|_2 to the whole vector.
 // The complex shrinkage factor is shrink_keep (step.cuh).
 
+// Two CTAs per SM (32 registers a thread): the nb blocks of the 128 x 128
+// workload (256) then run as one wave over the 152 SMs instead of two.
 template <typename T2, typename Acc>
-__global__ void __launch_bounds__(FIN_THREADS)
+__global__ void __launch_bounds__(FIN_THREADS, 2)
     k_fista_finalize(const T2* __restrict__ segpart,
                      const T2* __restrict__ tilepart,
                      const int* __restrict__ seg_begin, int nb,
@@ -478,7 +480,7 @@ void launch_mv(osar_ctx* ctx, MvArgs<T, R> a, int gated) {
   const unsigned grid = (unsigned)(ctx->nseg < slots ? ctx->nseg : slots);
   k_matvec<T, R, false><<<grid, C::THREADS, C::SMEM, ctx->stream>>>(
       (const typename Vec<T>::T2*)ctx->g_hi, a, ctx->segs, ctx->nseg, ctx->nb,
-      ctx->scal, gated, matvec_queue(ctx->scal), MvBatch{}, MvFin<T>{});
+      ctx->scal, gated, matvec_queue(ctx->scal), MvBatch{});
 }
 
 // Device address of solution l's stop flag (pointer arithmetic only).
@@ -486,37 +488,6 @@ const int32_t* stop_flag(const osar_ctx* ctx, int l) {
   return reinterpret_cast<const int32_t*>(
       reinterpret_cast<const char*>(ctx->scal + l) +
       offsetof(DevScalars, converged));
-}
-
-// One FISTA step in one launch: the gated pass over z with Algorithm 1's
-// step fused (k_matvec<T, 1, false, true>); bitwise the pass + finalize.
-template <typename T>
-void launch_fista_fused(osar_ctx* ctx) {
-  using C = Mv<T, 1>;
-  using T2 = typename Vec<T>::T2;
-  MvArgs<T, 1> a;
-  a.x[0] = (const T2*)ctx->zt;
-  a.segpart[0] = (T2*)ctx->segpart;
-  a.tilepart[0] = (T2*)ctx->tilepart;
-  a.gate[0] = stop_flag(ctx, 0);
-  a.keep_l2 = ctx->nblk * BLK * BLK * (int64_t)sizeof(T2) <= KEEP_L2_BYTES;
-  MvFin<T> f;
-  f.seg_begin = ctx->seg_begin;
-  f.cnt = ctx->blk_cnt;
-  f.b = ctx->b;
-  f.c = ctx->c;
-  f.z = ctx->z;
-  f.zt = (T2*)ctx->zt;
-  f.part = ctx->part;
-  f.sc = ctx->scal;
-  f.count_pass = 1;
-  cudaFuncSetAttribute(k_matvec<T, 1, false, true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-  const int slots = C::CTAS * ctx->sm_count;
-  const unsigned grid = (unsigned)(ctx->nseg < slots ? ctx->nseg : slots);
-  k_matvec<T, 1, false, true><<<grid, C::THREADS, C::SMEM, ctx->stream>>>(
-      (const T2*)ctx->g_hi, a, ctx->segs, ctx->nseg, ctx->nb, ctx->scal, 1,
-      matvec_queue(ctx->scal), MvBatch{}, f);
 }
 
 // Partial-sum buffers for vector slot l of a pass: 0 the main ones, 1 the
@@ -788,18 +759,6 @@ cudaError_t launch_fista_step(osar_ctx* ctx) {
   // power step (already counted as a Gram pass)
   const bool pre = ctx->first_ready;
   ctx->first_ready = false;
-  if (!pre && ctx->cfg.fuse_step && !ctx->cfg.defer_gram) {
-    // the pass and the step in one launch
-    ProfEvent ev;
-    prof_begin(ctx, KCL_MATVEC, &ev);
-    if (fp64)
-      launch_fista_fused<double>(ctx);
-    else
-      launch_fista_fused<float>(ctx);
-    prof_end(ctx, &ev);
-    ctx->launches++;
-    return cudaGetLastError();
-  }
   if (!pre) matvec(ctx, ctx->zt, 1);
   ProfEvent ev;
   prof_begin(ctx, KCL_FIN, &ev);

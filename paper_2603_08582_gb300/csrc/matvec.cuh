@@ -25,7 +25,6 @@
 #pragma once
 
 #include "batch.h"
-#include "step.cuh"
 
 namespace osar {
 namespace {
@@ -111,15 +110,14 @@ struct Mv {
   static constexpr int CTAS = sizeof(T) == 4 && R == 1 ? 2 : 1;  // per SM
   static constexpr int RB = CTAS == 2 ? 1 : 2;  // block-partial buffers
   static constexpr int RED_BYTES = RB * R * CW * BLK * (int)sizeof(T2);
-  static constexpr int FIN_BYTES = 256;  // fused step: flags, scalars, warp sums
-  static constexpr int FIXED = RED_BYTES + 16 + FIN_BYTES;
+  static constexpr int FIXED = RED_BYTES + 16;
   static constexpr int PER_STAGE = STAGE + 2 * 8 + 16;         // + barriers, meta
   // shared memory of one CTA: 228 KB per SM, 1 KB of it reserved per CTA
   static constexpr int BUDGET = CTAS == 2 ? 228 * 1024 / 2 - 1024 : 227 * 1024;
   static constexpr int NST = (BUDGET - FIXED) / PER_STAGE > 6
                                  ? 6 : (BUDGET - FIXED) / PER_STAGE;  // ring depth
   static constexpr int SMEM = NST * STAGE + RED_BYTES + 2 * NST * 8 +
-                              NST * 16 + 16 + FIN_BYTES;
+                              NST * 16 + 16;
   static constexpr int THREADS = 32 * (CW + 1);  // producer warp + consumers
 };
 static_assert(Mv<float, 1>::NST >= 3 && Mv<float, 2>::NST >= 4 &&
@@ -151,162 +149,6 @@ struct MvBatch {
   int pstep;  // power step of the pass, or -1 for a FISTA pass
 };
 
-// The fused Algorithm-1 step of a FISTA pass (FIN): each output block K
-// has a completion counter; the CTA whose contribution completes K (the
-// segment partials of block column K and the block partials of row K) runs
-// K's step while the other CTAs keep streaming, and the CTA that finishes
-// the last output block updates the scalars.  Nothing waits on another CTA.
-template <typename T>
-struct MvFin {
-  const int* seg_begin;       // segment slots of block column J (nb + 1)
-  unsigned* cnt;              // nb completion counters, zero between passes
-  const double2* b;           // b_n
-  double2* c;                 // c^(k-1) in, c^(k) out
-  double2* z;                 // z^(k) in, z^(k+1) out
-  typename Vec<T>::T2* zt;    // z^(k+1) in the matvec's precision (the pass's x)
-  double2* part;              // per-block (|c - z|^2, |c|^2)
-  DevScalars* sc;
-  int count_pass;
-};
-
-// Shared scratch of the fused step (Mv::FIN_BYTES).
-struct FinShared {
-  int job[2];        // output blocks this CTA finalizes after the current block
-  int is_last;       // this CTA finalized the pass's last output block
-  int pad;
-  double sh[3];      // tau, alpha = lambda tau, beta = (t - 1) / t'
-  double2 wsum[8];   // per consumer warp (|c - z|^2, |c|^2)
-};
-
-constexpr int FIN_GROUPS = 8;                  // partial-list splits per block
-constexpr int FIN_THREADS = FIN_GROUPS * BLK;  // 1024
-
-// Sum (a, b) over the 32 * nw consumer threads (ct = 0 .. ); ct == 0 gets the
-// total: a butterfly per warp, then the warp sums in warp order.  The same
-// arithmetic as block_sum whenever only the first warps hold non-zeros.
-__device__ __forceinline__ double2 group_sum(double a, double b, int ct, int nw,
-                                             double2* wsum) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  if ((ct & 31) == 0) wsum[ct >> 5] = make_double2(a, b);
-  named_barrier(1, 32 * nw);
-  double2 t = make_double2(0, 0);
-  if (ct == 0)
-    for (int w = 0; w < nw; ++w) {
-      t.x += wsum[w].x;
-      t.y += wsum[w].y;
-    }
-  return t;
-}
-
-// Algorithm 1's step for output block K, run by the nw consumer warps of the
-// CTA that completed K (ct: consumer thread).  Gather and step take exactly
-// the arithmetic of gather_row and k_fista_finalize (FIN_GROUPS strided
-// group sums combined in group order, the FP64 step, the warp-ordered
-// partials), so the fused pass is bitwise the two-launch one.  Partials come
-// from other CTAs through L2 (ld.global.cg after the acquiring counter).
-template <typename T, int NW>
-__device__ __forceinline__ void fin_block(const MvFin<T>& f,
-                                          const typename Vec<T>::T2* __restrict__ segpart,
-                                          const typename Vec<T>::T2* __restrict__ tilepart,
-                                          int nb, int K, int ct, T* red,
-                                          FinShared* fs) {
-  using T2 = typename Vec<T>::T2;
-  static_assert(NW * 32 == 2 * BLK, "the fused step takes 256 consumer threads");
-  volatile DevScalars* vsc = f.sc;
-  if (ct == 0) {
-    const double t = vsc->t, tau = vsc->tau;
-    const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    fs->sh[0] = tau;
-    fs->sh[1] = vsc->lambda * tau;
-    fs->sh[2] = (t - 1.0) / t_next;
-  }
-  T* red_r = red;                        // [FIN_GROUPS][BLK]
-  T* red_i = red + FIN_GROUPS * BLK;
-  const int i = ct % BLK, h = ct / BLK;  // groups h, h + 2, h + 4, h + 6
-  const int s0 = f.seg_begin[K], nseg = f.seg_begin[K + 1] - s0;
-  const int total = nseg + (nb - 1 - K);
-  const int64_t t0 = packed_block(K, K, nb) + 1;  // block (K, K+1)
-  T yr[4] = {0, 0, 0, 0}, yi[4] = {0, 0, 0, 0};
-#pragma unroll 2
-  for (int q0 = 0; q0 < total; q0 += FIN_GROUPS) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int q = q0 + h + 2 * j;
-      if (q < total) {
-        const T2 v = q < nseg ? __ldcg(segpart + (int64_t)(s0 + q) * BLK + i)
-                              : __ldcg(tilepart + (t0 + (q - nseg)) * BLK + i);
-        yr[j] += v.x;
-        yi[j] += v.y;
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    red_r[(h + 2 * j) * BLK + i] = yr[j];
-    red_i[(h + 2 * j) * BLK + i] = yi[j];
-  }
-  named_barrier(1, 32 * NW);
-  double p0 = 0.0, p1 = 0.0;
-  if (ct < BLK) {
-    T sr = 0, si = 0;
-#pragma unroll
-    for (int k = 0; k < FIN_GROUPS; ++k) {
-      sr += red_r[k * BLK + i];
-      si += red_i[k * BLK + i];
-    }
-    const double tau = fs->sh[0], alpha = fs->sh[1], beta = fs->sh[2];
-    const int idx = K * BLK + i;
-    const double2 zk = f.z[idx], bk = f.b[idx], cprev = f.c[idx];
-    const double ur = zk.x - tau * ((double)sr - bk.x);
-    const double ui = zk.y - tau * ((double)si - bk.y);
-    const double keep = shrink_keep<T2>(ur * ur + ui * ui, alpha);
-    const double cr = ur * keep, ci = ui * keep;
-    const double2 zn = make_double2(cr + beta * (cr - cprev.x),
-                                    ci + beta * (ci - cprev.y));
-    f.c[idx] = make_double2(cr, ci);
-    f.z[idx] = zn;
-    T2 znt;
-    znt.x = zn.x;
-    znt.y = zn.y;
-    f.zt[idx] = znt;
-    const double dr = cr - zk.x, di = ci - zk.y;
-    p0 = dr * dr + di * di;
-    p1 = cr * cr + ci * ci;
-  }
-  const double2 s = group_sum(p0, p1, ct, NW, fs->wsum);
-  if (ct == 0) {
-    f.part[K] = s;
-    f.cnt[K] = 0;  // no other contribution to K comes in this pass
-    fs->is_last = atomic_add_acq_rel_gpu(&f.sc->done, 1u) == (unsigned)nb - 1;
-  }
-  named_barrier(1, 32 * NW);
-  if (fs->is_last) {
-    // every output block has stepped: the scalars (as k_fista_finalize's
-    // last block, with the partials summed in the canonical order)
-    double a = 0.0, b = 0.0;
-    if (ct < BLK)
-      for (int k = ct; k < nb; k += BLK) {
-        const double2 v = __ldcg(f.part + k);
-        a += v.x;
-        b += v.y;
-      }
-    const double2 tot = group_sum(a, b, ct, NW, fs->wsum);
-    if (ct == 0) {
-      const double t = vsc->t;
-      vsc->t = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-      vsc->iters += 1;
-      vsc->passes += f.count_pass;
-      if (vsc->tol > 0.0 && sqrt(tot.x) <= vsc->tol * sqrt(tot.y)) vsc->converged = 1;
-      vsc->done = 0;
-    }
-  }
-  named_barrier(1, 32 * NW);  // red and fs free for the next block
-}
-
 constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
 
 // One Gram pass.  Each thread accumulates y_J over NACC of the block's stored
@@ -318,20 +160,14 @@ constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
 // kernel spreads over whatever SMs are free, e.g. beside the next pulse's
 // dictionary product.  Every wait is bounded; on a timeout the CTA records
 // the error, stops at the next per-block barrier and drains its copies.
-//
-// FIN (one vector, single context): the pass also runs Algorithm 1's step
-// (fin_block) for each output block as soon as its last contribution is
-// written, so a FISTA step is one launch.
-template <typename T, int R, bool BATCH, bool FIN = false>
+template <typename T, int R, bool BATCH>
 __global__ void __launch_bounds__(Mv<T, R>::THREADS, Mv<T, R>::CTAS)
     k_matvec(const typename Vec<T>::T2* __restrict__ G, const MvArgs<T, R> a,
              const int4* __restrict__ segs, int nseg, int nb,
              DevScalars* __restrict__ sc, int gated,
-             unsigned* __restrict__ queue, const MvBatch mb,
-             const MvFin<T> fin) {
+             unsigned* __restrict__ queue, const MvBatch mb) {
   using C = Mv<T, R>;
   using T2 = typename Vec<T>::T2;
-  static_assert(!FIN || (R == 1 && !BATCH), "the fused step is one-vector only");
   if (!BATCH && gated) {
     bool all = true;
 #pragma unroll
@@ -343,12 +179,9 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, Mv<T, R>::CTAS)
   uint64_t* full = reinterpret_cast<uint64_t*>(mv_smem + C::NST * C::STAGE +
                                                C::RED_BYTES);
   uint64_t* empty = full + C::NST;
-  // per stage: (packed block of the Gram, block column J, segment slot,
-  // flags | block row I << 2)
+  // per stage: (packed block of the Gram, diagonal?, segment slot, flags)
   int4* meta = reinterpret_cast<int4*>(empty + C::NST);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(meta + C::NST);
-  FinShared* fs = reinterpret_cast<FinShared*>(mv_smem + C::SMEM - C::FIN_BYTES);
-  static_assert(sizeof(FinShared) <= C::FIN_BYTES, "fused-step scratch");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int i = 0; i < C::NST; ++i) {
@@ -399,9 +232,8 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, Mv<T, R>::CTAS)
             break;
           }
           if (k == 0)
-            meta[stage] = make_int4((int)pb, sg.x, sg.w,
-                                    (I == sg.y ? 1 : 0) | (I == sg.z - 1 ? 2 : 0) |
-                                        (I << 2));
+            meta[stage] = make_int4((int)pb, I == sg.x ? 1 : 0, sg.w,
+                                    (I == sg.y ? 1 : 0) | (I == sg.z - 1 ? 2 : 0));
           uint8_t* st = mv_smem + stage * C::STAGE;
           mbar_expect_tx(&full[stage], C::STAGE);
           bulk_load_hint(st, blk + (int64_t)k * C::CC * BLK, C::G_BYTES,
@@ -463,8 +295,8 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, Mv<T, R>::CTAS)
                                                 &sc->error, MV_WAIT_LIMIT_NS);
     const int4 m = ok ? meta[stage] : make_int4(-1, 0, 0, 0);
     const bool work = ok && m.x >= 0;
-    const bool diag = work && (m.w >> 2) == m.y;
     if (work) {
+      const bool diag = m.y != 0;
       if (m.w & 1) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -594,7 +426,7 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, Mv<T, R>::CTAS)
     // decision is the barrier's OR over all consumer threads).
     if (named_barrier_or(1, 32 * C::CW, !work || *abort_flag)) break;
     const int rr = (int)threadIdx.x - 32;
-    if (!diag && rr < R * BLK) {
+    if (!m.y && rr < R * BLK) {
       const int r = rr / BLK, row = rr % BLK;
       T sr = 0, si = 0;
 #pragma unroll
@@ -607,41 +439,15 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, Mv<T, R>::CTAS)
       v.y = si;
       a.tilepart[r][(int64_t)m.x * BLK + row] = v;
     }
-    if constexpr (FIN) {
-      // This block's partials are written (the segment partial before the
-      // barrier above, the block partial just now); one thread releases
-      // them to the counters of output blocks I (block partial, off the
-      // diagonal) and J (segment partial, at a segment's end) and learns
-      // whether they completed an output block, which the CTA then steps.
-      named_barrier(1, 32 * C::CW);
-      if (rr == 0) {
-        int j0 = -1, j1 = -1;
-        const int I = m.w >> 2, J = m.y;
-        auto expected = [&](int K) {
-          return (unsigned)(fin.seg_begin[K + 1] - fin.seg_begin[K] + nb - 1 - K);
-        };
-        if (!diag && atomic_add_acq_rel_gpu(&fin.cnt[I], 1u) + 1 == expected(I)) j0 = I;
-        if ((m.w & 2) && atomic_add_acq_rel_gpu(&fin.cnt[J], 1u) + 1 == expected(J)) j1 = J;
-        fs->job[0] = j0;
-        fs->job[1] = j1;
-      }
-      named_barrier(1, 32 * C::CW);
-      const int j0 = fs->job[0], j1 = fs->job[1];
-      if (j0 >= 0)
-        fin_block<T, C::CW>(fin, a.segpart[0], a.tilepart[0], nb, j0, rr,
-                            reinterpret_cast<T*>(red), fs);
-      if (j1 >= 0)
-        fin_block<T, C::CW>(fin, a.segpart[0], a.tilepart[0], nb, j1, rr,
-                            reinterpret_cast<T*>(red), fs);
-      if (C::RB == 2) rp ^= 1;
-    } else {
-      if (C::RB == 2)
-        rp ^= 1;
-      else
-        named_barrier(1, 32 * C::CW);  // one buffer: read before the next block's writes
-    }
+    if (C::RB == 2)
+      rp ^= 1;
+    else
+      named_barrier(1, 32 * C::CW);  // one buffer: read before the next block's writes
   }
 }
+
+constexpr int FIN_GROUPS = 8;                  // partial-list splits per block
+constexpr int FIN_THREADS = FIN_GROUPS * BLK;  // 1024
 
 // y_K = sum of the segment partials of block column K and the block partials
 // of (K, J), J > K, accumulated in Acc (FP32 on the FP32-Gram paths).  The
@@ -725,12 +531,10 @@ __device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblocks) 
   return is_last != 0;
 }
 
-// Sum of the per-block (x, y) partials in a fixed order, by one block of at
-// least BLK threads: thread i < BLK sums k = i, i + BLK, ..., then block_sum;
-// the order does not depend on the block size.
+// Sum of the per-block (x, y) partials in a fixed order, by one block.
 __device__ __forceinline__ double2 sum_parts(const double2* part, int n) {
   double a = 0.0, b = 0.0;
-  for (int k = threadIdx.x; threadIdx.x < BLK && k < n; k += BLK) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const double2 v = __ldcg(part + k);
     a += v.x;
     b += v.y;

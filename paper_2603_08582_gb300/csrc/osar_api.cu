@@ -69,7 +69,7 @@ void free_all(osar_ctx* ctx) {
                   ctx->segpart_x, ctx->tilepart_x, ctx->gn_hi, ctx->gn_lo,
                   ctx->Apl_alt, ctx->corr, ctx->corr_u, ctx->corr_tick,
                   ctx->atom_ptr, ctx->atom_pix, ctx->wk_dev, ctx->gp_col,
-                  ctx->gp_row, ctx->metrics_buf, ctx->blk_cnt};
+                  ctx->gp_row, ctx->metrics_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->pg) {
@@ -170,8 +170,6 @@ osar_status validate(const osar_config* c, std::string* why) {
     return *why = "fuse_first_step must be 0 or 1", OSAR_E_INVALID;
   if (c->fuse_power_gram != 0 && c->fuse_power_gram != 1)
     return *why = "fuse_power_gram must be 0 or 1", OSAR_E_INVALID;
-  if (c->fuse_step != 0 && c->fuse_step != 1)
-    return *why = "fuse_step must be 0 or 1", OSAR_E_INVALID;
   if (c->pixel_gram != 0 && c->pixel_gram != 1)
     return *why = "pixel_gram must be 0 or 1", OSAR_E_INVALID;
   if (c->pixel_gram &&
@@ -217,11 +215,10 @@ void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
     }
   }
   seg_begin[nb] = (int)segs.size();
-  // Hand the segments out from the last block column down: output block K
-  // takes contributions from block columns J >= K only, so the outputs
-  // complete one after another during a pass (the FISTA pass steps each as
-  // soon as it completes), and the longest columns go first.  The partial
-  // slots (.w) keep the column order that seg_begin indexes.
+  // Hand the segments out from the last block column down: the longest
+  // columns go first and the one-block columns last, which evens out the
+  // pass's tail.  The partial slots (.w) keep the column order that
+  // seg_begin indexes.
   std::reverse(segs.begin(), segs.end());
   // Gram tiles: upper blocks grouped in SB x SB super-blocks so that the
   // CTAs running at the same time share operand rows in L2.
@@ -380,7 +377,6 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
   AL(ctx->w, 16 * Mp);
   AL(ctx->xtmp, 16 * Mp);
   AL(ctx->part, 16 * (int64_t)ctx->nb);
-  AL(ctx->blk_cnt, 4 * (int64_t)ctx->nb);
   AL(ctx->d_dev, 16 * Kp);
   AL(ctx->turns, 16 * Np);
   AL(ctx->g_hi, cplx * bb * ctx->nblk);
@@ -945,7 +941,6 @@ void osar_config_default(osar_config* c) {
   c->guard_bytes = 0;
   c->fuse_power_gram = 1;
   c->pixel_gram = 0;
-  c->fuse_step = 1;
 }
 
 namespace {

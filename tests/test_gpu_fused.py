@@ -9,7 +9,7 @@ import os
 import numpy as np
 import pytest
 
-from paper_2603_08582_gb300 import osar, synth
+from paper_2603_08582_gb300 import osar
 from tests.helpers import small_workload, build_problem
 from tests.gpu_helpers import gpu_config
 
@@ -64,55 +64,3 @@ def test_fused_first_step_across_a_checkpoint(tmp_path):
         x.iterate(10)
     _same(ref, g)
     _same(ref, h)
-
-
-# --------------------------------------------------------------------------
-# One-launch FISTA step (fuse_step): the pass runs Algorithm 1's step for
-# each output block as soon as the block's partials are complete; bitwise
-# the pass followed by the separate step launch.
-
-def _ctx_step(w, prec, fused, first=True):
-    cfg = gpu_config(w, prec)
-    cfg.fuse_step = 1 if fused else 0
-    cfg.fuse_first_step = 1 if first else 0
-    return osar.Osar(cfg)
-
-
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32", "fp64"])
-@pytest.mark.parametrize("first", [True, False])
-def test_one_launch_step_is_bitwise_neutral(prec, first):
-    # 20 x 18 pixels: M = 360, 3 output blocks, the last one ragged
-    w = small_workload(nx=20, ny=18, n_freq=64, n_pulses=6, sparsity=0.05, seed=43)
-    track, _, _, data = build_problem(w)
-    a, b = _ctx_step(w, prec, False, first), _ctx_step(w, prec, True, first)
-    for s in range(len(track)):
-        counts = []
-        for g in (a, b):
-            g.push_pulse(track[s], data[s])
-            counts.append(g.iterate(9, 1e-5 if s >= 3 else 0.0))
-        assert counts[0] == counts[1]
-        _same(a, b)
-    assert np.array_equal(a.b(), b.b())
-
-
-def test_one_launch_step_many_blocks_and_segments():
-    """64 x 64 pixels with 8192 Gaussian atoms: 64 output blocks, thousands
-    of segments handed out by ticket, so output blocks complete on many CTAs
-    at different times during the pass."""
-    w = small_workload(nx=64, ny=64, n_freq=256, n_pulses=3, dictionary="gaussian",
-                       n_atoms=8192, sparsity=0.03, seed=44, dict_seed=2)
-    a, b = _ctx_step(w, "split_bf16", False), _ctx_step(w, "split_bf16", True)
-    track = synth.workload_track(w)
-    rng = np.random.default_rng(5)
-    for s in range(w.n_pulses):
-        d = rng.standard_normal(w.n_freq) + 1j * rng.standard_normal(w.n_freq)
-        for g in (a, b):
-            g.push_pulse(track[s], d)
-            g.iterate(12)
-        _same(a, b)
-    # iterate splitting stays exact with the one-launch step
-    for g in (a, b):
-        g.push_pulse(track[0], d)
-        g.iterate(5)
-        g.iterate(7)
-    _same(a, b)
