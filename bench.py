@@ -488,6 +488,7 @@ def run_ours(args):
     if accuracy is not None:
         line["accuracy_vs_fp64_oracle"] = accuracy
     if rank == 0 and args.workload == "c2" and not args.no_large:
+        line["pixel_space_gram_128x128"] = run_pixel_space_dense(stream, w)
         line["large_online_256x256"] = run_large_online(stream)
     if args.forms and rank == 0:
         line["forms"] = run_forms(stream)
@@ -495,6 +496,74 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_pixel_space_dense(stream, w, warmup=4, pulses=16):
+    """The 128 x 128 / M = 32768 Gaussian workload in the pixel-space Gram
+    form (P_n, N x N; G_n applied as D^H P_n D): early pulses, every burst
+    its 20 steps, against the stored-Gram form on the same pulses."""
+    import torch
+    from paper_2603_08582_gb300 import osar
+    peaks, src = measured_peaks()
+    out = {"workload": w.name + " (pixel-space Gram form)", "pulses_timed": pulses,
+           "pulses_warmup": warmup, "inner_steps": INNER_STEPS}
+    track = data = None
+    for pixel in (False, True):
+        cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
+                               pixel_m=w.pixel_m, precision="split_bf16",
+                               dictionary="gaussian", n_atoms=w.m_atoms,
+                               dict_seed=w.dict_seed, lam=w.lambda_rel,
+                               stream=stream.cuda_stream, pixel_gram=pixel)
+        ctx = osar.Osar(cfg)
+        if track is None:
+            track, data = pulse_data(ctx, w, warmup + pulses)
+        for s in range(warmup):
+            ctx.push_pulse(track[s], data[s])
+            ctx.iterate(INNER_STEPS, 0.0, want_count=False)
+        ctx.synchronize()
+        ctx.profile_reset()
+        ctx.profile_enable(True)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for s in range(warmup, warmup + pulses):
+            ctx.push_pulse(track[s], data[s])
+            ctx.iterate(INNER_STEPS, 0.0, want_count=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / pulses
+        prof = {k: ctx.profile_read(k) for k in ("matvec", "dict_apply", "fista_finalize",
+                                                  "gram_gemm")}
+        ctx.profile_enable(False)
+        res = {"ms_per_pulse": round(ms, 2), "pulses_per_s": round(1e3 / ms, 2),
+               "device_gb": round(ctx.device_bytes() / 1e9, 2)}
+        if pixel:
+            nbp = (w.n_pixels + 127) // 128
+            p_bytes = nbp * (nbp + 1) // 2 * 128 * 128 * 8
+            d_bytes = 4 * 2 * ((w.m_atoms + 127) // 128 * 128) * ((w.n_pixels + 127) // 128 * 128)
+            mv_n, mv_ms = prof["matvec"]
+            da_n, da_ms = prof["dict_apply"]
+            fi_n, fi_ms = prof["fista_finalize"]
+            mv_a, da_a, fi_a = mv_ms / max(mv_n, 1), da_ms / max(da_n, 1), fi_ms / max(fi_n, 1)
+            res["per_step_kernels"] = {
+                "u = D x": {"avg_ms": round(da_a, 4), "bytes": d_bytes,
+                            "gbs": round(d_bytes / da_a / 1e6, 1),
+                            "frac_of_hbm": round(d_bytes / da_a / 1e6 / peaks["hbm_gbs"], 3)},
+                "w = P_n u (packed P_n pass)": {"avg_ms": round(mv_a, 4), "bytes": p_bytes,
+                                               "gbs": round(p_bytes / mv_a / 1e6, 1),
+                                               "frac_of_hbm": round(p_bytes / mv_a / 1e6
+                                                                    / peaks["hbm_gbs"], 3)},
+                "D^H w + step": {"avg_ms": round(fi_a, 4), "bytes": d_bytes,
+                                 "gbs": round(d_bytes / fi_a / 1e6, 1),
+                                 "frac_of_hbm": round(d_bytes / fi_a / 1e6 / peaks["hbm_gbs"], 3)}}
+            res["gram_update_ms"] = round(prof["gram_gemm"][1] / max(prof["gram_gemm"][0], 1), 3)
+            out["pixel_space_form"] = res
+        else:
+            out["stored_gram_form"] = res
+        ctx.close()
+    out["peak_source"] = src
+    return out
 
 
 def run_large_online(stream, warmup=4, pulses=24, tune_every=8):

@@ -60,7 +60,7 @@ inline unsigned* matvec_queue(DevScalars* s) {
 
 enum KernelClass {
   KCL_PHASE = 0, KCL_DICT = 1, KCL_GRAM = 2, KCL_BUPD = 3, KCL_MATVEC = 4,
-  KCL_FIN = 5, KCL_POWFIN = 6, KCL_CORR = 7, KCL_COUNT = 8
+  KCL_FIN = 5, KCL_POWFIN = 6, KCL_CORR = 7, KCL_DAPPLY = 8, KCL_COUNT = 9
 };
 
 struct ProfEvent {
@@ -74,6 +74,9 @@ struct ProfEvent {
 // coefficient side: G_n = H^H P_n H and b_n = H^H b_pix are applied, never
 // stored.
 struct PixGram {
+  bool dense = false;         // a dense dictionary D (Gaussian or host) in
+                              // the context's D / Dpl, not edgelet lists
+  void* upart = nullptr;      // dense: partial sums of u = D x (chunks x Np)
   int M = 0;                  // atoms
   int Mp = 0;                 // atoms padded to BLK
   int nb = 0;                 // Mp / BLK
@@ -263,6 +266,14 @@ cudaError_t pg_after_push(osar_ctx* ctx);
 cudaError_t prepare_pixgram_kernels();  // shared-memory carve-out, as the burst's
 cudaError_t pg_burst_begin(osar_ctx* ctx);
 cudaError_t pg_fista_step(osar_ctx* ctx);
+
+// ---- k_pixgram_dense.cu -----------------------------------------------------
+// the pixel-space form with a dense dictionary: u = D x into the pass's input
+// vector (zt), and (D^H w)_m with b_n / lambda_n (mode 0), a power step
+// (mode 1) or Algorithm 1's step (mode 2)
+int pgd_chunks(const osar_ctx* ctx);
+cudaError_t pgd_forward(osar_ctx* ctx, const double2* x, int gated);
+cudaError_t pgd_adjoint(osar_ctx* ctx, int mode, int last_step);
 
 // ---- k_defer.cu -------------------------------------------------------------
 // corr[set] = A_n^H (A_n x) for the pending forward block (nothing when no

@@ -419,7 +419,11 @@ cudaError_t launch_phase(osar_ctx* ctx, int grid_cap) {
 }
 
 cudaError_t launch_dictionary_build(osar_ctx* ctx, const double* host_dict) {
-  const int N = ctx->N, M = ctx->M, Mp = ctx->Mp, Np = ctx->Np;
+  // the atoms: the context's own, or the coefficient side of a pixel-space
+  // Gram form with a dense dictionary
+  const int N = ctx->N, Np = ctx->Np;
+  const int M = ctx->pg ? ctx->pg->M : ctx->M;
+  const int Mp = ctx->pg ? ctx->pg->Mp : ctx->Mp;
   cudaError_t e;
   double* inv_norm = nullptr;
   double2* host_copy = nullptr;
@@ -461,18 +465,19 @@ cudaError_t launch_dictionary_build(osar_ctx* ctx, const double* host_dict) {
 
 cudaError_t launch_simulate(osar_ctx* ctx, int nnz, double2* d_out) {
   const int Np = ctx->Np;
-  if (ctx->edgelet || ctx->pg) {
+  const int Mpd = ctx->pg ? ctx->pg->Mp : ctx->Mp;  // atoms of the dictionary rows
+  if (ctx->edgelet || (ctx->pg && !ctx->pg->dense)) {
     // the image H c (the pixel-space Gram form keeps H's lists too)
     cudaError_t e = launch_sim_rho_edgelet(ctx, nnz);
     if (e != cudaSuccess) return e;
-  } else if (!ctx->dict) {
+  } else if (!ctx->dict && !ctx->pg) {
     cudaMemsetAsync(ctx->sim_rho, 0, sizeof(double2) * Np, ctx->stream);
     if (nnz > 0)
       k_sim_scatter<<<blocks_for(nnz, 256), 256, 0, ctx->stream>>>(
           nnz, ctx->sim_idx, ctx->sim_nz, ctx->sim_rho);
   } else if (ctx->prec == OSAR_SPLIT_BF16) {
     k_sim_rho_planes<<<blocks_for(Np, 256), 256, 0, ctx->stream>>>(
-        ctx->Dpl, ctx->Mp, Np, nnz, ctx->sim_idx, ctx->sim_nz, ctx->sim_rho);
+        ctx->Dpl, Mpd, Np, nnz, ctx->sim_idx, ctx->sim_nz, ctx->sim_rho);
   } else if (ctx->prec == OSAR_FP64) {
     k_sim_rho_complex<double2><<<blocks_for(Np, 256), 256, 0, ctx->stream>>>(
         (const double2*)ctx->D, Np, nnz, ctx->sim_idx, ctx->sim_nz,

@@ -1,5 +1,6 @@
 // Pixel-space Gram form of Online FISTA for a binary edgelet dictionary H
-// (config pixel_gram).
+// (config pixel_gram; the dense dictionaries' products are in
+// k_pixgram_dense.cu).
 //
 // Eqs. 12-13 accumulate G_n = sum_s A_s^H A_s and b_n = sum_s A_s^H d_s with
 // A_s = F_s H (Eq. 6), so G_n = H^H P_n H and b_n = H^H b_pix with
@@ -210,9 +211,11 @@ __global__ void k_pg_burst_begin(double2* __restrict__ z,
 
 unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// u = H x into the matvec's input (the context's pixel working vector).
+// u = H x into the matvec's input (the context's pixel working vector);
+// u = D x for a dense dictionary.
 cudaError_t scatter(osar_ctx* ctx, const double2* x, int gated) {
   const PixGram& g = *ctx->pg;
+  if (g.dense) return pgd_forward(ctx, x, gated);
   if (ctx->prec == OSAR_FP64)
     k_pg_scatter<double2><<<blocks(ctx->Np, PG_THREADS), PG_THREADS, 0, ctx->stream>>>(
         x, g.pix_ptr, g.pix_atom, ctx->N, ctx->Np, (double2*)ctx->zt, ctx->scal,
@@ -250,10 +253,15 @@ cudaError_t prepare_pixgram_kernels() {
 
 cudaError_t pg_after_push(osar_ctx* ctx) {
   const PixGram& g = *ctx->pg;
-  k_pg_bvec<<<blocks(g.M, PG_THREADS), PG_THREADS, 0, ctx->stream>>>(
-      ctx->b, ctx->atom_ptr, ctx->atom_pix, g.M, g.b, g.bmax, ctx->scal,
-      ctx->lam.v[0], ctx->cfg.lambda_relative);
-  ctx->launches++;
+  if (g.dense) {
+    cudaError_t e = pgd_adjoint(ctx, 0, 0);  // b_n = D^H b_pix, lambda_n
+    if (e != cudaSuccess) return e;
+  } else {
+    k_pg_bvec<<<blocks(g.M, PG_THREADS), PG_THREADS, 0, ctx->stream>>>(
+        ctx->b, ctx->atom_ptr, ctx->atom_pix, g.M, g.b, g.bmax, ctx->scal,
+        ctx->lam.v[0], ctx->cfg.lambda_relative);
+    ctx->launches++;
+  }
   const int steps = ctx->n == 1 ? ctx->cfg.power_iters_first : ctx->cfg.power_iters;
   for (int s = 0; s < steps; ++s) {
     cudaError_t e = scatter(ctx, g.v, 0);
@@ -261,9 +269,14 @@ cudaError_t pg_after_push(osar_ctx* ctx) {
     if (e != cudaSuccess) return e;
     ProfEvent ev;
     prof_begin(ctx, KCL_POWFIN, &ev);
-    k_pg_power_finalize<<<(unsigned)g.nb, BLK, 0, ctx->stream>>>(
-        ctx->w, ctx->atom_ptr, ctx->atom_pix, g.M, g.v, g.w, g.part, ctx->scal,
-        s == steps - 1 ? 1 : 0, ctx->cfg.lipschitz_margin);
+    if (g.dense) {
+      e = pgd_adjoint(ctx, 1, s == steps - 1 ? 1 : 0);
+      ctx->launches--;  // counted below with the normalisation
+    } else {
+      k_pg_power_finalize<<<(unsigned)g.nb, BLK, 0, ctx->stream>>>(
+          ctx->w, ctx->atom_ptr, ctx->atom_pix, g.M, g.v, g.w, g.part, ctx->scal,
+          s == steps - 1 ? 1 : 0, ctx->cfg.lipschitz_margin);
+    }
     k_pg_normalize<<<blocks(g.Mp, PG_THREADS), PG_THREADS, 0, ctx->stream>>>(
         g.w, g.v, g.Mp, ctx->scal);
     prof_end(ctx, &ev);
@@ -288,6 +301,11 @@ cudaError_t pg_fista_step(osar_ctx* ctx) {
   if (e != cudaSuccess) return e;
   ProfEvent ev;
   prof_begin(ctx, KCL_FIN, &ev);
+  if (g.dense) {
+    e = pgd_adjoint(ctx, 2, 0);
+    prof_end(ctx, &ev);
+    return e;
+  }
   if (ctx->prec == OSAR_FP64)
     k_pg_fista_finalize<double2><<<(unsigned)g.nb, BLK, 0, ctx->stream>>>(
         ctx->w, ctx->atom_ptr, ctx->atom_pix, g.M, g.b, g.c, g.z, g.part,

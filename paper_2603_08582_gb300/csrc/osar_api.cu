@@ -76,7 +76,7 @@ void free_all(osar_ctx* ctx) {
     const PixGram& g = *ctx->pg;
     for (void* p : {(void*)g.pix_ptr, (void*)g.pix_atom, (void*)g.c, (void*)g.z,
                     (void*)g.b, (void*)g.v, (void*)g.w, (void*)g.part,
-                    (void*)g.bmax})
+                    (void*)g.bmax, g.upart})
       if (p) cudaFree(p);
     delete ctx->pg;
     ctx->pg = nullptr;
@@ -173,9 +173,9 @@ osar_status validate(const osar_config* c, std::string* why) {
   if (c->pixel_gram != 0 && c->pixel_gram != 1)
     return *why = "pixel_gram must be 0 or 1", OSAR_E_INVALID;
   if (c->pixel_gram &&
-      (c->dict_kind != OSAR_DICT_EDGELET || c->n_lambdas != 1 || c->defer_gram))
-    return *why = "pixel_gram needs the edgelet dictionary, one lambda and "
-                  "defer_gram = 0", OSAR_E_INVALID;
+      (c->dict_kind == OSAR_DICT_IDENTITY || c->n_lambdas != 1 || c->defer_gram))
+    return *why = "pixel_gram needs a dictionary (edgelet, Gaussian or host), "
+                  "one lambda and defer_gram = 0", OSAR_E_INVALID;
   if (c->n_lambdas < 1 || c->n_lambdas > MAX_LAMBDAS)
     return *why = "n_lambdas must be in [1, 8]", OSAR_E_INVALID;
   if (c->n_lambdas > 1) {
@@ -313,7 +313,9 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
                         : ctx->N;
   if (pixgram) {
     ctx->pg = new PixGram();
-    ctx->pg->M = cfg->n_edgelet_lengths * cfg->n_edgelet_angles * ctx->N;
+    ctx->pg->dense = cfg->dict_kind != OSAR_DICT_EDGELET;
+    ctx->pg->M = ctx->pg->dense ? cfg->n_atoms
+                                : cfg->n_edgelet_lengths * cfg->n_edgelet_angles * ctx->N;
     ctx->pg->Mp = (int)roundup(ctx->pg->M, BLK);
     ctx->pg->nb = ctx->pg->Mp / BLK;
   }
@@ -444,7 +446,24 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     AL(ctx->corr_tick, sizeof(unsigned));
   }
   std::vector<int> pix_ptr, pix_atom;
-  if (ctx->pg) {
+  if (ctx->pg && ctx->pg->dense) {
+    // a dense dictionary in its stored form for the two dictionary products
+    // of every Gram application, and the coefficient-side vectors
+    PixGram& g = *ctx->pg;
+    const int64_t gm = g.Mp;
+    if (ctx->prec == OSAR_SPLIT_BF16)
+      AL(ctx->Dpl, 2 * 4 * gm * Np);
+    else
+      AL(ctx->D, cplx * gm * Np);
+    AL(g.upart, cplx * (int64_t)pgd_chunks(ctx) * Np);
+    AL(g.c, 16 * gm);
+    AL(g.z, 16 * gm);
+    AL(g.b, 16 * gm);
+    AL(g.v, 16 * gm);
+    AL(g.w, 16 * gm);
+    AL(g.part, 16 * ((gm + 63) / 64));
+    AL(g.bmax, 8 * ((gm + 63) / 64));
+  } else if (ctx->pg) {
     // H both ways: the atoms' pixel lists and, per pixel, its atoms
     PixGram& g = *ctx->pg;
     build_edgelets(*cfg, atom_ptr, atom_pix);
@@ -553,6 +572,18 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     // the host lists leave scope below: the copies complete first
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "edgelet atoms"));
+  } else if (ctx->pg && ctx->pg->dense) {
+    // the coefficient power vector v = 1/sqrt(M) on the M atoms, and D
+    const PixGram& g = *ctx->pg;
+    std::vector<double2> vc((size_t)g.Mp, make_double2(0.0, 0.0));
+    for (int i = 0; i < g.M; ++i) vc[i].x = 1.0 / std::sqrt((double)g.M);
+    e = cudaMemcpyAsync(g.v, vc.data(), 16 * (size_t)g.Mp, cudaMemcpyHostToDevice,
+                        ctx->stream);
+    if (e == cudaSuccess)
+      e = launch_dictionary_build(
+          ctx, cfg->dict_kind == OSAR_DICT_HOST ? cfg->dict_c128 : nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "dictionary build"));
   } else if (ctx->pg) {
     // both lists, and the coefficient power vector v = 1/sqrt(M) on the
     // M atoms (the stored-Gram form's start)

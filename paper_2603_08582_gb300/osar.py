@@ -26,7 +26,7 @@ PRECISIONS = {"fp64": OSAR_FP64, "fp32": OSAR_FP32, "split_bf16": OSAR_SPLIT_BF1
 
 KERNEL_CLASSES = {"phase": 0, "dict_gemm": 1, "gram_gemm": 2, "data_update": 3,
                   "matvec": 4, "fista_finalize": 5, "power_finalize": 6,
-                  "block_term": 7}
+                  "block_term": 7, "dict_apply": 8}
 
 # Symbols declared in include/osar.h (checked by the CPU test suite).
 EXPORTS = [

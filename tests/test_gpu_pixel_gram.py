@@ -158,3 +158,76 @@ def test_pixel_gram_non_white_pulses(prec):
         assert_coeffs(g.coeffs(), of.s, t["c"], SUPPORT_DELTA[prec])
         st = g.state()
         assert abs(st["lipschitz"] - of.s.lip) <= max(t["gram"], 1e-7) * of.s.lip * 10
+
+
+# --------------------------------------------------------------------------
+# Dense dictionaries (Gaussian, host): G_n = D^H P_n D applied as
+# D^H (P_n (D x)), the two dictionary products as matrix-vector kernels.
+
+def _wg(nx=12, ny=12, n_freq=40, n_pulses=5, m=300, seed=19, dict_seed=7):
+    return small_workload(nx=nx, ny=ny, n_freq=n_freq, n_pulses=n_pulses,
+                          dictionary="gaussian", n_atoms=m, sparsity=0.03,
+                          seed=seed, dict_seed=dict_seed)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "split_bf16"])
+def test_dense_pixel_gram_parity_every_pulse(prec):
+    # 12 x 12 pixels (N = 144: 2 blocks), M = 300 Gaussian atoms (ragged), K = 40
+    w = _wg()
+    t = TOL[prec]
+
+    def check(s, of, g, no, ng, dic):
+        p = g.gram()
+        assert p.shape == (w.nx * w.ny, w.nx * w.ny)
+        assert_close(dic.conj().T @ p @ dic, of.s.gram, t["gram"], "D^H P D")
+        assert_close(g.b(), of.s.b, t["b"], "b")
+        assert_coeffs(g.coeffs(), of.s, t["c"], SUPPORT_DELTA[prec])
+        st = g.state()
+        assert st["n"] == of.s.n
+        assert abs(st["lambda"] - of.s.lam) <= t["b"] * of.s.lam
+        assert abs(st["lipschitz"] - of.s.lip) <= max(t["gram"], 1e-7) * of.s.lip * 10
+        assert st["t"] == pytest.approx(of.s.t, rel=1e-12)
+
+    _run(w, prec, steps=10, check=check)
+
+
+def test_dense_pixel_gram_host_dictionary_and_stop_rule():
+    w = _wg(nx=10, ny=9, m=200, n_pulses=5, seed=23)
+    track, dic, _, data = build_problem(w)
+    of = orc.OnlineFista(oracle_config(w, dic))
+    cfg = gpu_config(w, "fp64", host_dictionary=dic)
+    cfg.pixel_gram = 1
+    g = osar.Osar(cfg)
+    for s in range(w.n_pulses):
+        of.push_pulse(track[s], data[s])
+        g.push_pulse(track[s], data[s])
+        assert g.iterate(40, 1e-5) == of.iterate(40, 1e-5)
+        assert_coeffs(g.coeffs(), of.s, TOL["fp64"]["c"], SUPPORT_DELTA["fp64"])
+
+
+def test_dense_pixel_gram_against_the_stored_gram_form():
+    # 32 x 32 pixels, M = 2048 Gaussian atoms (16 blocks), N = 1024
+    w = _wg(nx=32, ny=32, n_freq=64, n_pulses=4, m=2048, seed=12)
+    track, _, _, data = build_problem(w)
+    a, b = _ctx(w, "split_bf16", pixel=False), _ctx(w, "split_bf16", pixel=True)
+    for s in range(track.shape[0]):
+        for g in (a, b):
+            g.push_pulse(track[s], data[s])
+            g.iterate(12, 0.0, want_count=False)
+        assert rel_err(b.coeffs(), a.coeffs()) <= 1e-4
+        assert rel_err(b.b(), a.b()) <= 1e-5
+        sa, sb = a.state(), b.state()
+        assert abs(sa["lipschitz"] - sb["lipschitz"]) <= 1e-5 * sa["lipschitz"]
+    assert b.device_bytes() < a.device_bytes()
+
+
+def test_dense_pixel_gram_simulated_pulse_matches_the_oracle():
+    w = _wg(nx=10, ny=7, n_freq=24, m=150)
+    track, dic, c_true, _ = build_problem(w)
+    g = _ctx(w, "fp64")
+    x = orc.pixel_positions(w.nx, w.ny, w.pixel_m)
+    f = orc.frequencies(w.n_freq, w.f_lo_hz, w.f_hi_hz)
+    for s in (0, 3):
+        want = orc.simulate_pulse(orc.forward_block(orc.phase_matrix(track[s], x, f), dic),
+                                  c_true)
+        assert rel_err(g.simulate_pulse(track[s], c_true), want) <= 1e-9

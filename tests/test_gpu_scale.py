@@ -9,7 +9,9 @@ multi-tile path runs:
   so each SM pair of the Gram update handles many tiles (TMEM double buffer,
   the epilogue's prefetch across tile boundaries, the fused power step's
   tile-parity reduction buffers) and the matvec hands out segment tickets;
-* the 128 x 128 / M = 32768 / K = 512 workload itself (its first pulses);
+* the 128 x 128 / M = 32768 / K = 512 workload itself (its first pulses),
+  in the stored-Gram form and in the pixel-space Gram form (P_n, N x N,
+  G_n applied as D^H P_n D);
 * the 256 x 256 pixel-basis workload (M = 65536, K = 1024, 10 steps per
   pulse; its first pulses), against the oracle in its matrix-free mode
   (Eq. 10: A_n x = sum_k G_k^H G_k x), since the 69 GB FP64 Gram does not
@@ -66,21 +68,41 @@ def _compare(of, gpu, rng, what):
                          f"{what} c")
 
 
-def _run(w, pulses, steps, rng):
+def _run(w, pulses, steps, rng, pixel_form=False):
+    """The stored-Gram context (and, with pixel_form, the pixel-space Gram
+    form of the same dictionary beside it) against one oracle run."""
     dic = host_gaussian_dictionary(w.n_pixels, w.m_atoms, w.dict_seed)
     track, _, data = dictionary_pulses(w, dic, pulses)
     of = orc.OnlineFista(oracle_config(w, dic, lam=w.lambda_rel))
     gpu = osar.Osar(gpu_config(w, "split_bf16", lam=w.lambda_rel))
+    pix = None
+    if pixel_form:
+        cfg = gpu_config(w, "split_bf16", lam=w.lambda_rel)
+        cfg.pixel_gram = 1
+        pix = osar.Osar(cfg)
     errs = []
     for s in range(pulses):
         of.push_pulse(track[s], data[s])
-        gpu.push_pulse(track[s], data[s])
+        for g in (gpu, pix):
+            if g is not None:
+                g.push_pulse(track[s], data[s])
+                assert g.iterate(steps) == steps
         assert of.iterate(steps) == steps
-        assert gpu.iterate(steps) == steps
         errs.append(_compare(of, gpu, rng, f"pulse {s}"))
+        if pix is not None:
+            assert_close(pix.b(), of.s.b, TOL_B, f"pulse {s} pixel form b")
+            st = pix.state()
+            assert abs(st["lipschitz"] - of.s.lip) <= 1e-3 * of.s.lip
+            assert abs(st["lambda"] - of.s.lam) <= 1e-3 * of.s.lam
+            errs.append(assert_coeffs(pix.coeffs(), of.s, TOL_C,
+                                      SUPPORT_DELTA["split_bf16"],
+                                      f"pulse {s} pixel form c"))
     # the matvec on a dense random vector, every row
     x = rng.standard_normal(w.m_atoms) + 1j * rng.standard_normal(w.m_atoms)
     assert_close(gpu.gram_apply(x), of.s.gram @ x, TOL_GRAM, "gram apply")
+    if pix is not None:
+        assert pix.device_bytes() < 0.6 * gpu.device_bytes()
+        pix.close()
     return of, gpu, errs
 
 
@@ -95,9 +117,10 @@ def test_multi_tile_64x64_M8192_every_pulse():
 
 def test_headline_128x128_M32768_first_pulses():
     w = synth.workloads()["c2_128x128_split_bf16"]
-    of, gpu, errs = _run(w, pulses=3, steps=20, rng=np.random.default_rng(2))
-    print("128x128 M=32768 split-BF16 coefficient errors per pulse:",
-          " ".join(f"{e:.2e}" for e in errs))
+    of, gpu, errs = _run(w, pulses=3, steps=20, rng=np.random.default_rng(2),
+                         pixel_form=True)
+    print("128x128 M=32768 split-BF16 coefficient errors per pulse "
+          "(stored form, pixel-space form):", " ".join(f"{e:.2e}" for e in errs))
 
 
 def test_large_online_256x256_first_pulses_matrix_free_oracle():
