@@ -446,8 +446,9 @@ osar_status osar_poke_guard(osar_ctx* ctx, int32_t index);
    launch of the listed kernel classes on the context's stream; reading the
    counters synchronises.  kernel: 0 phase, 1 dictionary GEMM, 2 Gram GEMM,
    3 data-vector update, 4 matvec (FISTA and power steps), 5 FISTA finalize,
-   6 power finalize, 7 deferred update's block term, 8 the pixel-space Gram
-   form's dictionary product u = D x (its D^H w is part of 5 and 6).
+   6 power finalize, 7 deferred update's block term, 8 the dense
+   dictionary products of the pixel-space Gram form (u = D x and D^H w, the
+   latter with its step).
    launches / total_ms may be NULL.
    Phase and dictionary launches of an overlapped push are bracketed on the
    side stream, so their time includes sharing the GPU with the burst. */

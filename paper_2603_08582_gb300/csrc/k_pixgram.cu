@@ -267,12 +267,15 @@ cudaError_t pg_after_push(osar_ctx* ctx) {
     cudaError_t e = scatter(ctx, g.v, 0);
     if (e == cudaSuccess) e = launch_gram_pass(ctx, ctx->zt, 0, ctx->w, KCL_POWFIN);
     if (e != cudaSuccess) return e;
+    if (g.dense) {
+      // D^H w with the power step (profiled as a dictionary product)
+      e = pgd_adjoint(ctx, 1, s == steps - 1 ? 1 : 0);
+      if (e != cudaSuccess) return e;
+      ctx->launches--;  // counted below with the normalisation
+    }
     ProfEvent ev;
     prof_begin(ctx, KCL_POWFIN, &ev);
-    if (g.dense) {
-      e = pgd_adjoint(ctx, 1, s == steps - 1 ? 1 : 0);
-      ctx->launches--;  // counted below with the normalisation
-    } else {
+    if (!g.dense) {
       k_pg_power_finalize<<<(unsigned)g.nb, BLK, 0, ctx->stream>>>(
           ctx->w, ctx->atom_ptr, ctx->atom_pix, g.M, g.v, g.w, g.part, ctx->scal,
           s == steps - 1 ? 1 : 0, ctx->cfg.lipschitz_margin);
@@ -299,13 +302,10 @@ cudaError_t pg_fista_step(osar_ctx* ctx) {
   cudaError_t e = scatter(ctx, g.z, 1);
   if (e == cudaSuccess) e = launch_gram_pass(ctx, ctx->zt, 1, ctx->w, KCL_FIN);
   if (e != cudaSuccess) return e;
+  // D^H w with the step (profiled as a dictionary product)
+  if (g.dense) return pgd_adjoint(ctx, 2, 0);
   ProfEvent ev;
   prof_begin(ctx, KCL_FIN, &ev);
-  if (g.dense) {
-    e = pgd_adjoint(ctx, 2, 0);
-    prof_end(ctx, &ev);
-    return e;
-  }
   if (ctx->prec == OSAR_FP64)
     k_pg_fista_finalize<double2><<<(unsigned)g.nb, BLK, 0, ctx->stream>>>(
         ctx->w, ctx->atom_ptr, ctx->atom_pix, g.M, g.b, g.c, g.z, g.part,

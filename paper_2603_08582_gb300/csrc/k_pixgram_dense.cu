@@ -190,7 +190,11 @@ __global__ void __launch_bounds__(PD_THREADS)
     k_pgd_adjoint(S d, int Np, const double2* __restrict__ w, PdArgs a) {
   using T2 = typename Vec<T>::T2;
   if (MODE == PD_FISTA && a.sc->converged) return;
-  __shared__ T2 ws[PD_CHUNK];
+  // w staged per chunk with PADW padding entries after every 8 pixels: a
+  // lane reads its 8 consecutive pixels with 16-byte loads, and the padding
+  // puts the 8 lanes of each shared-memory wavefront on distinct banks
+  constexpr int PADW = sizeof(T) == 4 ? 2 : 1;
+  __shared__ __align__(16) T2 ws[PD_CHUNK / 8 * (8 + PADW)];
   __shared__ double2 ys[PD_ATOMS];
   __shared__ double sh[3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -206,18 +210,33 @@ __global__ void __launch_bounds__(PD_THREADS)
       T2 t;
       t.x = (T)v.x;
       t.y = (T)v.y;
-      ws[i] = t;
+      ws[i + (i >> 3) * PADW] = t;
     }
     __syncthreads();
-#pragma unroll 1
+#pragma unroll
     for (int j = 0; j < 8; ++j) {
-#pragma unroll 2
+#pragma unroll 1
       for (int q = lane * 8; q < cl; q += 256) {
         T er[8], ei[8];
         d.template load8<T>(m0 + j, c0 + q, Np, er, ei);
+        const T2* wq = ws + q + (q >> 3) * PADW;
+        T2 wl[8];
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 v = reinterpret_cast<const float4*>(wq)[k];
+            wl[2 * k].x = v.x;
+            wl[2 * k].y = v.y;
+            wl[2 * k + 1].x = v.z;
+            wl[2 * k + 1].y = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) wl[k] = wq[k];
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const T2 wv = ws[q + i];
+          const T2 wv = wl[i];
           // conj(D) w
           ar[j] = fma(er[i], wv.x, fma(ei[i], wv.y, ar[j]));
           ai[j] = fma(er[i], wv.y, fma(-ei[i], wv.x, ai[j]));
@@ -388,6 +407,8 @@ cudaError_t pgd_adjoint(osar_ctx* ctx, int mode, int last_step) {
   a.margin = ctx->cfg.lipschitz_margin;
   const double2* w = mode == PD_BVEC ? ctx->b : ctx->w;
   const unsigned grid = cdiv(g.Mp, PD_ATOMS);
+  ProfEvent ev;
+  prof_begin(ctx, KCL_DAPPLY, &ev);
   cudaError_t e = with_dict(ctx, [&](auto d, auto zero) {
     using T = decltype(zero);
     if (mode == PD_BVEC)
@@ -401,6 +422,7 @@ cudaError_t pgd_adjoint(osar_ctx* ctx, int mode, int last_step) {
           d, ctx->Np, w, a);
     return cudaGetLastError();
   });
+  prof_end(ctx, &ev);
   ctx->launches++;
   return e;
 }
