@@ -77,6 +77,7 @@ struct PixGram {
   bool dense = false;         // a dense dictionary D (Gaussian or host) in
                               // the context's D / Dpl, not edgelet lists
   void* upart = nullptr;      // dense: partial sums of u = D x (chunks x Np)
+  void* apart = nullptr;      // dense: partial sums of D^H w (chunks x Mp)
   int M = 0;                  // atoms
   int Mp = 0;                 // atoms padded to BLK
   int nb = 0;                 // Mp / BLK
@@ -272,6 +273,7 @@ cudaError_t pg_fista_step(osar_ctx* ctx);
 // vector (zt), and (D^H w)_m with b_n / lambda_n (mode 0), a power step
 // (mode 1) or Algorithm 1's step (mode 2)
 int pgd_chunks(const osar_ctx* ctx);
+int pgd_adjoint_chunks(const osar_ctx* ctx);
 cudaError_t pgd_forward(osar_ctx* ctx, const double2* x, int gated);
 cudaError_t pgd_adjoint(osar_ctx* ctx, int mode, int last_step);
 

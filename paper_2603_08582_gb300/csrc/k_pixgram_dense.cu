@@ -180,67 +180,65 @@ struct PdArgs {
   double margin;
 };
 
-// y_m = (D^H w)_m for the PD_ATOMS atoms of this CTA (8 warps, 8 atoms each;
-// each lane sums its pixels in order, then a butterfly over the warp), then
-// per MODE: b_n and lambda_n (BVEC), a power step (POWER) or Algorithm 1's
-// step (FISTA), each finished by the grid's last CTA as the edgelet form's
-// kernels do.
-template <typename S, typename T, int MODE>
+// Partial sums of y_m = (D^H w)_m over one chunk of PD_CHUNK pixels for
+// the PD_ATOMS atoms of this CTA (8 warps, 8 atoms each; each lane sums its
+// pixels in order, then a butterfly over the warp): part[chunk][m].  Tiles
+// of (atoms, pixels) keep the grid many waves deep, so no SM idles at the
+// end of a pass over D.
+template <typename S, typename T>
 __global__ void __launch_bounds__(PD_THREADS)
-    k_pgd_adjoint(S d, int Np, const double2* __restrict__ w, PdArgs a) {
+    k_pgd_adjoint(S d, int Np, const double2* __restrict__ w,
+                  typename Vec<T>::T2* __restrict__ part, const DevScalars* sc,
+                  int gated) {
   using T2 = typename Vec<T>::T2;
-  if (MODE == PD_FISTA && a.sc->converged) return;
-  // w staged per chunk with PADW padding entries after every 8 pixels: a
-  // lane reads its 8 consecutive pixels with 16-byte loads, and the padding
-  // puts the 8 lanes of each shared-memory wavefront on distinct banks
+  if (gated && sc->converged) return;
+  // w staged with PADW padding entries after every 8 pixels: a lane reads
+  // its 8 consecutive pixels with 16-byte loads, and the padding puts the 8
+  // lanes of each shared-memory wavefront on distinct banks
   constexpr int PADW = sizeof(T) == 4 ? 2 : 1;
   __shared__ __align__(16) T2 ws[PD_CHUNK / 8 * (8 + PADW)];
-  __shared__ double2 ys[PD_ATOMS];
-  __shared__ double sh[3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * PD_ATOMS + warp * 8;
+  const int c0 = blockIdx.y * PD_CHUNK;
+  const int cl = min(PD_CHUNK, Np - c0);
+  for (int i = threadIdx.x; i < cl; i += PD_THREADS) {
+    const double2 v = w[c0 + i];
+    T2 t;
+    t.x = (T)v.x;
+    t.y = (T)v.y;
+    ws[i + (i >> 3) * PADW] = t;
+  }
+  __syncthreads();
   T ar[8], ai[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) ar[j] = ai[j] = T(0);
-  for (int c0 = 0; c0 < Np; c0 += PD_CHUNK) {
-    const int cl = min(PD_CHUNK, Np - c0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < cl; i += PD_THREADS) {
-      const double2 v = w[c0 + i];
-      T2 t;
-      t.x = (T)v.x;
-      t.y = (T)v.y;
-      ws[i + (i >> 3) * PADW] = t;
-    }
-    __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < 8; ++j) {
 #pragma unroll 1
-      for (int q = lane * 8; q < cl; q += 256) {
-        T er[8], ei[8];
-        d.template load8<T>(m0 + j, c0 + q, Np, er, ei);
-        const T2* wq = ws + q + (q >> 3) * PADW;
-        T2 wl[8];
-        if constexpr (sizeof(T) == 4) {
+    for (int q = lane * 8; q < cl; q += 256) {
+      T er[8], ei[8];
+      d.template load8<T>(m0 + j, c0 + q, Np, er, ei);
+      const T2* wq = ws + q + (q >> 3) * PADW;
+      T2 wl[8];
+      if constexpr (sizeof(T) == 4) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float4 v = reinterpret_cast<const float4*>(wq)[k];
-            wl[2 * k].x = v.x;
-            wl[2 * k].y = v.y;
-            wl[2 * k + 1].x = v.z;
-            wl[2 * k + 1].y = v.w;
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) wl[k] = wq[k];
+        for (int k = 0; k < 4; ++k) {
+          const float4 v = reinterpret_cast<const float4*>(wq)[k];
+          wl[2 * k].x = v.x;
+          wl[2 * k].y = v.y;
+          wl[2 * k + 1].x = v.z;
+          wl[2 * k + 1].y = v.w;
         }
+      } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const T2 wv = wl[i];
-          // conj(D) w
-          ar[j] = fma(er[i], wv.x, fma(ei[i], wv.y, ar[j]));
-          ai[j] = fma(er[i], wv.y, fma(-ei[i], wv.x, ai[j]));
-        }
+        for (int k = 0; k < 8; ++k) wl[k] = wq[k];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const T2 wv = wl[i];
+        // conj(D) w
+        ar[j] = fma(er[i], wv.x, fma(ei[i], wv.y, ar[j]));
+        ai[j] = fma(er[i], wv.y, fma(-ei[i], wv.x, ai[j]));
       }
     }
   }
@@ -252,10 +250,28 @@ __global__ void __launch_bounds__(PD_THREADS)
       ai[j] += __shfl_xor_sync(0xffffffffu, ai[j], o);
     }
   }
-  if (lane == 0)
+  if (lane == 0) {
+    T2* out = part + (int64_t)blockIdx.y * gridDim.x * PD_ATOMS + m0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      ys[warp * 8 + j] = make_double2((double)ar[j], (double)ai[j]);
+    for (int j = 0; j < 8; ++j) {
+      T2 v;
+      v.x = ar[j];
+      v.y = ai[j];
+      out[j] = v;
+    }
+  }
+}
+
+// y_m = the chunk partials summed in chunk order (FP64 from here), then per
+// MODE: b_n and lambda_n (BVEC), a power step (POWER) or Algorithm 1's step
+// (FISTA), each finished by the grid's last CTA as the edgelet form's
+// kernels do.  One CTA per 128 atoms.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(BLK)
+    k_pgd_finish(const typename Vec<T>::T2* __restrict__ part, int nchunk,
+                 int mp, PdArgs a) {
+  if (MODE == PD_FISTA && a.sc->converged) return;
+  __shared__ double sh[3];
   if (MODE == PD_FISTA && threadIdx.x == 0) {
     const double t = a.sc->t, tau = a.sc->tau;
     const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
@@ -264,23 +280,32 @@ __global__ void __launch_bounds__(PD_THREADS)
     sh[2] = (t - 1.0) / t_next;
   }
   __syncthreads();
-  const int i = threadIdx.x, idx = blockIdx.x * PD_ATOMS + i;
-  const bool mine = i < PD_ATOMS && idx < a.M;
-  const double2 y = mine ? ys[i] : make_double2(0.0, 0.0);
+  const int idx = blockIdx.x * BLK + threadIdx.x;
+  const bool mine = idx < a.M;
+  double2 y = make_double2(0.0, 0.0);
+  if (mine) {
+    T sr = 0, si = 0;
+    for (int k = 0; k < nchunk; ++k) {
+      const typename Vec<T>::T2 v = part[(int64_t)k * mp + idx];
+      sr += v.x;
+      si += v.y;
+    }
+    y = make_double2((double)sr, (double)si);
+  }
   if constexpr (MODE == PD_BVEC) {
     double m2 = 0.0;
     if (mine) {
       a.out[idx] = y;
       m2 = y.x * y.x + y.y * y.y;
     }
-    __shared__ double red[PD_THREADS / 32];
+    __shared__ double red[BLK / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-    if (lane == 0) red[warp] = m2;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m2;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
-      for (int k = 0; k < PD_THREADS / 32; ++k) t = fmax(t, red[k]);
+      for (int k = 0; k < BLK / 32; ++k) t = fmax(t, red[k]);
       a.bmax[blockIdx.x] = t;
     }
     if (!last_block(&a.sc->done, gridDim.x)) return;
@@ -322,7 +347,7 @@ __global__ void __launch_bounds__(PD_THREADS)
       const double2 zk = a.z[idx], bk = a.b[idx], cprev = a.c[idx];
       const double ur = zk.x - tau * (y.x - bk.x);
       const double ui = zk.y - tau * (y.y - bk.y);
-      const double keep = shrink_keep<T2>(ur * ur + ui * ui, alpha);
+      const double keep = shrink_keep<typename Vec<T>::T2>(ur * ur + ui * ui, alpha);
       const double cr = ur * keep, ci = ui * keep;
       a.c[idx] = make_double2(cr, ci);
       a.z[idx] = make_double2(cr + beta * (cr - cprev.x), ci + beta * (ci - cprev.y));
@@ -361,6 +386,10 @@ cudaError_t with_dict(const osar_ctx* ctx, F&& f) {
 
 int pgd_chunks(const osar_ctx* ctx) {
   return (int)cdiv(ctx->pg->Mp, PD_FWD_ATOMS);
+}
+
+int pgd_adjoint_chunks(const osar_ctx* ctx) {
+  return (int)cdiv(ctx->Np, PD_CHUNK);
 }
 
 // u = D x into the context's pixel working vector (zt).
@@ -406,24 +435,27 @@ cudaError_t pgd_adjoint(osar_ctx* ctx, int mode, int last_step) {
   a.last_step = last_step;
   a.margin = ctx->cfg.lipschitz_margin;
   const double2* w = mode == PD_BVEC ? ctx->b : ctx->w;
-  const unsigned grid = cdiv(g.Mp, PD_ATOMS);
+  const dim3 grid(cdiv(g.Mp, PD_ATOMS), cdiv(ctx->Np, PD_CHUNK));
+  const int gated = mode == PD_FISTA ? 1 : 0;
   ProfEvent ev;
   prof_begin(ctx, KCL_DAPPLY, &ev);
   cudaError_t e = with_dict(ctx, [&](auto d, auto zero) {
     using T = decltype(zero);
+    using T2 = typename Vec<T>::T2;
+    k_pgd_adjoint<decltype(d), T><<<grid, PD_THREADS, 0, ctx->stream>>>(
+        d, ctx->Np, w, (T2*)g.apart, ctx->scal, gated);
+    const unsigned fg = (unsigned)g.nb;
+    const int nch = (int)grid.y, mp = (int)grid.x * PD_ATOMS;
     if (mode == PD_BVEC)
-      k_pgd_adjoint<decltype(d), T, PD_BVEC><<<grid, PD_THREADS, 0, ctx->stream>>>(
-          d, ctx->Np, w, a);
+      k_pgd_finish<T, PD_BVEC><<<fg, BLK, 0, ctx->stream>>>((const T2*)g.apart, nch, mp, a);
     else if (mode == PD_POWER)
-      k_pgd_adjoint<decltype(d), T, PD_POWER><<<grid, PD_THREADS, 0, ctx->stream>>>(
-          d, ctx->Np, w, a);
+      k_pgd_finish<T, PD_POWER><<<fg, BLK, 0, ctx->stream>>>((const T2*)g.apart, nch, mp, a);
     else
-      k_pgd_adjoint<decltype(d), T, PD_FISTA><<<grid, PD_THREADS, 0, ctx->stream>>>(
-          d, ctx->Np, w, a);
+      k_pgd_finish<T, PD_FISTA><<<fg, BLK, 0, ctx->stream>>>((const T2*)g.apart, nch, mp, a);
     return cudaGetLastError();
   });
   prof_end(ctx, &ev);
-  ctx->launches++;
+  ctx->launches += 2;
   return e;
 }
 

@@ -76,7 +76,7 @@ void free_all(osar_ctx* ctx) {
     const PixGram& g = *ctx->pg;
     for (void* p : {(void*)g.pix_ptr, (void*)g.pix_atom, (void*)g.c, (void*)g.z,
                     (void*)g.b, (void*)g.v, (void*)g.w, (void*)g.part,
-                    (void*)g.bmax, g.upart})
+                    (void*)g.bmax, g.upart, g.apart})
       if (p) cudaFree(p);
     delete ctx->pg;
     ctx->pg = nullptr;
@@ -456,13 +456,14 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     else
       AL(ctx->D, cplx * gm * Np);
     AL(g.upart, cplx * (int64_t)pgd_chunks(ctx) * Np);
+    AL(g.apart, cplx * (int64_t)pgd_adjoint_chunks(ctx) * gm);
     AL(g.c, 16 * gm);
     AL(g.z, 16 * gm);
     AL(g.b, 16 * gm);
     AL(g.v, 16 * gm);
     AL(g.w, 16 * gm);
-    AL(g.part, 16 * ((gm + 63) / 64));
-    AL(g.bmax, 8 * ((gm + 63) / 64));
+    AL(g.part, 16 * (int64_t)g.nb);
+    AL(g.bmax, 8 * (int64_t)g.nb);
   } else if (ctx->pg) {
     // H both ways: the atoms' pixel lists and, per pixel, its atoms
     PixGram& g = *ctx->pg;
