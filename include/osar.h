@@ -524,11 +524,30 @@ osar_status osar_batch_get_coeffs(osar_batch* batch, int32_t scene,
 osar_status osar_batch_get_state(osar_batch* batch, int32_t scene, int32_t* n,
                                  double* lipschitz, double* lambda, double* t);
 
-/* Choose the matvec work-item size (blocks per segment) by timing the
-   candidates 1, 2, 4, 8, 16 on the device; the choice is cached in the text
-   file named by the environment variable OSAR_TUNE_CACHE (when set) and
-   reused by later batches of the same shape.  chosen (nullable). */
+/* Autotuner of the batching form, timing candidates on the device:
+    1. the Gram update's tile order: each scene's upper blocks in
+       super-blocks of 4, 8, 16 or 32 x 32 blocks (the tiles running together
+       share operand rows in L2), the scenes in index order or the largest
+       first.  Timed only when no pulse has been pushed yet (the statistics
+       and operands are then zero, so the timed updates change nothing);
+       after the first push the current order is kept.  Every output block is
+       one tile's, so results are bitwise the same in any order;
+    2. the matvec's work-item size: 1, 2, 4, 8 or 16 blocks per segment.
+   The choices are cached in the text file named by the environment variable
+   OSAR_TUNE_CACHE (when set) and reused by later batches of the same shape
+   (also at create).  chosen (nullable) receives the segment size.  No paper
+   counterpart. */
 osar_status osar_batch_autotune(osar_batch* batch, int32_t* chosen);
+
+/* The tuning in force: blocks per matvec segment, the Gram tile order's
+   super-block size and scene order (1: largest first), and the Gram update's
+   time in the default order (8, index order) and in the chosen one, as the
+   last autotune measured them (0 when it did not time them).  Any pointer
+   may be NULL. */
+osar_status osar_batch_get_tuning(const osar_batch* batch, int32_t* segment_blocks,
+                                  int32_t* gram_superblock,
+                                  int32_t* gram_largest_first,
+                                  double* gram_ms_default, double* gram_ms_chosen);
 
 /* Scene count, device bytes, kernel launches so far, segment size. */
 osar_status osar_batch_info(const osar_batch* batch, int32_t* n_scenes,

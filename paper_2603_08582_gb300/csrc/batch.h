@@ -42,6 +42,9 @@ struct osar_batch {
   int nseg = 0;
   int items = 0;         // sum of nb (finalize items)
   int seg_len = 0;       // blocks per matvec segment (autotuned)
+  int gram_sb = 8;       // Gram tile order: super-blocks of sb x sb blocks
+  int gram_lpt = 0;      // 1: the largest scenes' tiles first (autotuned)
+  double tune_gram_ms[2] = {0.0, 0.0};  // Gram update: default order, chosen
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int sm_count = 0;

@@ -12,6 +12,7 @@
 // segment length (blocks per work item) is chosen by a small autotuner that
 // times the candidates on the device and caches the choice in the file named
 // by OSAR_TUNE_CACHE.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -126,9 +127,38 @@ cudaError_t upload_desc(osar_batch* B) {
                          B->stream);
 }
 
+// Every scene's Gram tiles (global operand row blocks, global packed output
+// block, scene), each scene's upper blocks in gram_sb x gram_sb super-blocks
+// (the tiles running together share operand rows in L2), the scenes in
+// index order or, with gram_lpt, the largest first (their long tile runs
+// start early and the small scenes fill the tail).  Each output block is
+// one tile's, so the order never changes a result.
+void build_gram_tiles(osar_batch* B) {
+  std::vector<int> order(B->S);
+  for (int s = 0; s < B->S; ++s) order[s] = s;
+  if (B->gram_lpt)
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return B->desc_h[a].nb > B->desc_h[b].nb;
+    });
+  const int SB = B->gram_sb;
+  B->gram_tiles_all.clear();
+  for (int s : order) {
+    const SceneDesc& d = B->desc_h[s];
+    const int rb = d.row / BLK;
+    for (int bi = 0; bi < d.nb; bi += SB)
+      for (int bj = bi; bj < d.nb; bj += SB)
+        for (int I = bi; I < bi + SB && I < d.nb; ++I)
+          for (int J = (bj > I ? bj : I); J < bj + SB && J < d.nb; ++J)
+            B->gram_tiles_all.push_back(make_int4(
+                rb + I, rb + J, (int)(d.gblk + packed_block(I, J, d.nb)), s));
+  }
+  B->n_gram_tiles = 0;  // the next push uploads its active scenes' tiles
+}
+
 std::string tune_key(const osar_batch* B) {
   std::ostringstream k;
-  k << "batch_matvec_seg prec" << B->prec << " sm" << B->sm_count << " S" << B->S;
+  k << "batch_tune2 prec" << B->prec << " sm" << B->sm_count << " S" << B->S
+    << " K" << B->Kp;
   uint64_t h = 1469598103934665603ull;
   for (int s = 0; s < B->S; ++s) {
     h ^= (uint64_t)B->desc_h[s].nb;
@@ -138,25 +168,48 @@ std::string tune_key(const osar_batch* B) {
   return k.str();
 }
 
-int cache_lookup(const std::string& key) {
+// Tuning cache ($OSAR_TUNE_CACHE): lines "key=seg_len sb lpt"; the last
+// line for a key wins.  Returns false when the key is absent.
+bool cache_lookup(const std::string& key, int* seg, int* sb, int* lpt) {
   const char* path = std::getenv("OSAR_TUNE_CACHE");
-  if (!path) return 0;
+  if (!path) return false;
   std::ifstream f(path);
   std::string line;
+  bool found = false;
   while (std::getline(f, line)) {
     const size_t eq = line.rfind('=');
-    if (eq != std::string::npos && line.substr(0, eq) == key)
-      return std::atoi(line.c_str() + eq + 1);
+    if (eq == std::string::npos || line.substr(0, eq) != key) continue;
+    std::istringstream v(line.substr(eq + 1));
+    int a = 0, b = 0, c = -1;
+    if (v >> a >> b >> c && a > 0 && b > 0 && (c == 0 || c == 1)) {
+      *seg = a;
+      *sb = b;
+      *lpt = c;
+      found = true;
+    }
   }
-  return 0;
+  return found;
 }
 
-void cache_store(const std::string& key, int value) {
+void cache_store(const std::string& key, int seg, int sb, int lpt) {
   const char* path = std::getenv("OSAR_TUNE_CACHE");
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << "=" << value << "\n";
+  f << key << "=" << seg << " " << sb << " " << lpt << "\n";
 }
+
+// Two timing events, destroyed on every path.
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&a);
+    return e == cudaSuccess ? cudaEventCreate(&b) : e;
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
 
 }  // namespace
 
@@ -254,14 +307,6 @@ osar_status osar_batch_create(const osar_config* cfgs, int32_t n_scenes,
     d.margin = c.lipschitz_margin;
     for (int r = 0; r < mp; ++r) row_scene.push_back(s);
     for (int K = 0; K < d.nb; ++K) items_h.push_back(make_int2(s, K));
-    // Gram tiles in 8 x 8 super-blocks, global row blocks and output blocks
-    const int rb = rows / BLK, SB = 8;
-    for (int bi = 0; bi < d.nb; bi += SB)
-      for (int bj = bi; bj < d.nb; bj += SB)
-        for (int I = bi; I < bi + SB && I < d.nb; ++I)
-          for (int J = (bj > I ? bj : I); J < bj + SB && J < d.nb; ++J)
-            B->gram_tiles_all.push_back(make_int4(
-                rb + I, rb + J, (int)(blocks + packed_block(I, J, d.nb)), s));
     rows += mp;
     blocks += packed_count(d.nb);
     items += d.nb;
@@ -275,6 +320,7 @@ osar_status osar_batch_create(const osar_config* cfgs, int32_t n_scenes,
   B->rows = rows;
   B->blocks = blocks;
   B->items = items;
+  build_gram_tiles(B);
   const size_t cplx = prec == OSAR_FP64 ? 16 : 8;
   const int64_t R = rows, Kp = B->Kp;
 #define BA(p, bytes)                                        \
@@ -351,8 +397,13 @@ osar_status osar_batch_create(const osar_config* cfgs, int32_t n_scenes,
   int len = (int)(blocks / ((int64_t)B->sm_count * 2 * 12));
   if (len < 1) len = 1;
   if (len > 16) len = 16;
-  const int cached = cache_lookup(tune_key(B));
-  if (cached > 0) len = cached;
+  int c_seg = 0, c_sb = 0, c_lpt = 0;
+  if (cache_lookup(tune_key(B), &c_seg, &c_sb, &c_lpt)) {
+    len = c_seg;
+    B->gram_sb = c_sb;
+    B->gram_lpt = c_lpt;
+    build_gram_tiles(B);
+  }
   e = upload_segments(B, len);
   if (e != cudaSuccess) return bail(bcuda(B, e, "segments"));
   if (prec == OSAR_SPLIT_BF16) {
@@ -517,41 +568,88 @@ osar_status osar_batch_autotune(osar_batch* B, int32_t* chosen) {
   if (!B) return OSAR_E_INVALID;
   if (B->sticky != OSAR_OK) return B->sticky;
   const std::string key = tune_key(B);
-  int best = cache_lookup(key);
-  if (best <= 0) {
-    // time the batched matvec (all scenes active) for each segment length
+  int seg = 0, sb = 0, lpt = 0;
+  if (!cache_lookup(key, &seg, &sb, &lpt)) {
     std::vector<int> saved(B->S);
     for (int s = 0; s < B->S; ++s) {
       saved[s] = B->desc_h[s].active;
       B->desc_h[s].active = 1;
     }
     BCK(B, upload_desc(B));
-    cudaEvent_t a, b;
-    BCK(B, cudaEventCreate(&a));
-    BCK(B, cudaEventCreate(&b));
+    EventPair ev;
+    BCK(B, ev.create());
+    auto time_it = [&](auto&& launch, int reps, float* ms) -> cudaError_t {
+      cudaError_t e = launch();  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(ev.a, B->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+      if (e == cudaSuccess) e = cudaEventRecord(ev.b, B->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev.b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ev.a, ev.b);
+      return e;
+    };
+    // 1. The Gram update's tile order: super-block size and scene order.
+    // Timed only before the first pulse: the statistics and the operand
+    // planes are still zero, so each timed update adds exact zeros and
+    // leaves every Gram as it was.  Afterwards the order is kept.
+    bool pushed = false;
+    for (int s = 0; s < B->S; ++s) pushed |= B->n_h[s] > 0;
+    sb = B->gram_sb;
+    lpt = B->gram_lpt;
+    if (!pushed) {
+      float best_ms = 1e30f;
+      for (int cand_lpt : {0, 1})
+        for (int cand_sb : {4, 8, 16, 32}) {
+          B->gram_sb = cand_sb;
+          B->gram_lpt = cand_lpt;
+          build_gram_tiles(B);
+          B->n_gram_tiles = (int)B->gram_tiles_all.size();
+          BCK(B, cudaMemcpyAsync(B->gram_tiles, B->gram_tiles_all.data(),
+                                 sizeof(int4) * B->gram_tiles_all.size(),
+                                 cudaMemcpyHostToDevice, B->stream));
+          float ms = 0.f;
+          BCK(B, time_it([&] { return batch_launch_gram(B); }, 3, &ms));
+          if (cand_sb == 8 && cand_lpt == 0) B->tune_gram_ms[0] = ms / 3;
+          if (ms < best_ms) {
+            best_ms = ms;
+            sb = cand_sb;
+            lpt = cand_lpt;
+          }
+        }
+      B->tune_gram_ms[1] = best_ms / 3;
+    }
+    // 2. The matvec's work-item size (blocks per segment).
     float best_ms = 1e30f;
     for (int len : {1, 2, 4, 8, 16}) {
       BCK(B, upload_segments(B, len));
-      for (int r = 0; r < 2; ++r) BCK(B, batch_launch_matvec(B, B->zt, 0, -1));
-      BCK(B, cudaEventRecord(a, B->stream));
-      for (int r = 0; r < 5; ++r) BCK(B, batch_launch_matvec(B, B->zt, 0, -1));
-      BCK(B, cudaEventRecord(b, B->stream));
-      BCK(B, cudaEventSynchronize(b));
       float ms = 0.f;
-      BCK(B, cudaEventElapsedTime(&ms, a, b));
+      BCK(B, time_it([&] { return batch_launch_matvec(B, B->zt, 0, -1); }, 5, &ms));
       if (ms < best_ms) {
         best_ms = ms;
-        best = len;
+        seg = len;
       }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     for (int s = 0; s < B->S; ++s) B->desc_h[s].active = saved[s];
     BCK(B, upload_desc(B));
-    cache_store(key, best);
+    cache_store(key, seg, sb, lpt);
   }
-  BCK(B, upload_segments(B, best));
-  if (chosen) *chosen = best;
+  B->gram_sb = sb;
+  B->gram_lpt = lpt;
+  build_gram_tiles(B);
+  BCK(B, upload_segments(B, seg));
+  if (chosen) *chosen = seg;
+  return OSAR_OK;
+}
+
+osar_status osar_batch_get_tuning(const osar_batch* B, int32_t* segment_blocks,
+                                  int32_t* gram_superblock,
+                                  int32_t* gram_largest_first,
+                                  double* gram_ms_default, double* gram_ms_chosen) {
+  if (!B) return OSAR_E_INVALID;
+  if (segment_blocks) *segment_blocks = B->seg_len;
+  if (gram_superblock) *gram_superblock = B->gram_sb;
+  if (gram_largest_first) *gram_largest_first = B->gram_lpt;
+  if (gram_ms_default) *gram_ms_default = B->tune_gram_ms[0];
+  if (gram_ms_chosen) *gram_ms_chosen = B->tune_gram_ms[1];
   return OSAR_OK;
 }
 

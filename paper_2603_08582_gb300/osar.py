@@ -49,7 +49,8 @@ EXPORTS = [
     "osar_version",
     "osar_batch_create", "osar_batch_destroy", "osar_batch_push",
     "osar_batch_iterate", "osar_batch_get_coeffs", "osar_batch_get_state",
-    "osar_batch_autotune", "osar_batch_info", "osar_batch_synchronize",
+    "osar_batch_autotune", "osar_batch_get_tuning", "osar_batch_info",
+    "osar_batch_synchronize",
     "osar_batch_last_error",
 ]
 
@@ -156,6 +157,8 @@ def load_library(path: str = LIB_PATH):
         "osar_batch_get_coeffs": (I32, [P, I32, D]),
         "osar_batch_get_state": (I32, [P, I32, C.POINTER(I32), D, D, D]),
         "osar_batch_autotune": (I32, [P, C.POINTER(I32)]),
+        "osar_batch_get_tuning": (I32, [P, C.POINTER(I32), C.POINTER(I32),
+                                        C.POINTER(I32), D, D]),
         "osar_batch_info": (I32, [P, C.POINTER(I32), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64), C.POINTER(I32)]),
         "osar_batch_synchronize": (I32, [P]),
@@ -584,6 +587,16 @@ class OsarBatch:
         ch = C.c_int32()
         self._check(self._lib.osar_batch_autotune(self._h, C.byref(ch)))
         return ch.value
+
+    def tuning(self) -> dict:
+        seg, sb, lpt = C.c_int32(), C.c_int32(), C.c_int32()
+        d0, d1 = C.c_double(), C.c_double()
+        self._check(self._lib.osar_batch_get_tuning(self._h, C.byref(seg), C.byref(sb),
+                                                    C.byref(lpt), C.byref(d0),
+                                                    C.byref(d1)))
+        return {"segment_blocks": seg.value, "gram_superblock": sb.value,
+                "gram_largest_first": bool(lpt.value), "gram_ms_default": d0.value,
+                "gram_ms_chosen": d1.value}
 
     def info(self):
         n, seg = C.c_int32(), C.c_int32()

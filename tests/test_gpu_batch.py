@@ -116,6 +116,51 @@ def test_batch_autotune_keeps_results(tmp_path):
         del os.environ["OSAR_TUNE_CACHE"]
 
 
+def test_batch_autotune_gram_order(tmp_path):
+    """The Gram update's tile order is timed before the first pulse (the
+    timed updates add exact zeros: the results equal an untuned batch's) and
+    kept after it; the choice is cached with the segment size."""
+    os.environ["OSAR_TUNE_CACHE"] = str(tmp_path / "tune.txt")
+    try:
+        ws = _scenes(seed=6)
+        probs = [build_problem(w) for w in ws]
+        a = osar.OsarBatch([gpu_config(w, "split_bf16") for w in ws])
+        b = osar.OsarBatch([gpu_config(w, "split_bf16") for w in ws])
+        b.autotune()
+        t = b.tuning()
+        assert t["gram_superblock"] in (4, 8, 16, 32)
+        assert 0.0 < t["gram_ms_chosen"] <= t["gram_ms_default"]
+        for s in range(3):
+            gam = np.stack([pr[0][s] for pr in probs])
+            data = [pr[3][s] for pr in probs]
+            for x in (a, b):
+                x.push([1] * len(ws), gam, data)
+                x.iterate(6)
+        for q in range(len(ws)):
+            # the segment size regroups the matvec's FP32 partial sums
+            assert rel_err(b.coeffs(q), a.coeffs(q)) <= 1e-6
+        c = osar.OsarBatch([gpu_config(w, "split_bf16") for w in ws])
+        tc = c.tuning()                                  # read from the cache
+        assert (tc["segment_blocks"], tc["gram_superblock"], tc["gram_largest_first"]) == \
+            (t["segment_blocks"], t["gram_superblock"], t["gram_largest_first"])
+        # after a pulse the order is kept and the Gram update is not timed
+        del os.environ["OSAR_TUNE_CACHE"]
+        d = osar.OsarBatch([gpu_config(w, "split_bf16") for w in ws])
+        gam = np.stack([pr[0][0] for pr in probs])
+        d.push([1] * len(ws), gam, [pr[3][0] for pr in probs])
+        d.autotune()
+        td = d.tuning()
+        assert td["gram_ms_chosen"] == 0.0 and td["gram_superblock"] == 8
+        d.iterate(6)
+        e = osar.OsarBatch([gpu_config(w, "split_bf16") for w in ws])
+        e.push([1] * len(ws), gam, [pr[3][0] for pr in probs])
+        e.iterate(6)
+        for q in range(len(ws)):
+            assert rel_err(d.coeffs(q), e.coeffs(q)) <= 1e-6
+    finally:
+        os.environ.pop("OSAR_TUNE_CACHE", None)
+
+
 def test_batch_96_uneven_scenes_split_bf16():
     """The batching workload: 96 scenes, sides 32..96, K = 256, own tracks;
     three pulses each in split-BF16, checked against the FP64 oracle on four
