@@ -746,6 +746,7 @@ def run_forms(stream):
                                      precision=prec) for x in ws]
             b = osar.OsarBatch(cfgs, stream=stream.cuda_stream)
             seg = b.autotune()
+            tuning = b.tuning()
             datas = [[rng.standard_normal(x.n_freq) + 1j * rng.standard_normal(x.n_freq)
                       for x in ws] for _ in range(pulses + 1)]
             b.push([1] * len(ws), np.stack([t[0] for t in tracks]), datas[0])
@@ -759,6 +760,7 @@ def run_forms(stream):
             out[f"c4_batch96_{prec}"] = {
                 "batch_pulses": pulses, "scene_pulses_per_s": round(96 * pulses / (ms / 1e3), 1),
                 "ms_per_batch_pulse": round(ms / pulses, 2), "segment_blocks": seg,
+                "tuning": tuning,
                 "device_gb": round(b.info()["device_bytes"] / 1e9, 2)}
             b.close()
         if "c4_batch96_fp64" in out:
