@@ -63,6 +63,15 @@ enum KernelClass {
   KCL_FIN = 5, KCL_POWFIN = 6, KCL_CORR = 7, KCL_DAPPLY = 8, KCL_COUNT = 9
 };
 
+// A captured unrolled-gradient sequence and what it was captured for.
+struct AdjGraph {
+  cudaGraphExec_t exec = nullptr;
+  int T = 0, C = 0;
+  void* buf = nullptr;
+  size_t bytes = 0;
+  int64_t kernels = 0;  // launches one replay stands for
+};
+
 struct ProfEvent {
   int kind;
   cudaEvent_t a, b;
@@ -229,6 +238,7 @@ struct osar_ctx {
   // differentiation-form scratch (allocated by the first unrolled gradient)
   void* adj_buf = nullptr;
   size_t adj_bytes = 0;
+  osar::AdjGraph adj_graph;  // the gradient's device sequence, captured
 
   // host mirror
   int n = 0;

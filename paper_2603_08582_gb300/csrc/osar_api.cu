@@ -85,6 +85,7 @@ void free_all(osar_ctx* ctx) {
   if (ctx->h_wring) cudaFreeHost(ctx->h_wring);
   for (cudaEvent_t ev : ctx->w_ev)
     if (ev) cudaEventDestroy(ev);
+  if (ctx->adj_graph.exec) cudaGraphExecDestroy(ctx->adj_graph.exec);
   if (ctx->adj_buf) cudaFree(ctx->adj_buf);
   for (int i = 0; i < RING; ++i)
     if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);

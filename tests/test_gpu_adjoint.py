@@ -172,3 +172,35 @@ def test_adjoint_64x64_full_config():
     fd_t = (f(lam, tau * (1 + ht)) - f(lam, tau * (1 - ht))) / (2 * ht * tau)
     assert abs(fd_l - r64["d_lambda"]) <= 1e-4 * abs(fd_l)
     assert abs(fd_t - r64["d_tau"]) <= 1e-4 * abs(fd_t)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_replayed_gradient_sequence_takes_new_arguments(prec):
+    """The gradient's device sequence is captured once per (T, checkpoint
+    interval) and replayed: a replay with other lambda, tau, t0, c0 and
+    c_true, and a call with another T (a new capture) in between, give
+    bitwise what a fresh context computes for the same call."""
+    w = small_workload(nx=10, ny=10, n_freq=20, n_pulses=5, sparsity=0.06, seed=37)
+    track, _, c_true, data = build_problem(w)
+    a = osar.Osar(gpu_config(w, prec))
+    for s in range(w.n_pulses):
+        a.push_pulse(track[s], data[s])
+    st = a.state()
+    lam, tau = st["lambda"], 1.0 / st["lipschitz"]
+    rng = np.random.default_rng(3)
+    c0 = 0.1 * (rng.standard_normal(w.m_atoms) + 1j * rng.standard_normal(w.m_atoms))
+    calls = [(12, 3, lam, tau, 1.0, np.zeros(w.m_atoms, complex), c_true),
+             (12, 3, 1.3 * lam, 0.9 * tau, 2.5, c0, 0.5 * c_true),
+             (7, 2, 0.8 * lam, tau, 1.0, c0, c_true),
+             (12, 3, 0.7 * lam, 0.95 * tau, 1.7, -c0, c_true)]
+    for T, C, l, t, t0, x0, ct in calls:
+        got = a.unroll_grad(T, C, l, t, x0, ct, t0=t0)
+        b = osar.Osar(gpu_config(w, prec))
+        for s in range(w.n_pulses):
+            b.push_pulse(track[s], data[s])
+        want = b.unroll_grad(T, C, l, t, x0, ct, t0=t0)
+        b.close()
+        for k in ("loss", "d_lambda", "d_tau"):
+            assert got[k] == want[k], (T, k)
+        assert np.array_equal(got["d_b"], want["d_b"])
+        assert np.array_equal(got["c_T"], want["c_T"])
