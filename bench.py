@@ -70,7 +70,10 @@ def parse():
                     help="1: each pulse's Gram update runs on the side stream "
                          "beside its power steps and burst, which add the "
                          "pulse's block term to G_{n-1} x")
-    ap.add_argument("--workload", choices=["c2", "probe8k", "probe_dict"],
+    ap.add_argument("--gram-superblock", type=int, default=0,
+                    help="Gram update tile order: super-blocks of this many "
+                         "blocks (0: the library's 8)")
+    ap.add_argument("--workload", choices=["c2", "probe8k", "probe_dict", "probe16k"],
                     default="c2",
                     help="c2: the 128x128 headline workload; probe8k: a "
                          "64x128 pixel-basis scene (M = 8192, 272 MB packed "
@@ -207,6 +210,12 @@ def workload(name="c2"):
             name="probe8k_64x128", nx=128, ny=64, n_freq=512, f_lo_hz=9.75e9,
             f_hi_hz=10.25e9, n_pulses=64, span_deg=45.0, sparsity=0.03,
             snr_db=25.0, seed=8)
+    if name == "probe16k":
+        return synth.Workload(
+            name="probe16k_128x64_M16384", nx=128, ny=64, n_freq=512,
+            f_lo_hz=9.75e9, f_hi_hz=10.25e9, n_pulses=64, span_deg=45.0,
+            dictionary="gaussian", n_atoms=16384, dict_seed=2, sparsity=0.03,
+            snr_db=25.0, seed=10)
     if name == "probe_dict":
         return synth.Workload(
             name="probe_dict_64x64_M8192", nx=64, ny=64, n_freq=512,
@@ -217,7 +226,7 @@ def workload(name="c2"):
 
 
 def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
-             fuse=True, defer=False, power_gram=True):
+             fuse=True, defer=False, power_gram=True, gram_superblock=0):
     from paper_2603_08582_gb300 import osar
     gauss = w.dictionary == "gaussian"
     cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
@@ -230,7 +239,8 @@ def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
                            fuse_first_step=fuse,
                            defer_gram=(defer and overlap and gauss
                                        and precision == "split_bf16"),
-                           fuse_power_gram=power_gram)
+                           fuse_power_gram=power_gram,
+                           gram_superblock=gram_superblock)
     return osar.Osar(cfg)
 
 
@@ -267,7 +277,8 @@ def run_ours(args):
     ov = dict(overlap=not args.no_overlap, synth_ctas=args.synth_ctas,
               tc_pairs=args.tc_pairs, fuse=not args.no_fuse,
               defer=bool(args.defer_gram) and not args.no_overlap,
-              power_gram=bool(args.fuse_power_gram))
+              power_gram=bool(args.fuse_power_gram),
+              gram_superblock=args.gram_superblock)
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
     # power steps per pulse that are Gram passes of their own
     power_passes = POWER_ITERS - (1 if ov["power_gram"] and not ov["defer"] else 0)

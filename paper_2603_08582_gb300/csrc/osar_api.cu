@@ -173,6 +173,8 @@ osar_status validate(const osar_config* c, std::string* why) {
     return *why = "fuse_power_gram must be 0 or 1", OSAR_E_INVALID;
   if (c->pixel_gram != 0 && c->pixel_gram != 1)
     return *why = "pixel_gram must be 0 or 1", OSAR_E_INVALID;
+  if (c->gram_superblock < 0 || c->gram_superblock > 64)
+    return *why = "gram_superblock must be in [0, 64]", OSAR_E_INVALID;
   if (c->pixel_gram &&
       (c->dict_kind == OSAR_DICT_IDENTITY || c->n_lambdas != 1 || c->defer_gram))
     return *why = "pixel_gram needs a dictionary (edgelet, Gaussian or host), "
@@ -223,7 +225,7 @@ void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
   std::reverse(segs.begin(), segs.end());
   // Gram tiles: upper blocks grouped in SB x SB super-blocks so that the
   // CTAs running at the same time share operand rows in L2.
-  const int SB = 8;
+  const int SB = ctx->cfg.gram_superblock > 0 ? ctx->cfg.gram_superblock : 8;
   for (int bi = 0; bi < nb; bi += SB)
     for (int bj = bi; bj < nb; bj += SB)
       for (int I = bi; I < bi + SB && I < nb; ++I)

@@ -74,6 +74,7 @@ class OsarConfig(C.Structure):
         ("n_edgelet_lengths", C.c_int32), ("edgelet_lengths", C.c_void_p),
         ("n_edgelet_angles", C.c_int32), ("edgelet_angles_deg", C.c_void_p),
         ("fuse_power_gram", C.c_int32), ("pixel_gram", C.c_int32),
+        ("gram_superblock", C.c_int32),
     ]
 
 
@@ -193,7 +194,8 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
                 compensated=True, stream=None, overlap_synthesis=True,
                 synth_ctas=0, tc_pairs=3, fuse_first_step=True, lambdas=None,
                 defer_gram=False, guard_bytes=0, edgelet_lengths=None,
-                edgelet_angles=None, fuse_power_gram=True, pixel_gram=False):
+                edgelet_angles=None, fuse_power_gram=True, pixel_gram=False,
+                gram_superblock=0):
     """Build an osar_config.  dictionary: None (identity), "gaussian"
     (seeded Philox atoms, needs n_atoms), "edgelet" (binary edgelets of
     edgelet_lengths x edgelet_angles degrees at every pixel) or an N x M
@@ -241,6 +243,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
     cfg.guard_bytes = int(guard_bytes)
     cfg.fuse_power_gram = 1 if fuse_power_gram else 0
     cfg.pixel_gram = 1 if pixel_gram else 0
+    cfg.gram_superblock = int(gram_superblock)
     if lambdas is not None and len(lambdas) > 1:
         # lambda path: one solution per value (relative or absolute like lam)
         lv = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
