@@ -72,7 +72,7 @@ def parse():
                          "pulse's block term to G_{n-1} x")
     ap.add_argument("--gram-superblock", type=int, default=0,
                     help="Gram update tile order: super-blocks of this many "
-                         "blocks (0: the library's 8)")
+                         "blocks (0: the library's 32)")
     ap.add_argument("--workload", choices=["c2", "probe8k", "probe_dict", "probe16k"],
                     default="c2",
                     help="c2: the 128x128 headline workload; probe8k: a "

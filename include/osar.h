@@ -203,8 +203,8 @@ typedef struct {
   int32_t pixel_gram;
   /* Order of the Gram update's tiles: the upper blocks in super-blocks of
      gram_superblock x gram_superblock blocks, so that the tiles running at
-     the same time share operand rows in L2; 0 = 8.  Any order gives the same
-     results (each output block is one tile's).  In [0, 64]. */
+     the same time share operand rows in L2; 0 = 32.  Any order gives the
+     same results (each output block is one tile's).  In [0, 64]. */
   int32_t gram_superblock;
 } osar_config;
 
@@ -214,7 +214,7 @@ typedef struct {
    overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
    (both tensor-core products on SM pairs), fuse_first_step = 1,
    n_lambdas = 1, defer_gram = 0, guard_bytes = 0, fuse_power_gram = 1,
-   pixel_gram = 0, gram_superblock = 0 (8). */
+   pixel_gram = 0, gram_superblock = 0 (32). */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context for the problem of Sec. III-C: the online reconstruction

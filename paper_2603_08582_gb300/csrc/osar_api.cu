@@ -225,7 +225,7 @@ void build_tables(osar_ctx* ctx, std::vector<int4>& segs,
   std::reverse(segs.begin(), segs.end());
   // Gram tiles: upper blocks grouped in SB x SB super-blocks so that the
   // CTAs running at the same time share operand rows in L2.
-  const int SB = ctx->cfg.gram_superblock > 0 ? ctx->cfg.gram_superblock : 8;
+  const int SB = ctx->cfg.gram_superblock > 0 ? ctx->cfg.gram_superblock : 32;
   for (int bi = 0; bi < nb; bi += SB)
     for (int bj = bi; bj < nb; bj += SB)
       for (int I = bi; I < bi + SB && I < nb; ++I)
