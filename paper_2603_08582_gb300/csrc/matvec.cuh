@@ -467,10 +467,18 @@ __device__ __forceinline__ double2 gather_row(const T2* __restrict__ segpart,
   const int total = nseg + (nb - 1 - K);
   const int64_t t0 = packed_block(K, K, nb) + 1;  // block (K, K+1)
   Acc yr = 0, yi = 0;
+  // q = g, g + FIN_GROUPS, ... over the segment partials, then on over the
+  // block partials (two loops: no select in the load stream)
+  int q = g;
 #pragma unroll 4
-  for (int q = g; q < total; q += FIN_GROUPS) {
-    const T2 v = q < nseg ? segpart[(int64_t)(s0 + q) * BLK + i]
-                          : tilepart[(t0 + (q - nseg)) * BLK + i];
+  for (; q < nseg; q += FIN_GROUPS) {
+    const T2 v = segpart[(int64_t)(s0 + q) * BLK + i];
+    yr += (Acc)v.x;
+    yi += (Acc)v.y;
+  }
+#pragma unroll 8
+  for (; q < total; q += FIN_GROUPS) {
+    const T2 v = tilepart[(t0 + (q - nseg)) * BLK + i];
     yr += (Acc)v.x;
     yi += (Acc)v.y;
   }
