@@ -51,6 +51,38 @@ def test_config_defaults_and_layout(lib):
     assert cfg.n_lambdas == 1 and cfg.lambda_list is None
     assert cfg.defer_gram == 0 and cfg.guard_bytes == 0
     assert cfg.fuse_power_gram == 1 and cfg.pixel_gram == 0
+    assert cfg.gram_superblock == 0
+
+
+def test_config_struct_layout_matches_the_header(tmp_path):
+    """The binding's osar_config and osar_metrics have the C structs' size
+    and field offsets (a C program compiled against include/osar.h prints
+    them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"osar_config": osar.OsarConfig, "osar_metrics": osar.OsarMetrics}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "osar.h"',
+             "int main(void) {"]
+    for cname, ct in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in ct._fields_:
+            cf = "lambda" if f == "lam" else f
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {cf}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.splitlines():
+        cname, what, value = line.split()
+        ct = structs[cname]
+        want = C.sizeof(ct) if what == "size" else getattr(ct, what).offset
+        assert int(value) == want, line
 
 
 @pytest.mark.parametrize("changes", [
@@ -78,7 +110,8 @@ def test_create_rejects_unsupported_deferred_update(lib, changes):
     ("lam", float("nan")), ("lipschitz_margin", -0.5),
     ("overlap_synthesis", 2), ("synth_ctas", -1), ("tc_pairs", 4),
     ("fuse_first_step", 2), ("fuse_power_gram", 2), ("pixel_gram", 2),
-    ("pixel_gram", 1),  # the pixel-space Gram form needs edgelets
+    ("pixel_gram", 1),  # the pixel-space Gram form needs a dictionary
+    ("gram_superblock", -1), ("gram_superblock", 65),
     ("n_lambdas", 0),
     ("n_lambdas", 9),
     ("n_lambdas", 2),  # > 1 without a lambda_list
