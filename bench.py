@@ -646,6 +646,29 @@ def run_large_online(stream, warmup=4, pulses=24, tune_every=8):
         else:
             out["untuned"] = res
         ctx.close()
+    # accuracy against the FP64 oracle (matrix-free: the 69 GB FP64 Gram does
+    # not fit in host memory) on the aperture's first two pulses, host data
+    # from the oracle's own forward model, 10 steps each
+    from oracle import osar_oracle as orc
+    P = 2
+    tr = synth.workload_track(w)[:P]
+    x = orc.pixel_positions(w.nx, w.ny, w.pixel_m)
+    f = orc.frequencies(w.n_freq, w.f_lo_hz, w.f_hi_hz)
+    clean = np.stack([orc.phase_matrix(g, x, f) @ c_true for g in tr])
+    noise = synth.unit_noise(w.n_pulses, w.n_freq, w.seed)[:P]
+    dd = clean + synth.scale_noise(clean, noise, w.snr_db)
+    of = orc.OnlineFista(orc.OracleConfig(
+        nx=w.nx, ny=w.ny, pixel_m=w.pixel_m, n_freq=w.n_freq, f_lo_hz=w.f_lo_hz,
+        f_hi_hz=w.f_hi_hz, lam=w.lambda_rel), matrix_free=True)
+    for s_ in range(P):
+        of.push_pulse(tr[s_], dd[s_])
+        of.iterate(steps)
+    ctx = make_ctx(w, "split_bf16", stream.cuda_stream)
+    acc = compare_with_oracle(ctx, of, tr, dd, steps, 0.0, gram_sample=48)
+    ctx.close()
+    acc["oracle"] = ("FP64 CPU oracle in its matrix-free mode (Eq. 10), the "
+                     "oracle's forward model for the data")
+    out["accuracy_vs_fp64_oracle"] = acc
     out["peak_source"] = src
     return out
 
@@ -1034,27 +1057,49 @@ def precision_report(w, kept, stream, ov, n_sample=64):
     error."""
     of, track, data = kept["oracle"], kept["track"], kept["data"]
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
-    steps = []
+    out = compare_with_oracle(ctx, of, track, data, INNER_STEPS, TOL,
+                              gram_sample=n_sample)
+    ctx.close()
+    # the pixel-space Gram form of the same dictionary on the same pulses
+    from paper_2603_08582_gb300 import osar
+    cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
+                           pixel_m=w.pixel_m, precision="split_bf16",
+                           dictionary="gaussian", n_atoms=w.m_atoms,
+                           dict_seed=w.dict_seed, lam=w.lambda_rel,
+                           stream=stream.cuda_stream, pixel_gram=True)
+    pix = osar.Osar(cfg)
+    out["pixel_space_form"] = compare_with_oracle(pix, of, track, data,
+                                                  INNER_STEPS, TOL, gram_sample=0)
+    pix.close()
+    out["oracle"] = "FP64 CPU oracle, same host data (d_s = F_s (H c_true) + noise)"
+    return out
+
+
+def compare_with_oracle(ctx, of, track, data, steps, tol, gram_sample=64):
+    """Push the oracle's pulses through ctx and compare its state with the
+    oracle's: sampled Gram entries (when gram_sample > 0), b, the
+    coefficients with their support difference, lambda_n and L_n."""
+    used = []
     for s in range(track.shape[0]):
         ctx.push_pulse(track[s], data[s])
-        steps.append(ctx.iterate(INNER_STEPS, TOL))
-    rng = np.random.default_rng(0)
-    cols = np.sort(rng.choice(w.m_atoms, n_sample, replace=False))
-    rr, cc = np.meshgrid(cols, cols, indexing="ij")
-    g_gpu = ctx.gram_entries(rr.ravel(), cc.ravel())
-    g_orc = of.s.gram[rr.ravel(), cc.ravel()]
+        used.append(ctx.iterate(steps, tol))
+    res = {"pulses": int(track.shape[0]), "steps_per_pulse_gpu": used}
+    if gram_sample > 0:
+        rng = np.random.default_rng(0)
+        cols = np.sort(rng.choice(of.m, gram_sample, replace=False))
+        rr, cc = np.meshgrid(cols, cols, indexing="ij")
+        g_gpu = ctx.gram_entries(rr.ravel(), cc.ravel())
+        g_orc = (of.s.gram.entries(rr.ravel(), cc.ravel()) if of.matrix_free
+                 else of.s.gram[rr.ravel(), cc.ravel()])
+        res["gram_sampled_entries"] = {**_errors(g_gpu, g_orc), "entries": int(g_orc.size)}
     c_gpu, c_orc = ctx.coeffs(), of.s.c_hat
-    b_gpu = ctx.b()
     st = ctx.state()
     sup_gpu, sup_orc = np.abs(c_gpu) > 0, np.abs(c_orc) > 0
     alpha = of.s.lam / of.s.lip
     near = np.abs(np.abs(of.s.u) - alpha) <= 1e-3 * np.max(np.abs(of.s.u))
     diff = sup_gpu != sup_orc
-    ctx.close()
-    return {
-        "pulses": int(track.shape[0]), "steps_per_pulse_gpu": steps,
-        "gram_sampled_entries": {**_errors(g_gpu, g_orc), "entries": int(g_orc.size)},
-        "b": _errors(b_gpu, of.s.b),
+    res.update({
+        "b": _errors(ctx.b(), of.s.b),
         "coefficients": {**_errors(c_gpu, c_orc),
                          "support_size_oracle": int(np.count_nonzero(sup_orc)),
                          "support_differences": int(np.count_nonzero(diff)),
@@ -1062,8 +1107,8 @@ def precision_report(w, kept, stream, ov, n_sample=64):
                              int(np.count_nonzero(diff & ~near)),
                          "threshold_band": "||u_i| - lambda tau| <= 1e-3 max|u|"},
         "lambda_rel_err": abs(st["lambda"] - of.s.lam) / of.s.lam,
-        "lipschitz_rel_err": abs(st["lipschitz"] - of.s.lip) / of.s.lip,
-        "oracle": "FP64 CPU oracle, same host data (d_s = F_s (H c_true) + noise)"}
+        "lipschitz_rel_err": abs(st["lipschitz"] - of.s.lip) / of.s.lip})
+    return res
 
 
 def run_reference(args):
