@@ -441,10 +441,16 @@ def run_ours(args):
     if not args.no_fp64 and rank == 0 and args.workload == "c2":
         fp64 = run_precision_path(w, "fp64", track, data, stream, args.fp64_pulses)
         fp32 = run_precision_path(w, "fp32", track, data, stream, args.fp32_pulses)
-    cpu = accuracy = None
+    cpu = accuracy = large_ref = None
     if not args.no_cpu_baseline and rank == 0 and world == 1 and args.workload == "c2":
+        # the CPU-baseline leg: the oracle timed on the 128 x 128 workload,
+        # and its results on the first pulses of the 128 x 128 and (when that
+        # leg runs) 256 x 256 workloads, which the accuracy entries compare
+        # with the GPU path
         kept = {}
         cpu = cpu_baseline(w, pulses=1, keep=kept)
+        if not args.no_large:
+            large_ref = oracle_reference_large()
         accuracy = precision_report(w, kept, stream, ov)
         kept.clear()
 
@@ -500,7 +506,7 @@ def run_ours(args):
         line["accuracy_vs_fp64_oracle"] = accuracy
     if rank == 0 and args.workload == "c2" and not args.no_large:
         line["pixel_space_gram_128x128"] = run_pixel_space_dense(stream, w)
-        line["large_online_256x256"] = run_large_online(stream)
+        line["large_online_256x256"] = run_large_online(stream, ref=large_ref)
     if args.forms and rank == 0:
         line["forms"] = run_forms(stream)
     if rank == 0:
@@ -573,7 +579,7 @@ def run_pixel_space_dense(stream, w, warmup=4, pulses=16):
     return out
 
 
-def run_large_online(stream, warmup=4, pulses=24, tune_every=8):
+def run_large_online(stream, warmup=4, pulses=24, tune_every=8, ref=None):
     """The 256 x 256 pixel-basis workload (N = M = 65536, K = 1024, 10 FISTA
     steps per pulse, split-BF16), without and with online lambda tuning (the
     burst's adjoint every `tune_every` pulses against the synthetic scene,
@@ -646,29 +652,12 @@ def run_large_online(stream, warmup=4, pulses=24, tune_every=8):
         else:
             out["untuned"] = res
         ctx.close()
-    # accuracy against the FP64 oracle (matrix-free: the 69 GB FP64 Gram does
-    # not fit in host memory) on the aperture's first two pulses, host data
-    # from the oracle's own forward model, 10 steps each
-    from oracle import osar_oracle as orc
-    P = 2
-    tr = synth.workload_track(w)[:P]
-    x = orc.pixel_positions(w.nx, w.ny, w.pixel_m)
-    f = orc.frequencies(w.n_freq, w.f_lo_hz, w.f_hi_hz)
-    clean = np.stack([orc.phase_matrix(g, x, f) @ c_true for g in tr])
-    noise = synth.unit_noise(w.n_pulses, w.n_freq, w.seed)[:P]
-    dd = clean + synth.scale_noise(clean, noise, w.snr_db)
-    of = orc.OnlineFista(orc.OracleConfig(
-        nx=w.nx, ny=w.ny, pixel_m=w.pixel_m, n_freq=w.n_freq, f_lo_hz=w.f_lo_hz,
-        f_hi_hz=w.f_hi_hz, lam=w.lambda_rel), matrix_free=True)
-    for s_ in range(P):
-        of.push_pulse(tr[s_], dd[s_])
-        of.iterate(steps)
-    ctx = make_ctx(w, "split_bf16", stream.cuda_stream)
-    acc = compare_with_oracle(ctx, of, tr, dd, steps, 0.0, gram_sample=48)
-    ctx.close()
-    acc["oracle"] = ("FP64 CPU oracle in its matrix-free mode (Eq. 10), the "
-                     "oracle's forward model for the data")
-    out["accuracy_vs_fp64_oracle"] = acc
+    if ref is not None:
+        # accuracy against the FP64 oracle's run that the CPU-baseline leg made
+        ctx = make_ctx(w, "split_bf16", stream.cuda_stream)
+        acc = compare_with_oracle(ctx, ref, steps, 0.0)
+        ctx.close()
+        out["accuracy_vs_fp64_oracle"] = acc
     out["peak_source"] = src
     return out
 
@@ -1030,8 +1019,8 @@ def cpu_baseline(w, pulses=1, warmup=1, keep=None):
         of.iterate(INNER_STEPS, TOL)
     dt = time.perf_counter() - t0
     if keep is not None:
-        # what the precision report compares the GPU path with
-        keep.update(oracle=of, track=track[:total], data=data)
+        # what the precision report compares the GPU path with (arrays only)
+        keep.update(oracle_state(of, track[:total], data, INNER_STEPS, TOL))
     return {"value": round(pulses / dt, 5), "unit": "pulses/s", "cores": cores,
             "kind": "oracle",
             "sample": (f"{pulses} full pulse(s) (pulse index {warmup}..{total - 1}) of "
@@ -1049,18 +1038,59 @@ def _errors(got, ref):
             "worst_rel_max": float(np.max(np.abs(got - ref)) / scale) if scale > 0 else None}
 
 
-def precision_report(w, kept, stream, ov, n_sample=64):
+def oracle_state(of, track, data, steps, tol, gram_sample=64):
+    """Part of the CPU-baseline leg: the oracle's state after the pulses it
+    ran, as plain arrays (sampled Gram entries, b, c_hat, the last pre-shrink
+    vector u, lambda_n, L_n), so that the GPU comparison runs no oracle
+    code."""
+    rng = np.random.default_rng(0)
+    cols = np.sort(rng.choice(of.m, gram_sample, replace=False))
+    rr, cc = np.meshgrid(cols, cols, indexing="ij")
+    rows, cols2 = rr.ravel(), cc.ravel()
+    entries = (of.s.gram.entries(rows, cols2) if of.matrix_free
+               else of.s.gram[rows, cols2])
+    return {"track": track, "data": data, "steps": steps, "tol": tol,
+            "rows": rows, "cols": cols2, "gram_entries": np.array(entries),
+            "b": of.s.b.copy(), "c_hat": of.s.c_hat.copy(), "u": of.s.u.copy(),
+            "lam": of.s.lam, "lip": of.s.lip}
+
+
+def oracle_reference_large(pulses=2):
+    """Part of the CPU-baseline leg: the FP64 oracle in its matrix-free mode
+    (Eq. 10; the 69 GB FP64 Gram does not fit in host memory) on the first
+    pulses of the 256 x 256 workload, 10 steps each, host data from the
+    oracle's own forward model."""
+    from oracle import osar_oracle as orc
+    from paper_2603_08582_gb300 import synth
+    w = synth.workloads()["c5_256x256_split_bf16"]
+    tr = synth.workload_track(w)[:pulses]
+    c_true = synth.workload_scene(w)
+    x = orc.pixel_positions(w.nx, w.ny, w.pixel_m)
+    f = orc.frequencies(w.n_freq, w.f_lo_hz, w.f_hi_hz)
+    clean = np.stack([orc.phase_matrix(g, x, f) @ c_true for g in tr])
+    noise = synth.unit_noise(w.n_pulses, w.n_freq, w.seed)[:pulses]
+    dd = clean + synth.scale_noise(clean, noise, w.snr_db)
+    of = orc.OnlineFista(orc.OracleConfig(
+        nx=w.nx, ny=w.ny, pixel_m=w.pixel_m, n_freq=w.n_freq, f_lo_hz=w.f_lo_hz,
+        f_hi_hz=w.f_hi_hz, lam=w.lambda_rel), matrix_free=True)
+    for s in range(pulses):
+        of.push_pulse(tr[s], dd[s])
+        of.iterate(w.inner_steps)
+    ref = oracle_state(of, tr, dd, w.inner_steps, 0.0, gram_sample=48)
+    ref["oracle"] = ("FP64 CPU oracle in its matrix-free mode (Eq. 10), the "
+                     "oracle's forward model for the data")
+    return ref
+
+
+def precision_report(w, kept, stream, ov):
     """The split-BF16 path with the bench's launch configuration against the
     FP64 oracle on the pulses the CPU baseline ran (the aperture's first
     ones, the same host data): sampled Gram entries, b, the coefficients
     (with the support difference), lambda_n and L_n, each as a relative
-    error."""
-    of, track, data = kept["oracle"], kept["track"], kept["data"]
+    error; and the pixel-space Gram form on the same pulses."""
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
-    out = compare_with_oracle(ctx, of, track, data, INNER_STEPS, TOL,
-                              gram_sample=n_sample)
+    out = compare_with_oracle(ctx, kept, INNER_STEPS, TOL)
     ctx.close()
-    # the pixel-space Gram form of the same dictionary on the same pulses
     from paper_2603_08582_gb300 import osar
     cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
                            pixel_m=w.pixel_m, precision="split_bf16",
@@ -1068,46 +1098,45 @@ def precision_report(w, kept, stream, ov, n_sample=64):
                            dict_seed=w.dict_seed, lam=w.lambda_rel,
                            stream=stream.cuda_stream, pixel_gram=True)
     pix = osar.Osar(cfg)
-    out["pixel_space_form"] = compare_with_oracle(pix, of, track, data,
-                                                  INNER_STEPS, TOL, gram_sample=0)
+    out["pixel_space_form"] = compare_with_oracle(pix, kept, INNER_STEPS, TOL,
+                                                  with_gram=False)
     pix.close()
     out["oracle"] = "FP64 CPU oracle, same host data (d_s = F_s (H c_true) + noise)"
     return out
 
 
-def compare_with_oracle(ctx, of, track, data, steps, tol, gram_sample=64):
+def compare_with_oracle(ctx, ref, steps, tol, with_gram=True):
     """Push the oracle's pulses through ctx and compare its state with the
-    oracle's: sampled Gram entries (when gram_sample > 0), b, the
+    oracle's arrays (oracle_state): sampled Gram entries, b, the
     coefficients with their support difference, lambda_n and L_n."""
+    track, data = ref["track"], ref["data"]
     used = []
     for s in range(track.shape[0]):
         ctx.push_pulse(track[s], data[s])
         used.append(ctx.iterate(steps, tol))
     res = {"pulses": int(track.shape[0]), "steps_per_pulse_gpu": used}
-    if gram_sample > 0:
-        rng = np.random.default_rng(0)
-        cols = np.sort(rng.choice(of.m, gram_sample, replace=False))
-        rr, cc = np.meshgrid(cols, cols, indexing="ij")
-        g_gpu = ctx.gram_entries(rr.ravel(), cc.ravel())
-        g_orc = (of.s.gram.entries(rr.ravel(), cc.ravel()) if of.matrix_free
-                 else of.s.gram[rr.ravel(), cc.ravel()])
-        res["gram_sampled_entries"] = {**_errors(g_gpu, g_orc), "entries": int(g_orc.size)}
-    c_gpu, c_orc = ctx.coeffs(), of.s.c_hat
+    if with_gram:
+        g_gpu = ctx.gram_entries(ref["rows"], ref["cols"])
+        res["gram_sampled_entries"] = {**_errors(g_gpu, ref["gram_entries"]),
+                                       "entries": int(ref["gram_entries"].size)}
+    c_gpu, c_orc = ctx.coeffs(), ref["c_hat"]
     st = ctx.state()
     sup_gpu, sup_orc = np.abs(c_gpu) > 0, np.abs(c_orc) > 0
-    alpha = of.s.lam / of.s.lip
-    near = np.abs(np.abs(of.s.u) - alpha) <= 1e-3 * np.max(np.abs(of.s.u))
+    alpha = ref["lam"] / ref["lip"]
+    near = np.abs(np.abs(ref["u"]) - alpha) <= 1e-3 * np.max(np.abs(ref["u"]))
     diff = sup_gpu != sup_orc
     res.update({
-        "b": _errors(ctx.b(), of.s.b),
+        "b": _errors(ctx.b(), ref["b"]),
         "coefficients": {**_errors(c_gpu, c_orc),
                          "support_size_oracle": int(np.count_nonzero(sup_orc)),
                          "support_differences": int(np.count_nonzero(diff)),
                          "support_differences_outside_threshold_band":
                              int(np.count_nonzero(diff & ~near)),
                          "threshold_band": "||u_i| - lambda tau| <= 1e-3 max|u|"},
-        "lambda_rel_err": abs(st["lambda"] - of.s.lam) / of.s.lam,
-        "lipschitz_rel_err": abs(st["lipschitz"] - of.s.lip) / of.s.lip})
+        "lambda_rel_err": abs(st["lambda"] - ref["lam"]) / ref["lam"],
+        "lipschitz_rel_err": abs(st["lipschitz"] - ref["lip"]) / ref["lip"]})
+    if "oracle" in ref:
+        res["oracle"] = ref["oracle"]
     return res
 
 
