@@ -764,16 +764,18 @@ def run_forms(stream):
         ws = synth.batch_workloads(96)
         tracks = [synth.workload_track(x) for x in ws]
         rng = np.random.default_rng(0)
+        datas = [[rng.standard_normal(x.n_freq) + 1j * rng.standard_normal(x.n_freq)
+                  for x in ws] for _ in range(7)]
+        first = {}  # every scene's coefficients after the first pulse
         for prec, pulses in (("split_bf16", 6), ("fp32", 6), ("fp64", 1)):
             cfgs = [osar.make_config(x.nx, x.ny, x.n_freq, x.f_lo_hz, x.f_hi_hz,
                                      precision=prec) for x in ws]
             b = osar.OsarBatch(cfgs, stream=stream.cuda_stream)
             seg = b.autotune()
             tuning = b.tuning()
-            datas = [[rng.standard_normal(x.n_freq) + 1j * rng.standard_normal(x.n_freq)
-                      for x in ws] for _ in range(pulses + 1)]
             b.push([1] * len(ws), np.stack([t[0] for t in tracks]), datas[0])
             b.iterate(20, 0.0, want_counts=False)
+            first[prec] = [b.coeffs(q) for q in range(len(ws))]
 
             def runb(bb=b, dd=datas):
                 for s in range(1, pulses + 1):
@@ -791,6 +793,13 @@ def run_forms(stream):
             for prec in ("split_bf16", "fp32"):
                 out[f"c4_batch96_{prec}"]["speedup_vs_fp64"] = round(
                     out[f"c4_batch96_{prec}"]["scene_pulses_per_s"] / base, 1)
+                # the accuracy that speed-up comes at: each scene's
+                # coefficients after the first pulse (20 steps) against the
+                # FP64 batch's (which meets the oracle to 1e-7)
+                errs = [float(np.linalg.norm(a - r) / max(np.linalg.norm(r), 1e-300))
+                        for a, r in zip(first[prec], first["fp64"])]
+                out[f"c4_batch96_{prec}"]["rel_err_vs_fp64_first_pulse"] = {
+                    "max_over_scenes": max(errs), "median": float(np.median(errs))}
         # 256 x 256 large online form, split-BF16, 10 steps per pulse
         w = wl["c5_256x256_split_bf16"]
         ctx = _pixel_ctx(w, "split_bf16", stream)
