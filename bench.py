@@ -70,6 +70,10 @@ def parse():
                     help="1: each pulse's Gram update runs on the side stream "
                          "beside its power steps and burst, which add the "
                          "pulse's block term to G_{n-1} x")
+    ap.add_argument("--pixel-gram", action="store_true",
+                    help="dictionary workloads: run the pixel-space Gram form "
+                         "(P_n, N x N) instead of the stored M x M Gram (for "
+                         "profiler captures of its dictionary products)")
     ap.add_argument("--gram-superblock", type=int, default=0,
                     help="Gram update tile order: super-blocks of this many "
                          "blocks (0: the library's 32)")
@@ -226,7 +230,8 @@ def workload(name="c2"):
 
 
 def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
-             fuse=True, defer=False, power_gram=True, gram_superblock=0):
+             fuse=True, defer=False, power_gram=True, gram_superblock=0,
+             pixel_gram=False):
     from paper_2603_08582_gb300 import osar
     gauss = w.dictionary == "gaussian"
     cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
@@ -240,7 +245,8 @@ def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
                            defer_gram=(defer and overlap and gauss
                                        and precision == "split_bf16"),
                            fuse_power_gram=power_gram,
-                           gram_superblock=gram_superblock)
+                           gram_superblock=gram_superblock,
+                           pixel_gram=pixel_gram and gauss)
     return osar.Osar(cfg)
 
 
@@ -278,8 +284,11 @@ def run_ours(args):
               tc_pairs=args.tc_pairs, fuse=not args.no_fuse,
               defer=bool(args.defer_gram) and not args.no_overlap,
               power_gram=bool(args.fuse_power_gram),
-              gram_superblock=args.gram_superblock)
+              gram_superblock=args.gram_superblock,
+              pixel_gram=args.pixel_gram)
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
+    # the order of the stored Gram: M, or N in the pixel-space form
+    gdim = w.n_pixels if args.pixel_gram and w.dictionary == "gaussian" else w.m_atoms
     # power steps per pulse that are Gram passes of their own
     power_passes = POWER_ITERS - (1 if ov["power_gram"] and not ov["defer"] else 0)
     total = W + K + 1
@@ -322,7 +331,7 @@ def run_ours(args):
         # the same pass with the GPU to itself (Gram applies after the timed
         # region, nothing running beside them)
         ctx.profile_reset()
-        xs = np.random.default_rng(0).standard_normal(w.m_atoms).astype(np.complex128)
+        xs = np.random.default_rng(0).standard_normal(gdim).astype(np.complex128)
         for _ in range(8):
             ctx.gram_apply(xs)
         mv_alone = ctx.profile_read("matvec")
@@ -386,7 +395,7 @@ def run_ours(args):
     e2e_value = whole_job_rate(K, world, e2e_s)
 
     peaks, peak_src = measured_peaks()
-    nblk = ctx_blocks(w.m_atoms)
+    nblk = ctx_blocks(gdim)
     gram_bytes = nblk * 128 * 128 * 8
     mv_n, mv_ms = prof["matvec"]
     # launches skipped after the stop rule held return at once: average over
