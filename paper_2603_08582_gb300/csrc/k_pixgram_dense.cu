@@ -27,7 +27,7 @@ namespace {
 
 constexpr int PD_THREADS = 256;
 constexpr int PD_FWD_PIX = PD_THREADS * 8;   // pixels of a forward CTA (8 a thread)
-constexpr int PD_FWD_ATOMS = 256;            // atoms of a forward CTA
+constexpr int PD_FWD_ATOMS = 256;            // most atoms of a forward CTA
 constexpr int PD_ATOMS = 64;                 // atoms of an adjoint CTA (8 a warp)
 constexpr int PD_CHUNK = 2048;               // pixels of w staged at a time
 
@@ -89,20 +89,21 @@ struct DF64 {
   }
 };
 
-// u = D x, first as partial sums over chunks of PD_FWD_ATOMS atoms:
-// part[chunk][p] = sum over the chunk's atoms m (in order) of D[m][p] x_m.
+// u = D x, first as partial sums over chunks of `chunk` atoms (at most
+// PD_FWD_ATOMS; fewer for small scenes, so that the grid still fills the
+// GPU): part[c][p] = sum over chunk c's atoms m (in order) of D[m][p] x_m.
 // Padding atoms have zero rows and zero x.  gated: nothing once the stop
 // rule has been met.
 template <typename S, typename T>
 __global__ void __launch_bounds__(PD_THREADS)
-    k_pgd_forward(S d, int Mp, int Np, const double2* __restrict__ x,
+    k_pgd_forward(S d, int Mp, int Np, int chunk, const double2* __restrict__ x,
                   typename Vec<T>::T2* __restrict__ part,
                   const DevScalars* sc, int gated) {
   using T2 = typename Vec<T>::T2;
   if (gated && sc->converged) return;
   __shared__ T2 xs[PD_FWD_ATOMS];
-  const int a0 = blockIdx.y * PD_FWD_ATOMS;
-  const int na = min(PD_FWD_ATOMS, Mp - a0);
+  const int a0 = blockIdx.y * chunk;
+  const int na = min(chunk, Mp - a0);
   for (int i = threadIdx.x; i < PD_FWD_ATOMS; i += PD_THREADS) {
     T2 v;
     v.x = 0;
@@ -384,8 +385,18 @@ cudaError_t with_dict(const osar_ctx* ctx, F&& f) {
 
 }  // namespace
 
+// Atoms per forward CTA: the largest of 256, 128, 64, 32 that still gives
+// at least four CTAs per SM.
+int pgd_fwd_atoms(const osar_ctx* ctx) {
+  int a = PD_FWD_ATOMS;
+  const int64_t px_tiles = cdiv(ctx->Np, PD_FWD_PIX);
+  while (a > 32 && px_tiles * cdiv(ctx->pg->Mp, a) < 4 * (int64_t)ctx->sm_count)
+    a /= 2;
+  return a;
+}
+
 int pgd_chunks(const osar_ctx* ctx) {
-  return (int)cdiv(ctx->pg->Mp, PD_FWD_ATOMS);
+  return (int)cdiv(ctx->pg->Mp, pgd_fwd_atoms(ctx));
 }
 
 int pgd_adjoint_chunks(const osar_ctx* ctx) {
@@ -403,7 +414,7 @@ cudaError_t pgd_forward(osar_ctx* ctx, const double2* x, int gated) {
     using T2 = typename Vec<T>::T2;
     const dim3 grid(cdiv(ctx->Np, PD_FWD_PIX), (unsigned)nch);
     k_pgd_forward<decltype(d), T><<<grid, PD_THREADS, 0, ctx->stream>>>(
-        d, g.Mp, ctx->Np, x, (T2*)g.upart, ctx->scal, gated);
+        d, g.Mp, ctx->Np, pgd_fwd_atoms(ctx), x, (T2*)g.upart, ctx->scal, gated);
     if (ctx->prec == OSAR_FP64)
       k_pgd_reduce<T, double2><<<cdiv(ctx->Np, 256), 256, 0, ctx->stream>>>(
           (const T2*)g.upart, nch, ctx->Np, (double2*)ctx->zt, ctx->scal, gated);
