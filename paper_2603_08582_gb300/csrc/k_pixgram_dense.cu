@@ -142,25 +142,42 @@ __global__ void __launch_bounds__(PD_THREADS)
   }
 }
 
-// u_p = sum of the chunk partials in chunk order, into the matvec's input
-// vector (working precision).
+// u_p = the chunk partials summed, into the matvec's input vector (working
+// precision).  A CTA takes 32 pixels with 8 threads each: thread group g
+// sums chunks g, g + 8, ... in order, then the 8 group sums are added in
+// group order (a fixed order, independent of the grid).
+constexpr int PD_RED_PIX = 32, PD_RED_GROUPS = 8;
+
 template <typename T, typename TW2>
-__global__ void k_pgd_reduce(const typename Vec<T>::T2* __restrict__ part,
-                             int nchunk, int Np, TW2* __restrict__ u,
-                             const DevScalars* sc, int gated) {
+__global__ void __launch_bounds__(PD_RED_PIX * PD_RED_GROUPS)
+    k_pgd_reduce(const typename Vec<T>::T2* __restrict__ part, int nchunk,
+                 int Np, TW2* __restrict__ u, const DevScalars* sc, int gated) {
   if (gated && sc->converged) return;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= Np) return;
+  __shared__ T rs[PD_RED_GROUPS][PD_RED_PIX], is[PD_RED_GROUPS][PD_RED_PIX];
+  const int px = threadIdx.x % PD_RED_PIX, grp = threadIdx.x / PD_RED_PIX;
+  const int p = blockIdx.x * PD_RED_PIX + px;
   T sr = 0, si = 0;
-  for (int k = 0; k < nchunk; ++k) {
-    const typename Vec<T>::T2 v = part[(int64_t)k * Np + p];
-    sr += v.x;
-    si += v.y;
+  if (p < Np)
+    for (int k = grp; k < nchunk; k += PD_RED_GROUPS) {
+      const typename Vec<T>::T2 v = part[(int64_t)k * Np + p];
+      sr += v.x;
+      si += v.y;
+    }
+  rs[grp][px] = sr;
+  is[grp][px] = si;
+  __syncthreads();
+  if (grp == 0 && p < Np) {
+    T tr = 0, ti = 0;
+#pragma unroll
+    for (int q = 0; q < PD_RED_GROUPS; ++q) {
+      tr += rs[q][px];
+      ti += is[q][px];
+    }
+    TW2 o;
+    o.x = tr;
+    o.y = ti;
+    u[p] = o;
   }
-  TW2 o;
-  o.x = sr;
-  o.y = si;
-  u[p] = o;
 }
 
 enum { PD_BVEC = 0, PD_POWER = 1, PD_FISTA = 2 };
@@ -415,11 +432,13 @@ cudaError_t pgd_forward(osar_ctx* ctx, const double2* x, int gated) {
     const dim3 grid(cdiv(ctx->Np, PD_FWD_PIX), (unsigned)nch);
     k_pgd_forward<decltype(d), T><<<grid, PD_THREADS, 0, ctx->stream>>>(
         d, g.Mp, ctx->Np, pgd_fwd_atoms(ctx), x, (T2*)g.upart, ctx->scal, gated);
+    const unsigned rg = cdiv(ctx->Np, PD_RED_PIX);
+    const int rt = PD_RED_PIX * PD_RED_GROUPS;
     if (ctx->prec == OSAR_FP64)
-      k_pgd_reduce<T, double2><<<cdiv(ctx->Np, 256), 256, 0, ctx->stream>>>(
+      k_pgd_reduce<T, double2><<<rg, rt, 0, ctx->stream>>>(
           (const T2*)g.upart, nch, ctx->Np, (double2*)ctx->zt, ctx->scal, gated);
     else
-      k_pgd_reduce<T, float2><<<cdiv(ctx->Np, 256), 256, 0, ctx->stream>>>(
+      k_pgd_reduce<T, float2><<<rg, rt, 0, ctx->stream>>>(
           (const T2*)g.upart, nch, ctx->Np, (float2*)ctx->zt, ctx->scal, gated);
     return cudaGetLastError();
   });
