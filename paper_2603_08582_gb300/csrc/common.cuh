@@ -153,6 +153,19 @@ __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 // Wait until every committed bulk group of this thread has completed.
+// 16-byte asynchronous global -> shared copy (no register is held while it
+// is in flight); the issuing thread completes its copies with
+// async_copy_wait_all, after which it may read them.
+__device__ __forceinline__ void async_copy16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+
+__device__ __forceinline__ void async_copy_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256)
     cbar[i] = make_double2(2.0 * dr, 2.0 * di);
     s += dr * dr + di * di;
   }
-  const double2 bs = block_sum(s, 0.0);
+  const double2 bs = block_sum(s, 0.0, blockDim.x / 32);
   if (threadIdx.x == 0) part[blockIdx.x] = bs;
   if (!last_block(&as->done, gridDim.x)) return;
   const double2 tot = sum_parts(part, gridDim.x);
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256)
     const double2 bb = bbar[i];
     bbar[i] = make_double2(bb.x + tau * ub.x, bb.y + tau * ub.y);
   }
-  const double2 s = block_sum(pa, pt);
+  const double2 s = block_sum(pa, pt, blockDim.x / 32);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   if (!last_block(&as->done, gridDim.x)) return;
   const double2 tot = sum_parts(part, gridDim.x);

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
     p0 = dr * dr + di * di;
     p1 = cr * cr + ci * ci;
   }
-  const double2 ps = block_sum(p0, p1);
+  const double2 ps = block_sum(p0, p1, BLK / 32);
   if (i == 0) part[blockIdx.x] = ps;
   if (!last_block(&sc[s].done, d.nb)) return;
   const double2 tot = sum_parts(part + d.item0, d.nb);
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
     p0 = vk.x * y.x + vk.y * y.y;
     p1 = y.x * y.x + y.y * y.y;
   }
-  const double2 ps = block_sum(p0, p1);
+  const double2 ps = block_sum(p0, p1, BLK / 32);
   if (i == 0) part[blockIdx.x] = ps;
   if (!last_block(&sc[s].done, d.nb)) return;
   const double2 tot = sum_parts(part + d.item0, d.nb);

@@ -57,7 +57,20 @@ __global__ void __launch_bounds__(FIN_THREADS, 2)
                      DevScalars* gs, int count_pass,
                      const float2* __restrict__ corr) {
   // sc: this solution's scalars; gs: the shared ones (tau, tol, passes)
-  if (sc->converged) return;
+  const int K = blockIdx.x, i = threadIdx.x, idx = K * BLK + i;
+  // The step's inputs z, b, c_prev go to shared memory by asynchronous
+  // copies issued first, so that their round trip overlaps the converged
+  // check and the partial gather instead of following them.
+  __shared__ double2 in[3][BLK];
+  if (i < BLK) {
+    async_copy16(&in[0][i], z + idx);
+    async_copy16(&in[1][i], b + idx);
+    async_copy16(&in[2][i], c + idx);
+  }
+  if (sc->converged) {
+    async_copy_wait_all();
+    return;
+  }
   __shared__ double sh[3];  // tau, alpha, beta
   if (threadIdx.x == 0) {
     const double t = sc->t, tau = gs->tau;
@@ -66,12 +79,12 @@ __global__ void __launch_bounds__(FIN_THREADS, 2)
     sh[1] = sc->lambda * tau;
     sh[2] = (t - 1.0) / t_next;
   }
-  const int K = blockIdx.x, i = threadIdx.x, idx = K * BLK + i;
   const double2 y = gather_row<T2, Acc>(segpart, tilepart, seg_begin, nb, K, corr);
   double p0 = 0.0, p1 = 0.0;
   if (i < BLK) {
     const double tau = sh[0], alpha = sh[1], beta = sh[2];
-    const double2 zk = z[idx], bk = b[idx], cprev = c[idx];
+    async_copy_wait_all();
+    const double2 zk = in[0][i], bk = in[1][i], cprev = in[2][i];
     const double ur = zk.x - tau * (y.x - bk.x);
     const double ui = zk.y - tau * (y.y - bk.y);
     const double keep = shrink_keep<T2>(ur * ur + ui * ui, alpha);
@@ -88,7 +101,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 2)
     p0 = dr * dr + di * di;
     p1 = cr * cr + ci * ci;
   }
-  const double2 s = block_sum(p0, p1);
+  const double2 s = block_sum(p0, p1, BLK / 32);
   if (i == 0) part[K] = s;
   if (!last_block(&sc->done, gridDim.x)) return;
   const double2 tot = sum_parts(part, nb);
@@ -164,7 +177,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
     p0 = vk.x * y.x + vk.y * y.y;
     p1 = y.x * y.x + y.y * y.y;
   }
-  const double2 s = block_sum(p0, p1);
+  const double2 s = block_sum(p0, p1, BLK / 32);
   if (i == 0) part[K] = s;
   if (!last_block(&sc->done, gridDim.x)) return;
   const double2 tot = sum_parts(part, nb);

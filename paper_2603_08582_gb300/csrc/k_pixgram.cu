@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(BLK)
     p0 = vk.x * y.x + vk.y * y.y;
     p1 = y.x * y.x + y.y * y.y;
   }
-  const double2 s = block_sum(p0, p1);
+  const double2 s = block_sum(p0, p1, BLK / 32);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   if (!last_block(&sc->done, gridDim.x)) return;
   const double2 tot = sum_parts(part, gridDim.x);
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(BLK)
     p0 = dr * dr + di * di;
     p1 = cr * cr + ci * ci;
   }
-  const double2 s = block_sum(p0, p1);
+  const double2 s = block_sum(p0, p1, BLK / 32);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   if (!last_block(&sc->done, gridDim.x)) return;
   const double2 tot = sum_parts(part, gridDim.x);

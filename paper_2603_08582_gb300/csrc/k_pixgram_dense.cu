@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(BLK)
       p0 = vk.x * y.x + vk.y * y.y;
       p1 = y.x * y.x + y.y * y.y;
     }
-    const double2 s = block_sum(p0, p1);
+    const double2 s = block_sum(p0, p1, blockDim.x / 32);
     if (threadIdx.x == 0) a.part[blockIdx.x] = s;
     if (!last_block(&a.sc->done, gridDim.x)) return;
     const double2 tot = sum_parts(a.part, gridDim.x);
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(BLK)
       p0 = dr * dr + di * di;
       p1 = cr * cr + ci * ci;
     }
-    const double2 s = block_sum(p0, p1);
+    const double2 s = block_sum(p0, p1, blockDim.x / 32);
     if (threadIdx.x == 0) a.part[blockIdx.x] = s;
     if (!last_block(&a.sc->done, gridDim.x)) return;
     const double2 tot = sum_parts(a.part, gridDim.x);

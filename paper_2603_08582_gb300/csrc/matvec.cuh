@@ -503,22 +503,30 @@ __device__ __forceinline__ double2 gather_row(const T2* __restrict__ segpart,
   return y;
 }
 
-// Sum (a, b) over all threads of the block; thread 0 gets the total.
-__device__ __forceinline__ double2 block_sum(double a, double b) {
+// Sum (a, b) over the threads of the block's first nw warps (every other
+// thread of the block holds zeros: the total is the block's); thread 0 gets
+// the total.  GB300 issues FP64 arithmetic at about 1/64 of its FP32 rate,
+// one pipe per SM for all its warps, so the 1024-thread finalizes reduce
+// only the 4 warps that hold their block's 128 coefficients: the tree over
+// all 32 warps took 5-7 us of a 29 us step finalize.
+__device__ __forceinline__ double2 block_sum(double a, double b, int nw) {
   __shared__ double2 red[32];
   __syncthreads();
+  const int w = threadIdx.x >> 5;
+  if (w < nw) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[w] = make_double2(a, b);
   }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(a, b);
   __syncthreads();
   double2 t = make_double2(0, 0);
   if (threadIdx.x == 0) {
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      t.x += red[w].x;
-      t.y += red[w].y;
+    for (int k = 0; k < nw; ++k) {
+      t.x += red[k].x;
+      t.y += red[k].y;
     }
   }
   return t;
@@ -547,7 +555,8 @@ __device__ __forceinline__ double2 sum_parts(const double2* part, int n) {
     a += v.x;
     b += v.y;
   }
-  return block_sum(a, b);
+  const int used = n < (int)blockDim.x ? n : (int)blockDim.x;
+  return block_sum(a, b, (used + 31) >> 5);
 }
 
 }  // namespace
