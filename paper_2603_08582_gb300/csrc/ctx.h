@@ -248,6 +248,7 @@ struct osar_ctx {
 
   // profiling
   bool prof_on = false;
+  uint32_t prof_mask = ~0u;  // kernel classes bracketed while prof_on
   std::vector<osar::ProfEvent> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[osar::KCL_COUNT] = {0};

@@ -919,7 +919,7 @@ cudaError_t settle_gram(osar_ctx* ctx) {
 
 void prof_begin(osar_ctx* ctx, int kind, ProfEvent* ev) {
   ev->kind = -1;
-  if (!ctx->prof_on) return;
+  if (!ctx->prof_on || !((ctx->prof_mask >> kind) & 1u)) return;
   for (int i = 0; i < 2; ++i) {
     cudaEvent_t x;
     if (!ctx->ev_pool.empty()) {
@@ -1400,6 +1400,14 @@ osar_status osar_poke_guard(osar_ctx* ctx, int32_t index) {
 osar_status osar_profile_enable(osar_ctx* ctx, int32_t on) {
   if (!ctx) return OSAR_E_INVALID;
   ctx->prof_on = on != 0;
+  return OSAR_OK;
+}
+
+osar_status osar_profile_select(osar_ctx* ctx, uint32_t mask) {
+  if (!ctx) return OSAR_E_INVALID;
+  if (mask >> KCL_COUNT)
+    return fail(ctx, OSAR_E_INVALID, "osar_profile_select: mask has bits past the last kernel class");
+  ctx->prof_mask = mask;
   return OSAR_OK;
 }
 

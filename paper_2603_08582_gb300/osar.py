@@ -43,6 +43,7 @@ EXPORTS = [
     "osar_probe_bounded_wait", "osar_check_guards", "osar_poke_guard",
     "osar_batch_check_guards",
     "osar_profile_enable",
+    "osar_profile_select",
     "osar_profile_read", "osar_profile_reset", "osar_profile_passes",
     "osar_launch_count",
     "osar_device_bytes", "osar_save", "osar_load", "osar_last_error",
@@ -142,6 +143,7 @@ def load_library(path: str = LIB_PATH):
         "osar_poke_guard": (I32, [P, I32]),
         "osar_batch_check_guards": (I32, [P, C.POINTER(I32)]),
         "osar_profile_enable": (I32, [P, I32]),
+        "osar_profile_select": (I32, [P, C.c_uint32]),
         "osar_profile_read": (I32, [P, I32, C.POINTER(C.c_int64), D]),
         "osar_profile_reset": (I32, [P]),
         "osar_profile_passes": (I32, [P, C.POINTER(C.c_int64)]),
@@ -484,6 +486,15 @@ class Osar:
         n = C.c_int64()
         self._check(self._lib.osar_profile_passes(self._h, C.byref(n)))
         return n.value
+
+    def profile_select(self, *kernels: str):
+        """Bracket only these kernel classes (names of KERNEL_CLASSES) while
+        profiling is on; no names selects every class."""
+        mask = 0
+        for k in kernels:
+            mask |= 1 << KERNEL_CLASSES[k]
+        self._check(self._lib.osar_profile_select(
+            self._h, mask if kernels else (1 << len(KERNEL_CLASSES)) - 1))
 
     def profile_read(self, kernel: str):
         n = C.c_int64()
