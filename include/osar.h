@@ -458,12 +458,18 @@ osar_status osar_poke_guard(osar_ctx* ctx, int32_t index);
    Phase and dictionary launches of an overlapped push are bracketed on the
    side stream, so their time includes sharing the GPU with the burst. */
 osar_status osar_profile_enable(osar_ctx* ctx, int32_t on);
-/* Restricts the bracketed classes to the set bits of mask (bit k = class k
-   above; the default is every class).  Each bracket is two event records
-   on the stream, about a microsecond of device time apiece between
-   launches, so a timing run that needs one class can leave the others
-   unbracketed.  OSAR_E_INVALID for bits past the last class. */
+/* Restricts the bracketed launches to the classes whose bits are set in
+   mask (bit k = class k above; the default is every class).  Each bracket
+   adds two event records to the stream between launches, which lengthens
+   a sequence of short launches measurably, so a timing run can bracket
+   only the classes it needs.  OSAR_E_INVALID for bits past the last
+   class. */
 osar_status osar_profile_select(osar_ctx* ctx, uint32_t mask);
+/* Brackets one launch in `every` of class `kernel` (the next one first,
+   and again after each osar_profile_reset; the default is 1, every
+   launch): the counters then hold that sample.  OSAR_E_INVALID for an
+   unknown class or every < 1. */
+osar_status osar_profile_sample(osar_ctx* ctx, int32_t kernel, int32_t every);
 osar_status osar_profile_read(osar_ctx* ctx, int32_t kernel,
                               int64_t* launches, double* total_ms);
 /* Clears the timing counters, the launch count and the pass count. */

@@ -249,6 +249,8 @@ struct osar_ctx {
   // profiling
   bool prof_on = false;
   uint32_t prof_mask = ~0u;  // kernel classes bracketed while prof_on
+  int32_t prof_every[osar::KCL_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // stride
+  int64_t prof_seq[osar::KCL_COUNT] = {0};  // launches seen per class
   std::vector<osar::ProfEvent> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[osar::KCL_COUNT] = {0};

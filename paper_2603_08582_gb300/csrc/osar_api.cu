@@ -920,6 +920,7 @@ cudaError_t settle_gram(osar_ctx* ctx) {
 void prof_begin(osar_ctx* ctx, int kind, ProfEvent* ev) {
   ev->kind = -1;
   if (!ctx->prof_on || !((ctx->prof_mask >> kind) & 1u)) return;
+  if (ctx->prof_seq[kind]++ % ctx->prof_every[kind] != 0) return;
   for (int i = 0; i < 2; ++i) {
     cudaEvent_t x;
     if (!ctx->ev_pool.empty()) {
@@ -1411,6 +1412,15 @@ osar_status osar_profile_select(osar_ctx* ctx, uint32_t mask) {
   return OSAR_OK;
 }
 
+osar_status osar_profile_sample(osar_ctx* ctx, int32_t kernel, int32_t every) {
+  if (!ctx) return OSAR_E_INVALID;
+  if (kernel < 0 || kernel >= KCL_COUNT || every < 1)
+    return fail(ctx, OSAR_E_INVALID, "osar_profile_sample: kernel class or every out of range");
+  ctx->prof_every[kernel] = every;
+  ctx->prof_seq[kernel] = 0;
+  return OSAR_OK;
+}
+
 static osar_status profile_collect(osar_ctx* ctx) {
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   for (auto& pe : ctx->prof_pending) {
@@ -1447,6 +1457,7 @@ osar_status osar_profile_reset(osar_ctx* ctx) {
   for (int k = 0; k < KCL_COUNT; ++k) {
     ctx->prof_ms[k] = 0.0;
     ctx->prof_launches[k] = 0;
+    ctx->prof_seq[k] = 0;
   }
   ctx->launches = 0;
   CK(ctx, cudaMemsetAsync(reinterpret_cast<char*>(ctx->scal) +

@@ -44,6 +44,7 @@ EXPORTS = [
     "osar_batch_check_guards",
     "osar_profile_enable",
     "osar_profile_select",
+    "osar_profile_sample",
     "osar_profile_read", "osar_profile_reset", "osar_profile_passes",
     "osar_launch_count",
     "osar_device_bytes", "osar_save", "osar_load", "osar_last_error",
@@ -144,6 +145,7 @@ def load_library(path: str = LIB_PATH):
         "osar_batch_check_guards": (I32, [P, C.POINTER(I32)]),
         "osar_profile_enable": (I32, [P, I32]),
         "osar_profile_select": (I32, [P, C.c_uint32]),
+        "osar_profile_sample": (I32, [P, I32, I32]),
         "osar_profile_read": (I32, [P, I32, C.POINTER(C.c_int64), D]),
         "osar_profile_reset": (I32, [P]),
         "osar_profile_passes": (I32, [P, C.POINTER(C.c_int64)]),
@@ -495,6 +497,10 @@ class Osar:
             mask |= 1 << KERNEL_CLASSES[k]
         self._check(self._lib.osar_profile_select(
             self._h, mask if kernels else (1 << len(KERNEL_CLASSES)) - 1))
+
+    def profile_sample(self, kernel: str, every: int):
+        """Bracket one launch in `every` of this class."""
+        self._check(self._lib.osar_profile_sample(self._h, KERNEL_CLASSES[kernel], every))
 
     def profile_read(self, kernel: str):
         n = C.c_int64()
