@@ -769,10 +769,18 @@ bool encode_planes(CUtensorMap* m, void* base, int cols, int rows, int planes,
 
 // Launch one persistent tcgen05 grid over p.n_tiles work items (tiles, or
 // tile pairs on CTA pairs) with at most grid_cap CTAs (0: one per SM).
+// Tiles are dealt round-robin (unit u takes tiles u, u + units, ...).  With
+// a capped grid (beside a burst) the unit count is rounded down to a
+// multiple of `group` (the dictionary's frequency tiles per atom block):
+// every unit then keeps one frequency tile, and the tiles that read the same
+// dictionary rows run in the same round on different units at about the
+// same time, so that most of those rows come from HBM once.  128 x 128 /
+// M = 32768, one-pass DRAM counters of the product alone: 34 pairs read
+// 6.5-6.7 GB, 32 pairs 5.4-5.7 GB, for a 4.3 GB dictionary.
 template <bool PAIR>
 cudaError_t launch_tc_grid(cudaStream_t st, int sm_count, int pair_limit,
                            const CUtensorMap& ma, const CUtensorMap& mb,
-                           const TcParams& p, int grid_cap) {
+                           const TcParams& p, int grid_cap, int group) {
   cudaError_t e = cudaFuncSetAttribute(
       k_tc_cgemm<PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       TcCfg<PAIR>::SMEM);
@@ -780,12 +788,14 @@ cudaError_t launch_tc_grid(cudaStream_t st, int sm_count, int pair_limit,
   const int cap = grid_cap > 0 && grid_cap < sm_count ? grid_cap : sm_count;
   if (p.n_tiles <= 0) return cudaSuccess;
   if (!PAIR) {
-    const int grid = p.n_tiles < cap ? p.n_tiles : cap;
+    int grid = p.n_tiles < cap ? p.n_tiles : cap;
+    if (grid_cap > 0 && group > 1 && grid > group) grid -= grid % group;
     k_tc_cgemm<PAIR><<<grid, TC_THREADS, TcCfg<PAIR>::SMEM, st>>>(ma, mb, p);
     return cudaGetLastError();
   }
   int pairs = std::min(p.n_tiles, std::max(1, cap / 2));
   if (pair_limit > 0) pairs = std::min(pairs, pair_limit);
+  if (grid_cap > 0 && group > 1 && pairs > group) pairs -= pairs % group;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(2 * pairs));
   cfg.blockDim = dim3(TC_THREADS);
@@ -831,14 +841,14 @@ int pair_limit(osar_ctx* ctx) {
 
 cudaError_t launch_tc(osar_ctx* ctx, const CUtensorMap& ma,
                       const CUtensorMap& mb, const TcParams& p, int kind,
-                      bool pairs, int grid_cap) {
+                      bool pairs, int grid_cap, int group) {
   ProfEvent ev;
   prof_begin(ctx, kind, &ev);
   const cudaError_t e =
       pairs ? launch_tc_grid<true>(ctx->stream, ctx->sm_count, pair_limit(ctx),
-                                   ma, mb, p, grid_cap)
+                                   ma, mb, p, grid_cap, group)
             : launch_tc_grid<false>(ctx->stream, ctx->sm_count, 0, ma, mb, p,
-                                    grid_cap);
+                                    grid_cap, group);
   prof_end(ctx, &ev);
   ctx->launches++;
   return e != cudaSuccess ? e : cudaGetLastError();
@@ -891,7 +901,7 @@ cudaError_t launch_dict_tc(osar_ctx* ctx, int grid_cap) {
   p.err = &ctx->scal->error;
   cudaError_t e = launch_tc(ctx, ctx->map_d_rows1,
                             pairs ? ctx->map_f_rows1 : ctx->map_f_rows2, p,
-                            KCL_DICT, pairs, grid_cap);
+                            KCL_DICT, pairs, grid_cap, ctx->Kp / BLK);
   if (e != cudaSuccess) return e;
   const int64_t groups = (int64_t)ctx->Mp * ctx->Kp / 8;
   int64_t rg = (groups + 255) / 256;
@@ -933,7 +943,7 @@ cudaError_t launch_gram_tc(osar_ctx* ctx, void* dst_hi, __nv_bfloat162* dst_lo,
   }
   return launch_tc(ctx, ctx->map_a_rows1,
                    pairs ? ctx->map_a_rows1 : ctx->map_a_rows2, p, KCL_GRAM,
-                   pairs, grid_cap);
+                   pairs, grid_cap, 1);
 }
 
 bool encode_plane_map(CUtensorMap* m, void* base, int cols, int rows,
@@ -961,7 +971,7 @@ cudaError_t launch_gram_tc_tiles(cudaStream_t st, int sm_count,
   p.gs_hi = g_hi;
   p.gs_lo = g_lo;
   p.err = err;
-  return launch_tc_grid<false>(st, sm_count, 0, m1, m2, p, 0);
+  return launch_tc_grid<false>(st, sm_count, 0, m1, m2, p, 0, 1);
 }
 
 }  // namespace osar
