@@ -22,7 +22,7 @@
 #include <cmath>
 #include <vector>
 
-#include "matvec.cuh"
+#include "finalize.cuh"
 
 namespace osar {
 namespace {

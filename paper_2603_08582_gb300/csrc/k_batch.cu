@@ -5,7 +5,7 @@
 // Algorithm 1); only the indexing differs.  A scene whose `active` flag is
 // clear (no pulse in the last push) is skipped by every kernel.
 #include "batch.h"
-#include "matvec.cuh"
+#include "finalize.cuh"
 
 namespace osar {
 namespace {

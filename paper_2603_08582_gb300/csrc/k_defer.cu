@@ -13,7 +13,7 @@
 // per entry, Mp x Kp entries, in 16-byte loads) and runs its sums in a fixed
 // order; Kp <= 2048.
 #include "ctx.h"
-#include "matvec.cuh"
+#include "finalize.cuh"
 
 namespace osar {
 namespace {

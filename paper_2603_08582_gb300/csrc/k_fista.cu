@@ -31,7 +31,7 @@
 // scalars t, L, lambda) run in FP64.
 #include "ctx.h"
 
-#include "matvec.cuh"
+#include "finalize.cuh"
 #include "step.cuh"
 
 namespace osar {

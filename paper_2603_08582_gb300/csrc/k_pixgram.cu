@@ -16,7 +16,7 @@
 // summation.
 #include "ctx.h"
 
-#include "matvec.cuh"
+#include "finalize.cuh"
 #include "step.cuh"
 
 namespace osar {

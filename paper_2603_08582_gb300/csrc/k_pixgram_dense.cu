@@ -19,7 +19,7 @@
 // FP64 path, each in a fixed order (results do not depend on the grid).
 #include "ctx.h"
 
-#include "matvec.cuh"
+#include "finalize.cuh"
 #include "step.cuh"
 
 namespace osar {
