@@ -6,6 +6,7 @@
 // clear (no pulse in the last push) is skipped by every kernel.
 #include "batch.h"
 #include "finalize.cuh"
+#include "step.cuh"
 
 namespace osar {
 namespace {
@@ -271,19 +272,25 @@ __global__ void __launch_bounds__(FIN_THREADS)
   const int s = it.x, K = it.y;
   const SceneDesc& d = desc[s];
   if (!d.active || sc[s].converged) return;
+  // the scene's scalars once per CTA (FP64 square root and division: slow
+  // on GB300's FP64 pipe), visible after the gather's barrier
+  __shared__ double sh[3];  // tau, alpha, beta
+  if (threadIdx.x == 0) {
+    const double tau = sc[s].tau, t = sc[s].t;
+    const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    sh[0] = tau;
+    sh[1] = sc[s].lambda * tau;
+    sh[2] = (t - 1.0) / t_next;
+  }
   const double2 y = b_gather<T2, Acc>(segpart, tilepart, seg_begin, d, K);
   const int i = threadIdx.x, idx = d.row + K * BLK + i;
   double p0 = 0.0, p1 = 0.0;
   if (i < BLK) {
-    const double tau = sc[s].tau, lam = sc[s].lambda, t = sc[s].t;
-    const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    const double beta = (t - 1.0) / t_next;
+    const double tau = sh[0], alpha = sh[1], beta = sh[2];
     const double2 zk = z[idx], bk = b[idx], cprev = c[idx];
     const double ur = zk.x - tau * (y.x - bk.x);
     const double ui = zk.y - tau * (y.y - bk.y);
-    const double mag = hypot(ur, ui);
-    const double alpha = lam * tau;
-    const double keep = mag > alpha ? 1.0 - alpha / mag : 0.0;
+    const double keep = shrink_keep<T2>(ur * ur + ui * ui, alpha);
     const double cr = ur * keep, ci = ui * keep;
     const double2 zn = make_double2(cr + beta * (cr - cprev.x),
                                     ci + beta * (ci - cprev.y));

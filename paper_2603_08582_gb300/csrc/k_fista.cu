@@ -240,38 +240,50 @@ __global__ void __launch_bounds__(FIN_THREADS)
 
 // ------------------------------------------------------- data vector, lambda
 // The last CTA of a data-update grid sets lambda_n = rel * max_j |b_j| (or
-// the absolute value) and counts the pulse.
-__device__ __forceinline__ void lambda_tail(double local_max2, double* bmax,
-                                            DevScalars* sc, const LamSet& lam,
-                                            int relative) {
-  __shared__ double red[32];
-  double m = local_max2;
+// the absolute value) and counts the pulse.  Each thread brings the bit
+// pattern of its largest |b_j|^2 (0 if none): non-negative doubles order as
+// their bit patterns, so the maximum is taken with 64-bit integer compares
+// instead of FP64 ones, of which GB300 issues about 1/64 as many.
+__device__ __forceinline__ void lambda_tail(unsigned long long bits,
+                                            double* bmax, DevScalars* sc,
+                                            const LamSet& lam, int relative) {
+  __shared__ unsigned long long red[32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = v > bits ? v : bits;
+  }
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bits;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t = fmax(t, red[w2]);
-    bmax[blockIdx.x] = t;
+    unsigned long long t = 0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t = red[w2] > t ? red[w2] : t;
+    bmax[blockIdx.x] = __longlong_as_double((long long)t);
   }
   if (!last_block(&sc->done, gridDim.x)) return;
-  double mx = 0.0;
-  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
-    mx = fmax(mx, __ldcg(bmax + k));
+  unsigned long long mx = 0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+    const unsigned long long v =
+        (unsigned long long)__double_as_longlong(__ldcg(bmax + k));
+    mx = v > mx ? v : mx;
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = v > mx ? v : mx;
+  }
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t = fmax(t, red[w2]);
+    unsigned long long t = 0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t = red[w2] > t ? red[w2] : t;
+    const double m2 = __longlong_as_double((long long)t);
     // every solution of the lambda path: lambda_n = factor x ||b_n||_inf
     // (Eq. 11's lambda, relative) or the absolute value
     for (int l = 0; l < lam.n; ++l)
-      sc[l].lambda = relative ? lam.v[l] * sqrt(t) : lam.v[l];
+      sc[l].lambda = relative ? lam.v[l] * sqrt(m2) : lam.v[l];
     sc->n += 1;
     sc->done = 0;
   }
@@ -286,7 +298,7 @@ __global__ void __launch_bounds__(256)
                           int relative) {
   const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  double m2 = 0.0;
+  unsigned long long m2b = 0;
   if (j < Mp) {
     const T2* row = A + (int64_t)j * Kp;
     double sr = 0.0, si = 0.0;
@@ -305,57 +317,72 @@ __global__ void __launch_bounds__(256)
       const double2 bj = b[j];
       const double2 nb2 = make_double2(bj.x + sr, bj.y + si);
       b[j] = nb2;
-      m2 = nb2.x * nb2.x + nb2.y * nb2.y;
+      m2b = (unsigned long long)__double_as_longlong(nb2.x * nb2.x + nb2.y * nb2.y);
     }
   }
-  lambda_tail(m2, bmax, sc, lam, relative);
+  lambda_tail(m2b, bmax, sc, lam, relative);
 }
 
 // Split-BF16 planes: A = (re_hi + re_lo) + i (im_hi + im_lo), FP32 products
-// and sums (8 entries per lane per load), one FP64 add into b_j per atom.
-__global__ void __launch_bounds__(256)
+// and sums.  A CTA takes DU_ATOMS consecutive atoms: each warp forms the
+// dot products of DU_ATOMS / DU_WARPS of them (8 entries per lane per load,
+// one xor tree per atom) into shared memory, then one lane per atom adds the
+// sum into b_j in FP64 and forms |b_j|^2.  One warp instruction of that FP64
+// tail covers 32 atoms; issued by one lane per warp and atom, the tail and
+// the lambda reduction's FP64 compares held the kernel at 72 us for the
+// 134 MB of planes of the 128 x 128 workload.
+constexpr int DU_WARPS = 16, DU_ATOMS = 128;
+__global__ void __launch_bounds__(DU_WARPS * 32)
     k_data_update_planes(const __nv_bfloat16* __restrict__ Ap, int Mp, int Kp,
                          const float2* __restrict__ d, double2* __restrict__ b,
                          double* bmax, DevScalars* sc, LamSet lam,
                          int relative) {
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  double m2 = 0.0;
-  if (j < Mp) {
-    const int64_t plane = (int64_t)Mp * Kp;
-    const __nv_bfloat16* rh = Ap + (int64_t)j * Kp;
+  __shared__ float2 sums[DU_ATOMS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = blockIdx.x * DU_ATOMS;
+  const int64_t plane = (int64_t)Mp * Kp;
+  for (int a = warp; a < DU_ATOMS; a += DU_WARPS) {
+    const int j = j0 + a;
     float sr = 0.f, si = 0.f;
-    for (int m0 = lane * 8; m0 < Kp; m0 += 256) {
-      const uint4 vrh = *reinterpret_cast<const uint4*>(rh + m0);
-      const uint4 vih = *reinterpret_cast<const uint4*>(rh + plane + m0);
-      const uint4 vrl = *reinterpret_cast<const uint4*>(rh + 3 * plane + m0);
-      const uint4 vil = *reinterpret_cast<const uint4*>(rh + 4 * plane + m0);
-      const __nv_bfloat16* prh = reinterpret_cast<const __nv_bfloat16*>(&vrh);
-      const __nv_bfloat16* pih = reinterpret_cast<const __nv_bfloat16*>(&vih);
-      const __nv_bfloat16* prl = reinterpret_cast<const __nv_bfloat16*>(&vrl);
-      const __nv_bfloat16* pil = reinterpret_cast<const __nv_bfloat16*>(&vil);
+    if (j < Mp) {
+      const __nv_bfloat16* rh = Ap + (int64_t)j * Kp;
+      for (int m0 = lane * 8; m0 < Kp; m0 += 256) {
+        const uint4 vrh = *reinterpret_cast<const uint4*>(rh + m0);
+        const uint4 vih = *reinterpret_cast<const uint4*>(rh + plane + m0);
+        const uint4 vrl = *reinterpret_cast<const uint4*>(rh + 3 * plane + m0);
+        const uint4 vil = *reinterpret_cast<const uint4*>(rh + 4 * plane + m0);
+        const __nv_bfloat16* prh = reinterpret_cast<const __nv_bfloat16*>(&vrh);
+        const __nv_bfloat16* pih = reinterpret_cast<const __nv_bfloat16*>(&vih);
+        const __nv_bfloat16* prl = reinterpret_cast<const __nv_bfloat16*>(&vrl);
+        const __nv_bfloat16* pil = reinterpret_cast<const __nv_bfloat16*>(&vil);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float ar = __bfloat162float(prh[q]) + __bfloat162float(prl[q]);
-        const float ai = __bfloat162float(pih[q]) + __bfloat162float(pil[q]);
-        const float2 dm = d[m0 + q];
-        sr = fmaf(ar, dm.x, fmaf(ai, dm.y, sr));
-        si = fmaf(ar, dm.y, fmaf(-ai, dm.x, si));
+        for (int q = 0; q < 8; ++q) {
+          const float ar = __bfloat162float(prh[q]) + __bfloat162float(prl[q]);
+          const float ai = __bfloat162float(pih[q]) + __bfloat162float(pil[q]);
+          const float2 dm = d[m0 + q];
+          sr = fmaf(ar, dm.x, fmaf(ai, dm.y, sr));
+          si = fmaf(ar, dm.y, fmaf(-ai, dm.x, si));
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_xor_sync(0xffffffffu, sr, o);
-      si += __shfl_xor_sync(0xffffffffu, si, o);
-    }
-    if (lane == 0) {
-      const double2 bj = b[j];
-      const double2 nb2 = make_double2(bj.x + (double)sr, bj.y + (double)si);
-      b[j] = nb2;
-      m2 = nb2.x * nb2.x + nb2.y * nb2.y;
-    }
+    if (lane == 0) sums[a] = make_float2(sr, si);
   }
-  lambda_tail(m2, bmax, sc, lam, relative);
+  __syncthreads();
+  unsigned long long m2b = 0;
+  const int j = j0 + (int)threadIdx.x;
+  if (threadIdx.x < DU_ATOMS && j < Mp) {
+    const float2 s = sums[threadIdx.x];
+    const double2 bj = b[j];
+    const double2 nb2 = make_double2(bj.x + (double)s.x, bj.y + (double)s.y);
+    b[j] = nb2;
+    m2b = (unsigned long long)__double_as_longlong(nb2.x * nb2.x + nb2.y * nb2.y);
+  }
+  lambda_tail(m2b, bmax, sc, lam, relative);
 }
 
 __global__ void k_stage_data(const double2* __restrict__ d,
@@ -583,7 +610,8 @@ cudaError_t launch_data_update(osar_ctx* ctx) {
   if (ctx->prec == OSAR_SPLIT_BF16) {
     k_stage_data<<<(unsigned)((ctx->Kp + 255) / 256), 256, 0, ctx->stream>>>(
         ctx->d_dev, ctx->d32, ctx->Kp);
-    k_data_update_planes<<<g, 256, 0, ctx->stream>>>(
+    k_data_update_planes<<<(unsigned)((ctx->Mp + DU_ATOMS - 1) / DU_ATOMS),
+                           DU_WARPS * 32, 0, ctx->stream>>>(
         ctx->Apl, ctx->Mp, ctx->Kp, ctx->d32, ctx->b, ctx->bmax, ctx->scal,
         lam, rel);
     ctx->launches++;
