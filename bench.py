@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--tc-pairs", type=int, default=3,
                     help="tensor-core products on SM pairs: bit 0 dictionary "
                          "product, bit 1 Gram update (0: one SM per tile)")
+    ap.add_argument("--gram-ahead", type=int, choices=[0, 1, 2], default=1,
+                    help="the Gram update beside the previous burst into a second "
+                         "Gram buffer: 0 never, 1 when the library's model expects "
+                         "it to pay (default), 2 always")
     ap.add_argument("--prof-every", type=int, default=1,
                     help="bracket one matvec launch in this many with CUDA events "
                          "in the timed region (a stride that shares a factor with "
@@ -235,7 +239,7 @@ def workload(name="c2"):
 
 def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
              fuse=True, defer=False, power_gram=True, gram_superblock=0,
-             pixel_gram=False):
+             pixel_gram=False, gram_ahead=0):
     from paper_2603_08582_gb300 import osar
     gauss = w.dictionary == "gaussian"
     cfg = osar.make_config(w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz,
@@ -250,7 +254,10 @@ def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
                                        and precision == "split_bf16"),
                            fuse_power_gram=power_gram,
                            gram_superblock=gram_superblock,
-                           pixel_gram=pixel_gram and gauss)
+                           pixel_gram=pixel_gram and gauss,
+                           gram_ahead=(gram_ahead if gauss and overlap and not defer
+                                       and not pixel_gram and precision == "split_bf16"
+                                       else 0))
     return osar.Osar(cfg)
 
 
@@ -289,7 +296,7 @@ def run_ours(args):
               defer=bool(args.defer_gram) and not args.no_overlap,
               power_gram=bool(args.fuse_power_gram),
               gram_superblock=args.gram_superblock,
-              pixel_gram=args.pixel_gram)
+              pixel_gram=args.pixel_gram, gram_ahead=args.gram_ahead)
     ctx = make_ctx(w, "split_bf16", stream.cuda_stream, **ov)
     # the order of the stored Gram: M, or N in the pixel-space form
     gdim = w.n_pixels if args.pixel_gram and w.dictionary == "gaussian" else w.m_atoms
@@ -339,6 +346,7 @@ def run_ours(args):
         launches = ctx.launch_count() - launches0
         prof = {k: ctx.profile_read(k) for k in osar.KERNEL_CLASSES}
         passes = ctx.profile_passes()
+        pushes_ahead, ahead_sms = ctx.profile_ahead(with_grid=True)
         # the same pass with the GPU to itself (Gram applies after the timed
         # region, nothing running beside them)
         ctx.profile_reset()
@@ -512,6 +520,9 @@ def run_ours(args):
                    "fused_first_step": not args.no_fuse,
                    "power_step_in_gram_update": bool(args.fuse_power_gram) and not ov["defer"],
                    "deferred_gram_update": bool(ov["defer"]),
+                   "gram_ahead": {0: "off", 1: "model", 2: "always"}[args.gram_ahead],
+                   "pushes_with_gram_ahead": f"{pushes_ahead} of {K}",
+                   "gram_ahead_side_sms": ahead_sms,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (packed Gram 4.3 GB streamed per step)"},
         "clocks": clocks,

@@ -206,6 +206,22 @@ typedef struct {
      the same time share operand rows in L2; 0 = 32.  Any order gives the
      same results (each output block is one tile's).  In [0, 64]. */
   int32_t gram_superblock;
+  /* SPLIT_BF16 with a dictionary, overlap_synthesis = 1, one lambda,
+     defer_gram = 0 and pixel_gram = 0.  The Gram update of Eqs. 12-13 run
+     ahead: a push queues the pulse's forward block A_n and
+     G_n = G_{n-1} + A_n^H A_n on the side stream, into a second Gram
+     buffer, so that both run beside the previous pulse's burst (which still
+     reads G_{n-1}); cuda_stream then waits for G_n, the buffers swap, and
+     the data update, power steps and burst follow as usual.  The update's
+     tensor work then overlaps the bandwidth-bound Gram passes instead of
+     running between bursts.  1: a model of the last bursts' length against
+     the tensor work decides per push between this and the in-order
+     schedule (the forward block beside the burst, the update after it on
+     cuda_stream), so short bursts keep the in-order one; 2: always ahead
+     (a push while cuda_stream is being captured still runs in order).
+     Every result is bitwise that of 0.  Needs a second Gram in device
+     memory.  0 (default): in order. */
+  int32_t gram_ahead;
 } osar_config;
 
 /* Fill *cfg with defaults: 32 x 32 grid, 1 m pixels, 128 frequencies over
@@ -214,7 +230,7 @@ typedef struct {
    overlap_synthesis = 1, synth_ctas = 0 (automatic), tc_pairs = 3
    (both tensor-core products on SM pairs), fuse_first_step = 1,
    n_lambdas = 1, defer_gram = 0, guard_bytes = 0, fuse_power_gram = 1,
-   pixel_gram = 0, gram_superblock = 0 (32). */
+   pixel_gram = 0, gram_superblock = 0 (32), gram_ahead = 0. */
 void osar_config_default(osar_config* cfg);
 
 /* Create a context for the problem of Sec. III-C: the online reconstruction
@@ -419,6 +435,12 @@ osar_status osar_unroll_grad(osar_ctx* ctx, int32_t steps, int32_t ckpt_every,
    while the pulses arrive.  Errors: OSAR_E_INVALID. */
 osar_status osar_set_lambda(osar_ctx* ctx, int32_t l, double lambda);
 
+/* The gram_ahead schedule (see osar_config) from the next push on: 0 in
+   order, 1 decided per push by the model, 2 ahead.  Results do not depend
+   on it.  OSAR_E_STATE when the context was created with gram_ahead = 0
+   (no second Gram buffer), OSAR_E_INVALID for another mode. */
+osar_status osar_set_gram_ahead(osar_ctx* ctx, int32_t mode);
+
 /* Wait for all work queued on the context's stream (and on its side
    stream, see overlap_synthesis). */
 osar_status osar_synchronize(osar_ctx* ctx);
@@ -480,6 +502,13 @@ osar_status osar_profile_reset(osar_ctx* ctx);
    rule held launch a matvec that returns at once and are not counted).
    Synchronises.  No paper counterpart: instrumentation for the roofline. */
 osar_status osar_profile_passes(osar_ctx* ctx, int64_t* passes);
+
+/* Pushes since the last osar_profile_reset whose Gram update ran ahead on
+   the side stream (gram_ahead); the others ran in order.  *last_grid
+   (nullable) gets the side stream's SM count of the last such push.
+   Host-side, no synchronisation. */
+osar_status osar_profile_ahead(const osar_ctx* ctx, int64_t* pushes,
+                               int32_t* last_grid);
 
 /* Total library kernel launches issued on this context since creation
    (or since the last reset); no synchronisation. */

@@ -202,6 +202,10 @@ struct osar_ctx {
   CUtensorMap map_alt_rows1;           // Apl_alt, box (KC, 128, 1)
   CUtensorMap map_alt_rows2;           // Apl_alt, box (KC, 128, 2)
   cudaEvent_t ev_gram = nullptr;       // side: the pending Gram update done
+  // gram_ahead: main stream past the last push's power steps (their reads of
+  // the Gram, of v and of the fused power step's partials are done)
+  cudaEvent_t ev_steps = nullptr;
+  bool steps_stale = false;            // ev_steps predates a captured push
   cudaEvent_t ev_mark[2] = {};         // main: all work before push n (n % 2)
   bool gram_pending = false;           // g_hi holds G_{n-1}, gn_hi gets G_n
   float2* corr = nullptr;              // A_n^H A_n x per partial set (2 x Mp)
@@ -244,6 +248,8 @@ struct osar_ctx {
   int n = 0;
   bool fresh = true;
   int64_t launches = 0;
+  int64_t pushes_ahead = 0;     // pushes whose Gram update ran ahead (gram_ahead)
+  int32_t ahead_grid_last = 0;  // side-stream SMs of the last such push
   int64_t dev_bytes = 0;
 
   // profiling

@@ -90,7 +90,7 @@ void free_all(osar_ctx* ctx) {
   for (int i = 0; i < RING; ++i)
     if (ctx->ring_ev[i]) cudaEventDestroy(ctx->ring_ev[i]);
   if (ctx->h_iters) cudaFreeHost(ctx->h_iters);
-  for (cudaEvent_t ev : {ctx->ev_free, ctx->ev_synth, ctx->ev_gram,
+  for (cudaEvent_t ev : {ctx->ev_free, ctx->ev_synth, ctx->ev_gram, ctx->ev_steps,
                          ctx->ev_mark[0], ctx->ev_mark[1]})
     if (ev) cudaEventDestroy(ev);
   for (cudaEvent_t ev : ctx->ev_iters)
@@ -196,6 +196,13 @@ osar_status validate(const osar_config* c, std::string* why) {
        !c->overlap_synthesis || c->n_lambdas != 1 || c->n_freq > 2048))
     return *why = "defer_gram needs SPLIT_BF16, a dictionary, overlap_synthesis, "
                   "one lambda and n_freq <= 2048", OSAR_E_INVALID;
+  if (c->gram_ahead < 0 || c->gram_ahead > 2)
+    return *why = "gram_ahead must be 0, 1 or 2", OSAR_E_INVALID;
+  if (c->gram_ahead &&
+      (c->precision != OSAR_SPLIT_BF16 || c->dict_kind == OSAR_DICT_IDENTITY ||
+       !c->overlap_synthesis || c->n_lambdas != 1 || c->defer_gram || c->pixel_gram))
+    return *why = "gram_ahead needs SPLIT_BF16, a dictionary, overlap_synthesis, "
+                  "one lambda, defer_gram = 0 and pixel_gram = 0", OSAR_E_INVALID;
   return OSAR_OK;
 }
 
@@ -439,6 +446,11 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
       AL(ctx->D, cplx * Mp * Np);
     }
   }
+  if (cfg->gram_ahead) {
+    // the second Gram buffer the update runs ahead into
+    AL(ctx->gn_hi, cplx * bb * ctx->nblk);
+    if (ctx->g_lo) AL(ctx->gn_lo, 4 * bb * ctx->nblk);
+  }
   if (cfg->defer_gram) {
     // second Gram and forward-block buffers, the pending block's term
     AL(ctx->gn_hi, cplx * bb * ctx->nblk);
@@ -523,6 +535,11 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
       e = cudaMallocHost((void**)&ctx->h_iters, sizeof(int32_t) * osar_ctx::ITERS_RING);
     if (cfg->defer_gram)
       for (cudaEvent_t* ev : {&ctx->ev_gram, &ctx->ev_mark[0], &ctx->ev_mark[1]}) {
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(*ev, ctx->stream);
+      }
+    if (cfg->gram_ahead)
+      for (cudaEvent_t* ev : {&ctx->ev_gram, &ctx->ev_steps}) {
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(*ev, ctx->stream);
       }
@@ -718,7 +735,8 @@ void refresh_iters_estimate(osar_ctx* ctx) {
 // with running the product alone on the whole GPU after the burst (0).  The
 // constants were measured on GB300 with the 128 x 128 workload (one SM:
 // 1.23e13 f/s alone, about 1.2e13 beside the burst).
-int synth_grid(const osar_ctx* ctx, bool main_idle) {
+int synth_grid(const osar_ctx* ctx, bool main_idle, double* t_model = nullptr) {
+  if (t_model) *t_model = 0.0;
   if (ctx->cfg.synth_ctas > 0) return std::min(ctx->cfg.synth_ctas, ctx->sm_count);
   // an edgelet block is a gather of phase rows, too short to overlap
   if (ctx->edgelet) return 0;
@@ -746,7 +764,55 @@ int synth_grid(const osar_ctx* ctx, bool main_idle) {
       best_g = g;
     }
   }
+  if (t_model) *t_model = best;
   return best_g;
+}
+
+// gram_ahead: SMs for the side stream when the pushed pulse's forward block
+// and its Gram update both run there beside the previous pulse's burst, or
+// 0 when the in-order schedule is expected to finish the pulse sooner.  The
+// in-order time is synth_grid's (the product beside the burst) plus the
+// update alone on the whole GPU; ahead, both products share g SMs (the
+// update at 1.05e13 f/s per SM, its measured rate) while the burst's passes
+// run on the rest and share HBM with the update's read-modify-write, the
+// model of defer_grid.  A burst too short to hide the update keeps the
+// in-order schedule.  gram_ahead = 2 always runs ahead (on synth_ctas SMs
+// when set; on half the GPU when nothing is in flight to model).
+int ahead_grid(const osar_ctx* ctx, bool main_idle) {
+  const int S = ctx->sm_count;
+  if (ctx->cfg.gram_ahead == 2) {
+    if (ctx->cfg.synth_ctas > 0) return std::min(ctx->cfg.synth_ctas, S);
+    if (main_idle) return S / 2;
+  } else if (main_idle) {
+    return 0;
+  }
+  constexpr double kDictRate = 1.2e13, kGramRate = 1.05e13;  // f/s per SM
+  constexpr double kHbm = 6.8e12, kSmBw = 105e9, kContention = 1.15;  // B/s
+  const double dict_f = ctx->edgelet ? 0.0 : 24.0 * ctx->Kp * (double)ctx->Np * ctx->Mp;
+  const double gram_f = 3.0 * 2.0 * BLK * 2.0 * BLK * 2.0 * ctx->Kp * (double)ctx->nblk;
+  const double bytes = (double)ctx->nblk * BLK * BLK * 8.0;
+  const double pass = bytes / kHbm;
+  const int power = ctx->n <= 1 ? ctx->cfg.power_iters_first : ctx->cfg.power_iters;
+  const double passes = power - (ctx->gp_col && power > 0 ? 1 : 0) + ctx->iters_est;
+  double t_inorder = 0.0;
+  if (synth_grid(ctx, false, &t_inorder) == 0 || t_inorder <= 0.0)
+    t_inorder = dict_f / (1.23e13 * S) + passes * pass;
+  t_inorder += gram_f / (kGramRate * S);
+  const double side = dict_f / kDictRate + gram_f / kGramRate;  // SM-seconds
+  double best = 0.0;
+  int best_g = 0;
+  for (int g = 16; g <= S - 16; g += 4) {
+    const double t_side = side / g;
+    const double t_pass = std::max(pass, bytes / ((S - g) * kSmBw)) * kContention;
+    const double beside = t_side / t_pass;  // passes made while the side works
+    const double t = passes <= beside ? t_side : t_side + (passes - beside) * pass;
+    if (best_g == 0 || t < best) {
+      best = t;
+      best_g = g;
+    }
+  }
+  if (ctx->cfg.gram_ahead == 2) return best_g;
+  return best < t_inorder ? best_g : 0;
 }
 
 // SMs for the side stream in the deferred mode, where this pulse's Gram
@@ -824,6 +890,60 @@ osar_status push_deferred(osar_ctx* ctx, const double gamma[3]) {
   return OSAR_OK;
 }
 
+// Push with the Gram update run ahead (gram_ahead) on `grid` SMs of the side
+// stream: the forward block A_n (after the main stream's last reader of the
+// block buffer, ev_free) and then G_n = G_{n-1} + A_n^H A_n into the second
+// Gram buffer (after the previous push's power steps, ev_steps: the last
+// main-stream reads of the Gram, of the power vector and of the fused power
+// step's partials that the update reads or writes); both run beside the
+// previous pulse's burst, which reads G_{n-1} in the other buffer.  The main
+// stream waits for G_n, takes the buffer that holds it, and runs the data
+// update and the power steps.  The arithmetic is the in-order push's.
+osar_status push_ahead(osar_ctx* ctx, const double gamma[3], int grid) {
+  cudaError_t e = cudaSuccess;
+  const bool early = ctx->dict && ctx->synth_side;
+  if (early) {
+    LaunchOn on(ctx, ctx->side);
+    e = synthesize_phase(ctx, gamma, grid);
+  }
+  if (ctx->free_stale && e == cudaSuccess)
+    e = cudaEventRecord(ctx->ev_free, ctx->stream);
+  ctx->free_stale = false;
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_free, 0);
+  if (e == cudaSuccess) {
+    LaunchOn on(ctx, ctx->side);
+    e = early ? synthesize_dict(ctx, grid) : synthesize(ctx, gamma, grid);
+  }
+  ctx->synth_side = true;
+  if (ctx->steps_stale && e == cudaSuccess) e = cudaEventRecord(ctx->ev_steps, ctx->stream);
+  ctx->steps_stale = false;
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_steps, 0);
+  if (e == cudaSuccess) {
+    LaunchOn on(ctx, ctx->side);
+    e = launch_gram_tc(ctx, ctx->gn_hi, ctx->gn_lo, grid, true);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_gram, ctx->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_gram, 0);
+  std::swap(ctx->g_hi, ctx->gn_hi);
+  std::swap(ctx->g_lo, ctx->gn_lo);
+  ctx->pushes_ahead++;
+  ctx->ahead_grid_last = grid;
+  if (e == cudaSuccess) e = launch_data_update(ctx);
+  // the data update was the block buffer's last main-stream reader
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_free, ctx->stream);
+  ctx->n += 1;
+  ctx->fresh = true;
+  ctx->first_ready = false;
+  if (e == cudaSuccess)
+    e = launch_power_steps(ctx,
+                           ctx->n == 1 ? ctx->cfg.power_iters_first
+                                       : ctx->cfg.power_iters,
+                           ctx->cfg.fuse_first_step != 0);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_steps, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_push_pulse");
+  return OSAR_OK;
+}
+
 // True when every launch on the main stream has finished (the caller waited
 // for the last burst before pushing).
 bool main_idle(osar_ctx* ctx) {
@@ -843,6 +963,10 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
   }
   if (ctx->side && !capturing(ctx->stream)) {
     refresh_iters_estimate(ctx);
+    if (ctx->cfg.gram_ahead) {
+      const int ahead = ahead_grid(ctx, idle);
+      if (ahead > 0) return push_ahead(ctx, gamma, ahead);
+    }
     const int grid = synth_grid(ctx, idle);
     if (grid > 0) {
       // With a dictionary the phase operand F is read only by the product:
@@ -897,6 +1021,13 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
                                      ctx->n == 1 ? ctx->cfg.power_iters_first
                                                  : ctx->cfg.power_iters,
                                      ctx->cfg.fuse_first_step != 0);
+  if (e == cudaSuccess && ctx->ev_steps) {
+    // a captured push leaves no usable ev_steps behind either
+    if (capturing(ctx->stream))
+      ctx->steps_stale = true;
+    else
+      e = cudaEventRecord(ctx->ev_steps, ctx->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_push_pulse");
   return OSAR_OK;
 }
@@ -1366,6 +1497,19 @@ osar_status osar_set_lambda(osar_ctx* ctx, int32_t l, double lambda) {
   return OSAR_OK;
 }
 
+osar_status osar_set_gram_ahead(osar_ctx* ctx, int32_t mode) {
+  osar::TraceRange trace_("osar_set_gram_ahead");
+  osar_status st = check_usable(ctx);
+  if (st != OSAR_OK) return st;
+  if (mode < 0 || mode > 2)
+    return fail(ctx, OSAR_E_INVALID, "osar_set_gram_ahead: mode must be 0, 1 or 2");
+  if (!ctx->gn_hi || !ctx->ev_steps)
+    return fail(ctx, OSAR_E_STATE,
+                "osar_set_gram_ahead: the context was created with gram_ahead = 0");
+  ctx->cfg.gram_ahead = mode;
+  return OSAR_OK;
+}
+
 osar_status osar_synchronize(osar_ctx* ctx) {
   osar::TraceRange trace_("osar_synchronize");
   osar_status st = check_usable(ctx);
@@ -1460,6 +1604,7 @@ osar_status osar_profile_reset(osar_ctx* ctx) {
     ctx->prof_seq[k] = 0;
   }
   ctx->launches = 0;
+  ctx->pushes_ahead = 0;
   CK(ctx, cudaMemsetAsync(reinterpret_cast<char*>(ctx->scal) +
                               offsetof(DevScalars, passes),
                           0, sizeof(unsigned long long), ctx->stream));
@@ -1474,6 +1619,14 @@ osar_status osar_profile_passes(osar_ctx* ctx, int64_t* passes) {
   st = read_scalars(ctx, &s);
   if (st != OSAR_OK) return st;
   *passes = (int64_t)s.passes;
+  return OSAR_OK;
+}
+
+osar_status osar_profile_ahead(const osar_ctx* ctx, int64_t* pushes,
+                               int32_t* last_grid) {
+  if (!ctx || !pushes) return OSAR_E_INVALID;
+  *pushes = ctx->pushes_ahead;
+  if (last_grid) *last_grid = ctx->ahead_grid_last;
   return OSAR_OK;
 }
 

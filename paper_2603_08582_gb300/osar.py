@@ -39,12 +39,13 @@ EXPORTS = [
     "osar_get_gram_entries", "osar_get_b", "osar_gram_apply",
     "osar_gram_apply_static",
     "osar_simulate_pulse", "osar_unroll_grad", "osar_synchronize",
-    "osar_get_metrics", "osar_set_lambda",
+    "osar_get_metrics", "osar_set_lambda", "osar_set_gram_ahead",
     "osar_probe_bounded_wait", "osar_check_guards", "osar_poke_guard",
     "osar_batch_check_guards",
     "osar_profile_enable",
     "osar_profile_select",
     "osar_profile_sample",
+    "osar_profile_ahead",
     "osar_profile_read", "osar_profile_reset", "osar_profile_passes",
     "osar_launch_count",
     "osar_device_bytes", "osar_save", "osar_load", "osar_last_error",
@@ -77,6 +78,7 @@ class OsarConfig(C.Structure):
         ("n_edgelet_angles", C.c_int32), ("edgelet_angles_deg", C.c_void_p),
         ("fuse_power_gram", C.c_int32), ("pixel_gram", C.c_int32),
         ("gram_superblock", C.c_int32),
+        ("gram_ahead", C.c_int32),
     ]
 
 
@@ -137,6 +139,7 @@ def load_library(path: str = LIB_PATH):
                                      C.c_double, D, D, D, D, D, D, D]),
         "osar_synchronize": (I32, [P]),
         "osar_set_lambda": (I32, [P, I32, C.c_double]),
+        "osar_set_gram_ahead": (I32, [P, I32]),
         "osar_get_metrics": (I32, [P, C.c_double, C.POINTER(I32), I32,
                                    C.POINTER(OsarMetrics)]),
         "osar_probe_bounded_wait": (I32, [P, C.c_int64]),
@@ -146,6 +149,7 @@ def load_library(path: str = LIB_PATH):
         "osar_profile_enable": (I32, [P, I32]),
         "osar_profile_select": (I32, [P, C.c_uint32]),
         "osar_profile_sample": (I32, [P, I32, I32]),
+        "osar_profile_ahead": (I32, [P, C.POINTER(C.c_int64), C.POINTER(I32)]),
         "osar_profile_read": (I32, [P, I32, C.POINTER(C.c_int64), D]),
         "osar_profile_reset": (I32, [P]),
         "osar_profile_passes": (I32, [P, C.POINTER(C.c_int64)]),
@@ -199,13 +203,15 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
                 synth_ctas=0, tc_pairs=3, fuse_first_step=True, lambdas=None,
                 defer_gram=False, guard_bytes=0, edgelet_lengths=None,
                 edgelet_angles=None, fuse_power_gram=True, pixel_gram=False,
-                gram_superblock=0):
+                gram_superblock=0, gram_ahead=0):
     """Build an osar_config.  dictionary: None (identity), "gaussian"
     (seeded Philox atoms, needs n_atoms), "edgelet" (binary edgelets of
     edgelet_lengths x edgelet_angles degrees at every pixel) or an N x M
     complex array.  pixel_gram (edgelets only): keep the pixel-basis Gram
     P_n = sum F^H F and apply G_n = H^H P_n H instead of storing G_n;
-    fuse_power_gram: form the pulse's first power step in the Gram update."""
+    fuse_power_gram: form the pulse's first power step in the Gram update;
+    gram_ahead: 0 in order, 1 the Gram update beside the previous burst when
+    a model expects that to pay, 2 always (into a second Gram buffer)."""
     cfg = default_config()
     cfg.nx, cfg.ny, cfg.pixel_m = int(nx), int(ny), float(pixel_m)
     cfg.n_freq, cfg.f_lo_hz, cfg.f_hi_hz = int(n_freq), float(f_lo_hz), float(f_hi_hz)
@@ -248,6 +254,7 @@ def make_config(nx, ny, n_freq, f_lo_hz, f_hi_hz, pixel_m=1.0,
     cfg.fuse_power_gram = 1 if fuse_power_gram else 0
     cfg.pixel_gram = 1 if pixel_gram else 0
     cfg.gram_superblock = int(gram_superblock)
+    cfg.gram_ahead = int(gram_ahead)
     if lambdas is not None and len(lambdas) > 1:
         # lambda path: one solution per value (relative or absolute like lam)
         lv = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
@@ -451,6 +458,10 @@ class Osar:
         ||b_n||_inf when the context is relative)."""
         self._check(self._lib.osar_set_lambda(self._h, int(l), float(lam)))
 
+    def set_gram_ahead(self, mode: int):
+        """The Gram update's schedule from the next push on (0, 1 or 2)."""
+        self._check(self._lib.osar_set_gram_ahead(self._h, int(mode)))
+
     def data_grad(self, gamma, d_b) -> np.ndarray:
         """dL/dd_s = G_s dL/db for the pulse at gamma (the forward model
         applied to the b-gradient)."""
@@ -497,6 +508,13 @@ class Osar:
             mask |= 1 << KERNEL_CLASSES[k]
         self._check(self._lib.osar_profile_select(
             self._h, mask if kernels else (1 << len(KERNEL_CLASSES)) - 1))
+
+    def profile_ahead(self, with_grid: bool = False):
+        """Pushes since the last profile reset whose Gram update ran ahead
+        (and, with_grid, the side stream's SMs of the last one)."""
+        n, g = C.c_int64(), C.c_int32()
+        self._check(self._lib.osar_profile_ahead(self._h, C.byref(n), C.byref(g)))
+        return (n.value, g.value) if with_grid else n.value
 
     def profile_sample(self, kernel: str, every: int):
         """Bracket one launch in `every` of this class."""

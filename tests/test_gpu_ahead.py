@@ -1,0 +1,103 @@
+"""The Gram update run ahead (gram_ahead): each push forms A_n and
+G_n = G_{n-1} + A_n^H A_n (Eqs. 12-13) on the side stream into a second
+Gram buffer, beside the previous pulse's burst, and the main stream waits
+for it and swaps buffers.  Only the schedule changes, so every result must
+be bitwise the in-order run's, which the parity tests hold to the oracle:
+
+* pulses queued without synchronisation (the update really runs beside the
+  previous burst), every push ahead: coefficients, state, b and the whole
+  Gram bitwise;
+* schedules mixed push by push (ahead, in order, the model's choice),
+  compared at every synchronisation;
+* the setter's and the config's refusals."""
+import numpy as np
+import pytest
+
+from paper_2603_08582_gb300 import osar
+from tests.helpers import small_workload, build_problem
+from tests.gpu_helpers import gpu_config
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem():
+    # 2048 atoms: 136 packed Gram blocks over several CTA pairs
+    w = small_workload(nx=32, ny=32, n_freq=128, n_pulses=8, span_deg=20.0,
+                       dictionary="gaussian", n_atoms=2048, sparsity=0.02,
+                       seed=21, dict_seed=7)
+    track, _, _, data = build_problem(w)
+    return w, track, data
+
+
+def _ctx(w, ahead):
+    cfg = gpu_config(w, "split_bf16")
+    cfg.gram_ahead = ahead
+    return osar.Osar(cfg)
+
+
+def _same(a, b, tag):
+    assert np.array_equal(a.coeffs(), b.coeffs()), tag
+    assert a.state() == b.state(), tag
+    assert np.array_equal(a.b(), b.b()), tag
+
+
+def test_queued_pulses_ahead_are_bitwise_in_order():
+    w, track, data = _problem()
+    ref, ahd = _ctx(w, 0), _ctx(w, 2)
+    for g in (ref, ahd):
+        for s in range(track.shape[0]):
+            g.push_pulse(track[s], data[s])
+            g.iterate(20, want_count=False)
+    _same(ref, ahd, "end")
+    assert np.array_equal(ref.gram(), ahd.gram())
+    assert ahd.profile_ahead() == track.shape[0]
+    assert ref.profile_ahead() == 0
+
+
+def test_mixed_schedules_are_bitwise_in_order():
+    w, track, data = _problem()
+    ref, ahd = _ctx(w, 0), _ctx(w, 2)
+    modes = [2, 2, 0, 2, 1, 0, 0, 2]
+    for s in range(track.shape[0]):
+        ahd.set_gram_ahead(modes[s])
+        before = ahd.profile_ahead()
+        for g in (ref, ahd):
+            g.push_pulse(track[s], data[s])
+            g.iterate(12 if s % 2 else 20, 1e-6, want_count=False)
+        if modes[s] == 2:
+            assert ahd.profile_ahead() == before + 1, s
+        if modes[s] == 0:
+            assert ahd.profile_ahead() == before, s
+        if s % 3 == 2:
+            _same(ref, ahd, s)
+    _same(ref, ahd, "end")
+    assert np.array_equal(ref.gram(), ahd.gram())
+    assert ahd.profile_ahead() >= 4
+
+
+def test_refusals():
+    w, _, _ = _problem()
+    g = _ctx(w, 0)
+    with pytest.raises(osar.OsarError) as e:
+        g.set_gram_ahead(1)
+    assert e.value.status == osar.OSAR_E_STATE
+    h = _ctx(w, 1)
+    with pytest.raises(osar.OsarError) as e:
+        h.set_gram_ahead(3)
+    assert e.value.status == osar.OSAR_E_INVALID
+    h.set_gram_ahead(0)
+    for prec, extra in [("fp32", {}), ("split_bf16", {"defer_gram": 1}),
+                        ("split_bf16", {"overlap_synthesis": 0})]:
+        cfg = gpu_config(w, prec)
+        cfg.gram_ahead = 1
+        for k, v in extra.items():
+            setattr(cfg, k, v)
+        with pytest.raises(osar.OsarError) as e:
+            osar.Osar(cfg)
+        assert e.value.status == osar.OSAR_E_INVALID, (prec, extra)
+    ident = small_workload(nx=16, ny=16, n_freq=32)
+    cfg = gpu_config(ident, "split_bf16")
+    cfg.gram_ahead = 2
+    with pytest.raises(osar.OsarError) as e:
+        osar.Osar(cfg)
+    assert e.value.status == osar.OSAR_E_INVALID
