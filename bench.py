@@ -447,7 +447,11 @@ def run_ours(args):
                 "frac_of_spec_7900_gbs": round(achieved / 7900.0, 4),
                 "passes": passes,
                 "note": ("timed-region average: part of the passes share the "
-                         "GPU with the next pulse's dictionary product"),
+                         "GPU with the next pulse's dictionary product"
+                         + (" and, when the update runs ahead, its Gram update "
+                            "(fewer SMs for the passes, HBM shared with its "
+                            "read-modify-write); `alone` is the same pass with "
+                            "the GPU to itself" if pushes_ahead else "")),
                 "alone": {"avg_launch_ms": round(mv_alone[1] / max(mv_alone[0], 1), 4),
                           "achieved": round(gram_bytes / (mv_alone[1] / max(mv_alone[0], 1) / 1e3) / 1e9, 1),
                           "frac": round(gram_bytes / (mv_alone[1] / max(mv_alone[0], 1) / 1e3) / 1e9
@@ -477,6 +481,13 @@ def run_ours(args):
     }
     if d_ms <= 0:
         tens.pop("dict")
+    if pushes_ahead and ahead_sms:
+        sm_all = torch.cuda.get_device_properties(local_rank).multi_processor_count
+        tens["gram"]["overlapped"] = (
+            f"side stream, {ahead_sms} of {sm_all} SMs, beside the previous burst "
+            f"({pushes_ahead} of {K} pushes): frac is of the whole GPU")
+        tens["gram"]["frac_of_its_sms"] = round(
+            tens["gram"]["achieved"] / (tens["gram"]["peak"] * ahead_sms / sm_all), 4)
     for v in tens.values():
         v["frac"] = round(v["achieved"] / v["peak"], 4)
     per_kernel = {k: {"launches": n, "total_ms": round(t, 3)} for k, (n, t) in brk.items()}
