@@ -490,6 +490,22 @@ def run_ours(args):
             tens["gram"]["achieved"] / (tens["gram"]["peak"] * ahead_sms / sm_all), 4)
     for v in tens.values():
         v["frac"] = round(v["achieved"] / v["peak"], 4)
+    # the whole pulse against HBM: the bytes its algorithm must move (the Gram
+    # passes, the compensated Gram's read-modify-write, one read of the
+    # dictionary planes) over the timed time per pulse; the Gram update's and
+    # the product's tensor work overlap the passes when they run beside them
+    step_bytes = (passes / K * gram_bytes + 2 * nblk * 128 * 128 * 12
+                  + (w.m_atoms * npx * 8 if w.dictionary == "gaussian" else 0))
+    step_roofline = {
+        "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+        "bytes_per_pulse": int(step_bytes),
+        "achieved": round(step_bytes / (ms / K / 1e3) / 1e9, 1),
+        "frac": round(step_bytes / (ms / K / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
+        "counts": ("per pulse: Gram passes x packed Gram bytes, the compensated "
+                   "Gram's read and write (12 B per stored entry each way), one read "
+                   "of the split dictionary planes (8 B per entry)")}
+    if args.pixel_gram:
+        step_roofline = None  # the pixel-space form moves other bytes
     per_kernel = {k: {"launches": n, "total_ms": round(t, 3)} for k, (n, t) in brk.items()}
     per_kernel["window"] = (f"pulses {W + K + 1}..{W + K + NBRK}, after the timed "
                             "region, every kernel class bracketed by events")
@@ -553,6 +569,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "tensor_rooflines": tens,
+        "step_roofline": step_roofline,
         "per_kernel": per_kernel,
     }
     if fp64 is not None:
