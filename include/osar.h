@@ -203,8 +203,9 @@ typedef struct {
   int32_t pixel_gram;
   /* Order of the Gram update's tiles: the upper blocks in super-blocks of
      gram_superblock x gram_superblock blocks, so that the tiles running at
-     the same time share operand rows in L2; 0 = 32.  Any order gives the
-     same results (each output block is one tile's).  In [0, 64]. */
+     the same time share operand rows in L2; 0 = 32 (16 with gram_ahead).
+     Any order gives the same results (each output block is one tile's).
+     In [0, 64]. */
   int32_t gram_superblock;
   /* SPLIT_BF16 with a dictionary, overlap_synthesis = 1, one lambda,
      defer_gram = 0 and pixel_gram = 0.  The Gram update of Eqs. 12-13 run
