@@ -51,7 +51,7 @@ def test_config_defaults_and_layout(lib):
     assert cfg.n_lambdas == 1 and cfg.lambda_list is None
     assert cfg.defer_gram == 0 and cfg.guard_bytes == 0
     assert cfg.fuse_power_gram == 1 and cfg.pixel_gram == 0
-    assert cfg.gram_superblock == 0
+    assert cfg.gram_superblock == 0 and cfg.gram_ahead == 0
 
 
 def test_config_struct_layout_matches_the_header(tmp_path):
@@ -112,6 +112,8 @@ def test_create_rejects_unsupported_deferred_update(lib, changes):
     ("fuse_first_step", 2), ("fuse_power_gram", 2), ("pixel_gram", 2),
     ("pixel_gram", 1),  # the pixel-space Gram form needs a dictionary
     ("gram_superblock", -1), ("gram_superblock", 65),
+    ("gram_ahead", -1), ("gram_ahead", 3),
+    ("gram_ahead", 1),  # the default config is FP64 with no dictionary
     ("n_lambdas", 0),
     ("n_lambdas", 9),
     ("n_lambdas", 2),  # > 1 without a lambda_list
