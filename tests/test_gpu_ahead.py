@@ -101,3 +101,28 @@ def test_refusals():
     with pytest.raises(osar.OsarError) as e:
         osar.Osar(cfg)
     assert e.value.status == osar.OSAR_E_INVALID
+
+
+def test_checkpoint_resume_with_the_update_ahead(tmp_path):
+    """A checkpoint taken between queued ahead pushes resumes bit for bit
+    (the save waits for the Gram the next burst reads, in whichever
+    buffer it sits)."""
+    w, track, data = _problem()
+    ref, ahd = _ctx(w, 0), _ctx(w, 2)
+    half = track.shape[0] // 2
+    for s in range(half):
+        for g in (ref, ahd):
+            g.push_pulse(track[s], data[s])
+            g.iterate(20, want_count=False)
+    path = str(tmp_path / "ahead.ckpt")
+    ahd.save(path)
+    ahd.close()
+    cfg = gpu_config(w, "split_bf16")
+    cfg.gram_ahead = 2
+    res = osar.Osar.load(path, cfg)
+    for s in range(half, track.shape[0]):
+        for g in (ref, res):
+            g.push_pulse(track[s], data[s])
+            g.iterate(20, want_count=False)
+    _same(ref, res, "resumed")
+    assert np.array_equal(ref.gram(), res.gram())
