@@ -126,3 +126,17 @@ def test_checkpoint_resume_with_the_update_ahead(tmp_path):
             g.iterate(20, want_count=False)
     _same(ref, res, "resumed")
     assert np.array_equal(ref.gram(), res.gram())
+
+
+def test_non_white_pulses_ahead_are_bitwise_in_order():
+    """Pulses with their own noise variances (the phase rows weighted by
+    1 / sigma_k on the stream that forms them) keep the in-order results."""
+    w, track, data = _problem()
+    var = np.random.default_rng(3).uniform(0.5, 2.0, size=(track.shape[0], w.n_freq))
+    ref, ahd = _ctx(w, 0), _ctx(w, 2)
+    for g in (ref, ahd):
+        for s in range(track.shape[0]):
+            g.push_pulse(track[s], data[s], noise_var=var[s] if s % 2 else None)
+            g.iterate(20, want_count=False)
+    _same(ref, ahd, "end")
+    assert np.array_equal(ref.gram(), ahd.gram())
