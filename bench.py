@@ -255,7 +255,7 @@ def make_ctx(w, precision, stream, overlap=True, synth_ctas=0, tc_pairs=3,
                            fuse_power_gram=power_gram,
                            gram_superblock=gram_superblock,
                            pixel_gram=pixel_gram and gauss,
-                           gram_ahead=(gram_ahead if gauss and overlap and not defer
+                           gram_ahead=(gram_ahead if overlap and not defer
                                        and not pixel_gram and precision == "split_bf16"
                                        else 0))
     return osar.Osar(cfg)
@@ -583,7 +583,8 @@ def run_ours(args):
         line["accuracy_vs_fp64_oracle"] = accuracy
     if rank == 0 and args.workload == "c2" and not args.no_large:
         line["pixel_space_gram_128x128"] = run_pixel_space_dense(stream, w)
-        line["large_online_256x256"] = run_large_online(stream, ref=large_ref)
+        line["large_online_256x256"] = run_large_online(stream, ref=large_ref,
+                                                        gram_ahead=args.gram_ahead)
     if args.forms and rank == 0:
         line["forms"] = run_forms(stream)
     if rank == 0:
@@ -656,7 +657,8 @@ def run_pixel_space_dense(stream, w, warmup=4, pulses=16):
     return out
 
 
-def run_large_online(stream, warmup=4, pulses=24, tune_every=8, ref=None):
+def run_large_online(stream, warmup=4, pulses=24, tune_every=8, ref=None,
+                     gram_ahead=0):
     """The 256 x 256 pixel-basis workload (N = M = 65536, K = 1024, 10 FISTA
     steps per pulse, split-BF16), without and with online lambda tuning (the
     burst's adjoint every `tune_every` pulses against the synthetic scene,
@@ -673,7 +675,7 @@ def run_large_online(stream, warmup=4, pulses=24, tune_every=8, ref=None):
            "pulses_warmup": warmup}
     track = data = None
     for tuned in (False, True):
-        ctx = make_ctx(w, "split_bf16", stream.cuda_stream)
+        ctx = make_ctx(w, "split_bf16", stream.cuda_stream, gram_ahead=gram_ahead)
         if track is None:
             track, data = pulse_data(ctx, w, warmup + pulses)
         tuner = (OnlineLambdaTuner(ctx, c_true, rho=w.lambda_rel, steps=steps,
@@ -698,6 +700,7 @@ def run_large_online(stream, warmup=4, pulses=24, tune_every=8, ref=None):
         g_n, g_ms = ctx.profile_read("gram_gemm")
         mv_n, mv_ms = ctx.profile_read("matvec")
         passes = ctx.profile_passes()
+        ahead, ahead_sms = ctx.profile_ahead(with_grid=True)
         ctx.profile_enable(False)
         err = float(np.linalg.norm(ctx.coeffs() - c_true) / np.linalg.norm(c_true))
         nblk = ctx_blocks(w.m_atoms)
@@ -709,6 +712,7 @@ def run_large_online(stream, warmup=4, pulses=24, tune_every=8, ref=None):
                "ms_per_pulse": round(1e3 * wall / pulses, 2),
                "device_gb": round(ctx.device_bytes() / 1e9, 1),
                "rel_err_vs_scene": round(err, 4),
+               "gram_ahead": f"{ahead} of {pulses} pushes, {ahead_sms} side SMs",
                "gram_update": {"avg_ms": round(g_ms / max(g_n, 1), 3),
                                "tflops": round(gram_flops / (g_ms / max(g_n, 1) / 1e3) / 1e12, 1),
                                "frac_of_sustained": round(gram_flops / (g_ms / max(g_n, 1) / 1e3) / 1e12

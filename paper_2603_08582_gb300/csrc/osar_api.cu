@@ -199,10 +199,10 @@ osar_status validate(const osar_config* c, std::string* why) {
   if (c->gram_ahead < 0 || c->gram_ahead > 2)
     return *why = "gram_ahead must be 0, 1 or 2", OSAR_E_INVALID;
   if (c->gram_ahead &&
-      (c->precision != OSAR_SPLIT_BF16 || c->dict_kind == OSAR_DICT_IDENTITY ||
-       !c->overlap_synthesis || c->n_lambdas != 1 || c->defer_gram || c->pixel_gram))
-    return *why = "gram_ahead needs SPLIT_BF16, a dictionary, overlap_synthesis, "
-                  "one lambda, defer_gram = 0 and pixel_gram = 0", OSAR_E_INVALID;
+      (c->precision != OSAR_SPLIT_BF16 || !c->overlap_synthesis || c->n_lambdas != 1 ||
+       c->defer_gram || c->pixel_gram))
+    return *why = "gram_ahead needs SPLIT_BF16, overlap_synthesis, one lambda, "
+                  "defer_gram = 0 and pixel_gram = 0", OSAR_E_INVALID;
   return OSAR_OK;
 }
 
@@ -529,7 +529,9 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaEventCreate"));
   }
-  if (ctx->dict && cfg->overlap_synthesis) {
+  // the side stream: the next pulse's forward block beside the burst (a
+  // dictionary), and the Gram update run ahead (gram_ahead, any basis)
+  if ((ctx->dict || cfg->gram_ahead) && cfg->overlap_synthesis) {
     e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
     for (cudaEvent_t* ev : {&ctx->ev_free, &ctx->ev_synth})
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
@@ -742,8 +744,9 @@ void refresh_iters_estimate(osar_ctx* ctx) {
 int synth_grid(const osar_ctx* ctx, bool main_idle, double* t_model = nullptr) {
   if (t_model) *t_model = 0.0;
   if (ctx->cfg.synth_ctas > 0) return std::min(ctx->cfg.synth_ctas, ctx->sm_count);
-  // an edgelet block is a gather of phase rows, too short to overlap
-  if (ctx->edgelet) return 0;
+  // an edgelet block is a gather of phase rows, too short to overlap; the
+  // pixel basis has no product (its side stream serves gram_ahead)
+  if (ctx->edgelet || !ctx->dict) return 0;
   // nothing in flight on the main stream (the caller waited for the last
   // burst): the product has the GPU to itself
   if (main_idle) return 0;
@@ -792,7 +795,8 @@ int ahead_grid(const osar_ctx* ctx, bool main_idle) {
   }
   constexpr double kDictRate = 1.2e13, kGramRate = 1.05e13;  // f/s per SM
   constexpr double kHbm = 6.8e12, kSmBw = 105e9, kContention = 1.15;  // B/s
-  const double dict_f = ctx->edgelet ? 0.0 : 24.0 * ctx->Kp * (double)ctx->Np * ctx->Mp;
+  const double dict_f =
+      ctx->edgelet || !ctx->dict ? 0.0 : 24.0 * ctx->Kp * (double)ctx->Np * ctx->Mp;
   const double gram_f = 3.0 * 2.0 * BLK * 2.0 * BLK * 2.0 * ctx->Kp * (double)ctx->nblk;
   const double bytes = (double)ctx->nblk * BLK * BLK * 8.0;
   const double pass = bytes / kHbm;

@@ -9,7 +9,9 @@ be bitwise the in-order run's, which the parity tests hold to the oracle:
   Gram bitwise;
 * schedules mixed push by push (ahead, in order, the model's choice),
   compared at every synchronisation;
-* the setter's and the config's refusals."""
+* the pixel basis (no dictionary product: the side stream forms the phase
+  planes and the update);
+* checkpoints, non-white pulses, the setter's and the config's refusals."""
 import numpy as np
 import pytest
 
@@ -95,12 +97,7 @@ def test_refusals():
         with pytest.raises(osar.OsarError) as e:
             osar.Osar(cfg)
         assert e.value.status == osar.OSAR_E_INVALID, (prec, extra)
-    ident = small_workload(nx=16, ny=16, n_freq=32)
-    cfg = gpu_config(ident, "split_bf16")
-    cfg.gram_ahead = 2
-    with pytest.raises(osar.OsarError) as e:
-        osar.Osar(cfg)
-    assert e.value.status == osar.OSAR_E_INVALID
+
 
 
 def test_checkpoint_resume_with_the_update_ahead(tmp_path):
@@ -140,3 +137,17 @@ def test_non_white_pulses_ahead_are_bitwise_in_order():
             g.iterate(20, want_count=False)
     _same(ref, ahd, "end")
     assert np.array_equal(ref.gram(), ahd.gram())
+
+
+def test_pixel_basis_ahead_is_bitwise_in_order():
+    w = small_workload(nx=48, ny=48, n_freq=96, n_pulses=6, span_deg=20.0,
+                       sparsity=0.03, seed=23)
+    track, _, _, data = build_problem(w)
+    ref, ahd = _ctx(w, 0), _ctx(w, 2)
+    for g in (ref, ahd):
+        for s in range(track.shape[0]):
+            g.push_pulse(track[s], data[s])
+            g.iterate(15, want_count=False)
+    _same(ref, ahd, "end")
+    assert np.array_equal(ref.gram(), ahd.gram())
+    assert ahd.profile_ahead() == track.shape[0]
