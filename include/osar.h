@@ -219,10 +219,12 @@ typedef struct {
      running between bursts.  1: a model of the last bursts' length against
      the tensor work decides per push between this and the in-order
      schedule (the forward block beside the burst, the update after it on
-     cuda_stream), so short bursts keep the in-order one; 2: always ahead
-     (a push while cuda_stream is being captured still runs in order).
+     cuda_stream), so short bursts keep the in-order one; 2: always ahead.
      Every result is bitwise that of 0.  Needs a second Gram in device
-     memory.  0 (default): in order. */
+     memory.  A push while cuda_stream is being captured returns
+     OSAR_E_STATE; bursts and osar_unroll_grad may still be captured (the
+     Gram passes read the current buffer's address from device memory,
+     which each swap rewrites in stream order).  0 (default): in order. */
   int32_t gram_ahead;
 } osar_config;
 

@@ -197,6 +197,10 @@ struct osar_ctx {
   // deferred Gram update (defer_gram): G_n forms on `side` into the second
   // buffer while pulse n's passes read G_{n-1} and add A_n^H A_n x
   void* gn_hi = nullptr;               // the other Gram buffer
+  // with two Gram buffers: a device slot holding g_hi's address, rewritten
+  // in stream order at each swap, which the matvec reads (so that a burst
+  // captured in a CUDA graph follows the swaps)
+  void** gram_ref = nullptr;
   __nv_bfloat162* gn_lo = nullptr;
   __nv_bfloat16* Apl_alt = nullptr;    // the other forward-block buffer
   CUtensorMap map_alt_rows1;           // Apl_alt, box (KC, 128, 1)
@@ -269,6 +273,9 @@ namespace osar {
 // the main stream waits for a pending Gram update, whose result its passes
 // then read directly (no-op when none is pending)
 cudaError_t settle_gram(osar_ctx* ctx);
+// writes g_hi's address into gram_ref on the context's stream (no-op
+// without a second Gram buffer)
+cudaError_t launch_set_gram_ref(osar_ctx* ctx);
 
 // ---- launch bracketing for the per-kernel profile -------------------------
 void prof_begin(osar_ctx* ctx, int kind, ProfEvent* ev);

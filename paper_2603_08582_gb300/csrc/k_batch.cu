@@ -481,7 +481,7 @@ cudaError_t batch_launch_matvec(osar_batch* B, const void* xt, int gated,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     k_matvec<T, 1, true><<<grid, C::THREADS, C::SMEM, B->stream>>>(
         (const T2*)B->g_hi, a, B->segs, B->nseg, 0, B->sc, 0,
-        matvec_queue(B->sc), mb);
+        matvec_queue(B->sc), mb, nullptr);
   };
   if (B->prec == OSAR_FP64)
     go(0.0);

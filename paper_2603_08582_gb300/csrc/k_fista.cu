@@ -520,7 +520,8 @@ void launch_mv(osar_ctx* ctx, MvArgs<T, R> a, int gated) {
   const unsigned grid = (unsigned)(ctx->nseg < slots ? ctx->nseg : slots);
   k_matvec<T, R, false><<<grid, C::THREADS, C::SMEM, ctx->stream>>>(
       (const typename Vec<T>::T2*)ctx->g_hi, a, ctx->segs, ctx->nseg, ctx->nb,
-      ctx->scal, gated, matvec_queue(ctx->scal), MvBatch{});
+      ctx->scal, gated, matvec_queue(ctx->scal), MvBatch{},
+      (const void* const*)ctx->gram_ref);
 }
 
 // Device address of solution l's stop flag (pointer arithmetic only).
@@ -743,6 +744,15 @@ cudaError_t prepare_burst_kernels() {
   set((const void*)k_burst_begin<double2>);
   set((const void*)k_iter_begin);
   return e;
+}
+
+__global__ void k_set_gram_ref(void** ref, void* p) { *ref = p; }
+
+cudaError_t launch_set_gram_ref(osar_ctx* ctx) {
+  if (!ctx->gram_ref) return cudaSuccess;
+  k_set_gram_ref<<<1, 1, 0, ctx->stream>>>(ctx->gram_ref, ctx->g_hi);
+  ctx->launches++;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_iter_begin(osar_ctx* ctx, double tol) {

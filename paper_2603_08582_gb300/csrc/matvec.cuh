@@ -161,12 +161,17 @@ constexpr uint64_t MV_WAIT_LIMIT_NS = 2000000000ull;
 // kernel spreads over whatever SMs are free, e.g. beside the next pulse's
 // dictionary product.  Every wait is bounded; on a timeout the CTA records
 // the error, stops at the next per-block barrier and drains its copies.
+// gref (nullable): a device slot holding the Gram's address, which then
+// replaces G; a context whose Gram alternates between two buffers rewrites
+// the slot in stream order at each swap, so that a launch captured in a CUDA
+// graph reads the Gram current when it runs.
 template <typename T, int R, bool BATCH>
 __global__ void __launch_bounds__(Mv<T, R>::THREADS, Mv<T, R>::CTAS)
     k_matvec(const typename Vec<T>::T2* __restrict__ G, const MvArgs<T, R> a,
              const int4* __restrict__ segs, int nseg, int nb,
              DevScalars* __restrict__ sc, int gated,
-             unsigned* __restrict__ queue, const MvBatch mb) {
+             unsigned* __restrict__ queue, const MvBatch mb,
+             const void* const* __restrict__ gref) {
   using C = Mv<T, R>;
   using T2 = typename Vec<T>::T2;
   if (!BATCH && gated) {
@@ -201,6 +206,7 @@ __global__ void __launch_bounds__(Mv<T, R>::THREADS, Mv<T, R>::CTAS)
     // stays resident for the next pass
     const uint64_t stream_policy =
         a.keep_l2 ? l2_policy_evict_last() : l2_policy_evict_first();
+    if (gref) G = reinterpret_cast<const T2*>(*gref);
     uint32_t issued[C::NST];
     for (int i = 0; i < C::NST; ++i) issued[i] = 0;
     int stage = 0;

@@ -69,7 +69,7 @@ void free_all(osar_ctx* ctx) {
                   ctx->segpart_x, ctx->tilepart_x, ctx->gn_hi, ctx->gn_lo,
                   ctx->Apl_alt, ctx->corr, ctx->corr_u, ctx->corr_tick,
                   ctx->atom_ptr, ctx->atom_pix, ctx->wk_dev, ctx->gp_col,
-                  ctx->gp_row, ctx->metrics_buf};
+                  ctx->gp_row, ctx->metrics_buf, ctx->gram_ref};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->pg) {
@@ -455,6 +455,7 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
     AL(ctx->gn_hi, cplx * bb * ctx->nblk);
     if (ctx->g_lo) AL(ctx->gn_lo, 4 * bb * ctx->nblk);
   }
+  if (cfg->gram_ahead || cfg->defer_gram) AL(ctx->gram_ref, sizeof(void*));
   if (cfg->defer_gram) {
     // second Gram and forward-block buffers, the pending block's term
     AL(ctx->gn_hi, cplx * bb * ctx->nblk);
@@ -551,6 +552,8 @@ osar_status create_impl(const osar_config* cfg, osar_ctx** out) {
       }
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "side stream"));
   }
+  e = launch_set_gram_ref(ctx);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "Gram address slot"));
 
   e = cudaMemcpyAsync(ctx->segs, segs.data(), sizeof(int4) * segs.size(),
                       cudaMemcpyHostToDevice, ctx->stream);
@@ -934,6 +937,7 @@ osar_status push_ahead(osar_ctx* ctx, const double gamma[3], int grid) {
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_gram, 0);
   std::swap(ctx->g_hi, ctx->gn_hi);
   std::swap(ctx->g_lo, ctx->gn_lo);
+  if (e == cudaSuccess) e = launch_set_gram_ref(ctx);
   ctx->pushes_ahead++;
   ctx->ahead_grid_last = grid;
   if (e == cudaSuccess) e = launch_data_update(ctx);
@@ -963,6 +967,10 @@ bool main_idle(osar_ctx* ctx) {
 // idle: main_idle() taken before the pulse's data copy was queued.
 osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
   cudaError_t e = cudaSuccess;
+  if (ctx->cfg.gram_ahead && capturing(ctx->stream))
+    return fail(ctx, OSAR_E_STATE,
+                "gram_ahead: a push cannot be captured into a CUDA graph (the "
+                "Gram it updates alternates between two buffers)");
   if (ctx->cfg.defer_gram) {
     if (capturing(ctx->stream))
       return fail(ctx, OSAR_E_STATE,
@@ -1051,6 +1059,8 @@ cudaError_t settle_gram(osar_ctx* ctx) {
   std::swap(ctx->g_hi, ctx->gn_hi);
   std::swap(ctx->g_lo, ctx->gn_lo);
   ctx->gram_pending = false;
+  const cudaError_t e2 = launch_set_gram_ref(ctx);
+  if (e2 != cudaSuccess) return e2;
   // a fused first step's pass lacks the block's term: the step runs its own
   ctx->first_ready = false;
   return cudaSuccess;

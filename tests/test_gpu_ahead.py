@@ -151,3 +151,59 @@ def test_pixel_basis_ahead_is_bitwise_in_order():
     _same(ref, ahd, "end")
     assert np.array_equal(ref.gram(), ahd.gram())
     assert ahd.profile_ahead() == track.shape[0]
+
+
+def test_adjoint_after_ahead_pushes_is_bitwise_in_order():
+    """osar_unroll_grad replays a cached CUDA graph of its passes; after the
+    Gram buffers swap it must read the new Gram (the passes take its
+    address from device memory)."""
+    w, track, data = _problem()
+    ref, ahd = _ctx(w, 0), _ctx(w, 2)
+    c_true = np.zeros(w.m_atoms, complex)
+    c_true[::97] = 1.0
+    out = {}
+    for tag, g in (("ref", ref), ("ahd", ahd)):
+        res = []
+        for s in range(4):
+            g.push_pulse(track[s], data[s])
+            g.iterate(10, want_count=False)
+            st = g.state()
+            res.append(g.unroll_grad(8, 4, st["lambda"], 1.0 / st["lipschitz"],
+                                     g.coeffs(), c_true))
+        out[tag] = res
+    for a, b in zip(out["ref"], out["ahd"]):
+        assert a["loss"] == b["loss"]
+        assert a["d_lambda"] == b["d_lambda"] and a["d_tau"] == b["d_tau"]
+        assert np.array_equal(a["d_b"], b["d_b"])
+
+
+def test_captured_burst_follows_the_swaps():
+    """A burst captured once in a CUDA graph and replayed for later pulses
+    reads each pulse's Gram, in whichever buffer it sits."""
+    torch = pytest.importorskip("torch")
+    w, track, data = _problem()
+    stream = torch.cuda.Stream()
+
+    def ctx(ahead):
+        cfg = gpu_config(w, "split_bf16")
+        cfg.gram_ahead = ahead
+        cfg.cuda_stream = stream.cuda_stream
+        return osar.Osar(cfg)
+
+    eager, replay = ctx(0), ctx(2)
+    graph = None
+    for s in range(track.shape[0]):
+        for g in (eager, replay):
+            g.push_pulse(track[s], data[s])
+            g.iterate(4, want_count=False)
+        eager.iterate(6, want_count=False)
+        if graph is None:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                replay.iterate(6, want_count=False)
+        with torch.cuda.stream(stream):
+            graph.replay()
+        stream.synchronize()
+        assert np.array_equal(eager.coeffs(), replay.coeffs()), s
+        assert eager.state() == replay.state(), s
+    assert replay.profile_ahead() == track.shape[0]
