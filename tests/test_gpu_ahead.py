@@ -207,3 +207,20 @@ def test_captured_burst_follows_the_swaps():
         assert np.array_equal(eager.coeffs(), replay.coeffs()), s
         assert eager.state() == replay.state(), s
     assert replay.profile_ahead() == track.shape[0]
+
+
+def test_edgelet_dictionary_ahead_is_bitwise_in_order():
+    """Edgelet blocks (sums of phase rows, no GEMM) formed on the side
+    stream with the update run ahead."""
+    w = small_workload(nx=24, ny=24, n_freq=64, n_pulses=6, span_deg=20.0,
+                       dictionary="edgelet", edgelet_lengths=(4,),
+                       edgelet_angles=(0.0, 90.0), sparsity=0.02, seed=25)
+    track, _, _, data = build_problem(w)
+    ref, ahd = _ctx(w, 0), _ctx(w, 2)
+    for g in (ref, ahd):
+        for s in range(track.shape[0]):
+            g.push_pulse(track[s], data[s])
+            g.iterate(15, want_count=False)
+    _same(ref, ahd, "end")
+    assert np.array_equal(ref.gram(), ahd.gram())
+    assert ahd.profile_ahead() == track.shape[0]
