@@ -209,7 +209,6 @@ struct osar_ctx {
   // gram_ahead: main stream past the last push's power steps (their reads of
   // the Gram, of v and of the fused power step's partials are done)
   cudaEvent_t ev_steps = nullptr;
-  bool steps_stale = false;            // ev_steps predates a captured push
   cudaEvent_t ev_mark[2] = {};         // main: all work before push n (n % 2)
   bool gram_pending = false;           // g_hi holds G_{n-1}, gn_hi gets G_n
   float2* corr = nullptr;              // A_n^H A_n x per partial set (2 x Mp)

@@ -926,8 +926,6 @@ osar_status push_ahead(osar_ctx* ctx, const double gamma[3], int grid) {
     e = early ? synthesize_dict(ctx, grid) : synthesize(ctx, gamma, grid);
   }
   ctx->synth_side = true;
-  if (ctx->steps_stale && e == cudaSuccess) e = cudaEventRecord(ctx->ev_steps, ctx->stream);
-  ctx->steps_stale = false;
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_steps, 0);
   if (e == cudaSuccess) {
     LaunchOn on(ctx, ctx->side);
@@ -1037,13 +1035,8 @@ osar_status push_impl(osar_ctx* ctx, const double gamma[3], bool idle) {
                                      ctx->n == 1 ? ctx->cfg.power_iters_first
                                                  : ctx->cfg.power_iters,
                                      ctx->cfg.fuse_first_step != 0);
-  if (e == cudaSuccess && ctx->ev_steps) {
-    // a captured push leaves no usable ev_steps behind either
-    if (capturing(ctx->stream))
-      ctx->steps_stale = true;
-    else
-      e = cudaEventRecord(ctx->ev_steps, ctx->stream);
-  }
+  // (with gram_ahead; a push is then never captured)
+  if (e == cudaSuccess && ctx->ev_steps) e = cudaEventRecord(ctx->ev_steps, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "osar_push_pulse");
   return OSAR_OK;
 }
