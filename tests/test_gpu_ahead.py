@@ -224,3 +224,24 @@ def test_edgelet_dictionary_ahead_is_bitwise_in_order():
     _same(ref, ahd, "end")
     assert np.array_equal(ref.gram(), ahd.gram())
     assert ahd.profile_ahead() == track.shape[0]
+
+
+@pytest.mark.parametrize("tc_pairs,power_gram", [(0, 0), (1, 1), (2, 0)])
+def test_other_kernel_choices_ahead_are_bitwise_in_order(tc_pairs, power_gram):
+    """The update run ahead on single-SM tiles or SM pairs, with or without
+    the power step in its epilogue."""
+    w, track, data = _problem()
+    ctxs = []
+    for ahead in (0, 2):
+        cfg = gpu_config(w, "split_bf16")
+        cfg.gram_ahead = ahead
+        cfg.tc_pairs = tc_pairs
+        cfg.fuse_power_gram = power_gram
+        ctxs.append(osar.Osar(cfg))
+    ref, ahd = ctxs
+    for g in (ref, ahd):
+        for s in range(4):
+            g.push_pulse(track[s], data[s])
+            g.iterate(12, want_count=False)
+    _same(ref, ahd, (tc_pairs, power_gram))
+    assert np.array_equal(ref.gram(), ahd.gram())
