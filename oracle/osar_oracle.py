@@ -47,10 +47,13 @@ Readings taken where the paper is silent, ambiguous or garbled:
   coefficient domain: the true atoms against the rest.
 
 Parity status: every function below is pinned by closed forms, invariants,
-brute force or an independent solver in tests/test_oracle_pins.py, except the
-online trajectory as a whole (lambda_n schedule, carried t, noise draw), whose
-only check is agreement between this oracle and the CUDA path: parity unpinned
-for `OnlineFista` as a whole-trajectory reference.
+brute force or an independent solver in tests/test_oracle_pins.py.  The
+online trajectory has no closed form; `OnlineFista` is pinned pulse by pulse
+instead: lambda_n against the batch data vector, L_n against G_n's spectrum
+and the stored power vector, the warm start and the carried t, two bursts
+equal to one, and every pulse's converged image against the LASSO optimality
+conditions of that pulse's (G_n, b_n, lambda_n).  The noise draws are inputs
+from the seeded generators, not part of this module.
 """
 from __future__ import annotations
 

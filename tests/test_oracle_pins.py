@@ -649,3 +649,62 @@ def test_non_white_increments_are_the_weighted_sums():
                            for i in range(4)], rtol=1e-13, atol=0)
     assert np.allclose(orc.gram_increment(a, np.full(6, 4.0)),
                        orc.gram_increment(a) / 4.0, rtol=1e-13, atol=0)
+
+
+# ------------------------------------------------- the online trajectory ---
+
+@pytest.mark.parametrize("dictionary", [None, "gaussian"])
+def test_online_trajectory_pulse_by_pulse(dictionary):
+    """The online run pinned pulse by pulse to what the paper fixes, so that
+    a mistake anywhere along the trajectory (lambda's schedule, the Lipschitz
+    bound, the warm start, the carried momentum, the problem each burst
+    solves) fails here and not only in oracle-GPU agreement:
+
+    * lambda_n = rho max|b_n| with b_n the batch sum over the pulses so far,
+      formed here from the phase matrices with an einsum (Eqs. 11, 13);
+    * L_n is non-decreasing, at most (1 + delta) lambda_max(G_n), and where
+      it grew it is (1 + delta) times the last power step's Rayleigh
+      quotient, hence at most that of the stored power vector (one more step
+      on a PSD matrix can only raise it) (Eq. 14, Eq. 11);
+    * a burst starts from the previous pulse's image (c^(0) = z^(1) =
+      c_hat_{n-1}) with t carried (t_1 = 1 only on the first pulse);
+    * run to convergence, every pulse's image satisfies the LASSO
+      optimality conditions of (G_n, b_n, lambda_n) (Eq. 8)."""
+    if dictionary is None:
+        w = small_workload(nx=6, ny=6, n_freq=12, n_pulses=6, seed=4)
+    else:
+        w = small_workload(nx=6, ny=6, n_freq=12, n_pulses=6, seed=4,
+                           dictionary="gaussian", n_atoms=50, dict_seed=3)
+    track, dic, _, data = build_problem(w)
+    cfg = oracle_config(w, dic, lam=0.05)
+    of = orc.OnlineFista(cfg)
+    x = orc.pixel_positions(w.nx, w.ny, w.pixel_m)
+    f = orc.frequencies(w.n_freq, w.f_lo_hz, w.f_hi_hz)
+    blocks = []
+    lip_prev = 0.0
+    c_prev_pulse = np.zeros(of.m, complex)
+    t_prev = None
+    for n in range(w.n_pulses):
+        of.push_pulse(track[n], data[n])
+        p = orc.phase_matrix(track[n], x, f)
+        blocks.append(p if dic is None else p @ dic)
+        a = np.stack(blocks)                          # pulses x K x M
+        b_batch = np.einsum("skm,sk->m", a.conj(), data[: n + 1])
+        g_batch = np.einsum("skm,skj->mj", a.conj(), a)
+        s = of.s
+        assert abs(s.lam - 0.05 * np.max(np.abs(b_batch))) <= 1e-12 * s.lam
+        eig = np.linalg.eigvalsh(g_batch)
+        mu = float(np.real(np.vdot(s.v, g_batch @ s.v)) / np.vdot(s.v, s.v).real)
+        assert s.lip >= lip_prev
+        assert s.lip <= (1 + cfg.lipschitz_margin) * eig[-1] * (1 + 1e-12)
+        if s.lip > lip_prev:
+            assert s.lip <= (1 + cfg.lipschitz_margin) * mu * (1 + 1e-12)
+        lip_prev = s.lip
+        assert of.iterate(0) == 0                      # starts the burst only
+        assert np.array_equal(s.z, c_prev_pulse)
+        assert np.array_equal(s.c_prev, c_prev_pulse)
+        assert s.t == (1.0 if n == 0 else t_prev)
+        of.iterate(200000, 1e-13)
+        assert orc.kkt_residual(g_batch, b_batch, s.c_hat, s.lam) <= 1e-6, n
+        c_prev_pulse = s.c_hat.copy()
+        t_prev = s.t
