@@ -1,9 +1,11 @@
 """Parity at the sizes the bench runs: the split-BF16 path with the bench's
 launch configuration (SM-pair tensor-core products, the first power step in
 the Gram update's epilogue, the last power step fused with the first FISTA
-step, overlapped synthesis) against the FP64 oracle after every pulse's
-20-step burst (Algorithm 1; Eqs. 11-13), on problems large enough that every
-multi-tile path runs:
+step, overlapped synthesis, the Gram update run ahead into the second Gram
+buffer on part of the GPU: gram_ahead = 2, so that it runs ahead on every
+push even after the synchronising iterate) against the FP64 oracle after
+every pulse's 20-step burst (Algorithm 1; Eqs. 11-13), on problems large
+enough that every multi-tile path runs:
 
 * 64 x 64 pixels, M = 8192 Gaussian atoms, K = 512: 2080 packed Gram blocks,
   so each SM pair of the Gram update handles many tiles (TMEM double buffer,
@@ -74,7 +76,9 @@ def _run(w, pulses, steps, rng, pixel_form=False):
     dic = host_gaussian_dictionary(w.n_pixels, w.m_atoms, w.dict_seed)
     track, _, data = dictionary_pulses(w, dic, pulses)
     of = orc.OnlineFista(oracle_config(w, dic, lam=w.lambda_rel))
-    gpu = osar.Osar(gpu_config(w, "split_bf16", lam=w.lambda_rel))
+    cfg = gpu_config(w, "split_bf16", lam=w.lambda_rel)
+    cfg.gram_ahead = 2
+    gpu = osar.Osar(cfg)
     pix = None
     if pixel_form:
         cfg = gpu_config(w, "split_bf16", lam=w.lambda_rel)
@@ -97,6 +101,7 @@ def _run(w, pulses, steps, rng, pixel_form=False):
             errs.append(assert_coeffs(pix.coeffs(), of.s, TOL_C,
                                       SUPPORT_DELTA["split_bf16"],
                                       f"pulse {s} pixel form c"))
+    assert gpu.profile_ahead() == pulses
     # the matvec on a dense random vector, every row
     x = rng.standard_normal(w.m_atoms) + 1j * rng.standard_normal(w.m_atoms)
     assert_close(gpu.gram_apply(x), of.s.gram @ x, TOL_GRAM, "gram apply")
@@ -134,7 +139,9 @@ def test_large_online_256x256_first_pulses_matrix_free_oracle():
     noise = synth.unit_noise(w.n_pulses, w.n_freq, w.seed)[:P]
     data = clean + synth.scale_noise(clean, noise, w.snr_db)
     of = orc.OnlineFista(oracle_config(w, None, lam=w.lambda_rel), matrix_free=True)
-    gpu = osar.Osar(gpu_config(w, "split_bf16", lam=w.lambda_rel))
+    cfg = gpu_config(w, "split_bf16", lam=w.lambda_rel)
+    cfg.gram_ahead = 2
+    gpu = osar.Osar(cfg)
     rng = np.random.default_rng(3)
     errs = []
     for s in range(P):
@@ -143,6 +150,7 @@ def test_large_online_256x256_first_pulses_matrix_free_oracle():
         assert of.iterate(steps) == steps
         assert gpu.iterate(steps) == steps
         errs.append(_compare(of, gpu, rng, f"pulse {s}"))
+    assert gpu.profile_ahead() == P
     xv = rng.standard_normal(w.m_atoms) + 1j * rng.standard_normal(w.m_atoms)
     assert_close(gpu.gram_apply(xv), of.s.gram @ xv, TOL_GRAM, "gram apply")
     gpu.close()
