@@ -210,11 +210,10 @@ typedef struct {
   /* SPLIT_BF16, overlap_synthesis = 1, one lambda, defer_gram = 0 and
      pixel_gram = 0 (any dictionary, the pixel basis included).  The Gram
      update of Eqs. 12-13 run ahead: a push queues the pulse's forward block
-     A_n and
-     G_n = G_{n-1} + A_n^H A_n on the side stream, into a second Gram
-     buffer, so that both run beside the previous pulse's burst (which still
-     reads G_{n-1}); cuda_stream then waits for G_n, the buffers swap, and
-     the data update, power steps and burst follow as usual.  The update's
+     A_n and G_n = G_{n-1} + A_n^H A_n on the side stream, into a second
+     Gram buffer, so that both run beside the previous pulse's burst (which
+     still reads G_{n-1}); cuda_stream then waits for G_n, the buffers swap,
+     and the data update, power steps and burst follow as usual.  The update's
      tensor work then overlaps the bandwidth-bound Gram passes instead of
      running between bursts.  1: a model of the last bursts' length against
      the tensor work decides per push between this and the in-order
