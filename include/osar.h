@@ -218,7 +218,10 @@ typedef struct {
      running between bursts.  1: a model of the last bursts' length against
      the tensor work decides per push between this and the in-order
      schedule (the forward block beside the burst, the update after it on
-     cuda_stream), so short bursts keep the in-order one; 2: always ahead.
+     cuda_stream), so short bursts keep the in-order one, and so does a
+     push queued while cuda_stream is idle (after an osar_iterate that
+     returned its step count, say: nothing runs for the update to hide
+     beside); 2: always ahead.
      Every result is bitwise that of 0.  Needs a second Gram in device
      memory.  A push while cuda_stream is being captured returns
      OSAR_E_STATE; bursts and osar_unroll_grad may still be captured (the
