@@ -245,3 +245,24 @@ def test_other_kernel_choices_ahead_are_bitwise_in_order(tc_pairs, power_gram):
             g.iterate(12, want_count=False)
     _same(ref, ahd, (tc_pairs, power_gram))
     assert np.array_equal(ref.gram(), ahd.gram())
+
+
+def test_static_gram_apply_reads_the_current_buffer():
+    """The allocation-free Gram apply after ahead pushes (the Gram then sits
+    in either buffer) equals the allocating apply bit for bit."""
+    torch = pytest.importorskip("torch")
+    w, track, data = _problem()
+    g = _ctx(w, 2)
+    rng = np.random.default_rng(8)
+    for s in range(3):
+        g.push_pulse(track[s], data[s])
+        g.iterate(5, want_count=False)
+        x = rng.standard_normal(w.m_atoms) + 1j * rng.standard_normal(w.m_atoms)
+        ref = g.gram_apply(x)
+        xd = torch.from_numpy(x).to("cuda")
+        yd = torch.empty_like(xd)
+        torch.cuda.synchronize()
+        g.gram_apply_static(xd.data_ptr(), yd.data_ptr())
+        g.synchronize()
+        assert np.array_equal(yd.cpu().numpy(), ref), s
+    assert g.profile_ahead() == 3
