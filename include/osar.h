@@ -207,8 +207,8 @@ typedef struct {
      Any order gives the same results (each output block is one tile's).
      In [0, 64]. */
   int32_t gram_superblock;
-  /* SPLIT_BF16, overlap_synthesis = 1, one lambda, defer_gram = 0 and
-     pixel_gram = 0 (any dictionary, the pixel basis included).  The Gram
+  /* SPLIT_BF16, overlap_synthesis = 1, defer_gram = 0 and pixel_gram = 0
+     (any dictionary, the pixel basis included, lambda paths too).  The Gram
      update of Eqs. 12-13 run ahead: a push queues the pulse's forward block
      A_n and G_n = G_{n-1} + A_n^H A_n on the side stream, into a second
      Gram buffer, so that both run beside the previous pulse's burst (which

@@ -199,10 +199,10 @@ osar_status validate(const osar_config* c, std::string* why) {
   if (c->gram_ahead < 0 || c->gram_ahead > 2)
     return *why = "gram_ahead must be 0, 1 or 2", OSAR_E_INVALID;
   if (c->gram_ahead &&
-      (c->precision != OSAR_SPLIT_BF16 || !c->overlap_synthesis || c->n_lambdas != 1 ||
-       c->defer_gram || c->pixel_gram))
-    return *why = "gram_ahead needs SPLIT_BF16, overlap_synthesis, one lambda, "
-                  "defer_gram = 0 and pixel_gram = 0", OSAR_E_INVALID;
+      (c->precision != OSAR_SPLIT_BF16 || !c->overlap_synthesis || c->defer_gram ||
+       c->pixel_gram))
+    return *why = "gram_ahead needs SPLIT_BF16, overlap_synthesis, defer_gram = 0 "
+                  "and pixel_gram = 0", OSAR_E_INVALID;
   return OSAR_OK;
 }
 

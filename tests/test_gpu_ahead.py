@@ -266,3 +266,28 @@ def test_static_gram_apply_reads_the_current_buffer():
         g.synchronize()
         assert np.array_equal(yd.cpu().numpy(), ref), s
     assert g.profile_ahead() == 3
+
+
+def test_lambda_path_ahead_is_bitwise_in_order():
+    """Several solutions sharing one Gram (the lambda path) with the update
+    run ahead."""
+    w, track, data = _problem()
+    lams = np.asarray([0.02, 0.05, 0.11], dtype=np.float64)
+    ctxs = []
+    for ahead in (0, 2):
+        cfg = gpu_config(w, "split_bf16")
+        cfg.n_lambdas = len(lams)
+        cfg.lambda_list = lams.ctypes.data
+        cfg.gram_ahead = ahead
+        ctxs.append(osar.Osar(cfg))
+    ref, ahd = ctxs
+    for g in (ref, ahd):
+        for s in range(5):
+            g.push_pulse(track[s], data[s])
+            g.iterate(12, want_count=False)
+    for l in range(len(lams)):
+        a, b = ref.lambda_state(l), ahd.lambda_state(l)
+        assert np.array_equal(a["coeffs"], b["coeffs"]), l
+        assert a["lambda"] == b["lambda"] and a["t"] == b["t"], l
+    assert np.array_equal(ref.gram(), ahd.gram())
+    assert ahd.profile_ahead() == 5
