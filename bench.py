@@ -920,7 +920,7 @@ def run_forms(stream):
                 w.nx, w.ny, w.n_freq, w.f_lo_hz, w.f_hi_hz, pixel_m=w.pixel_m,
                 precision="split_bf16", dictionary="gaussian", n_atoms=w.m_atoms,
                 dict_seed=w.dict_seed, lam=lams[0], stream=stream.cuda_stream,
-                lambdas=lams[:n])
+                lambdas=lams[:n], gram_ahead=1)
             ctx = osar.Osar(cfg)
             track, data, _ = _sim_pulses(ctx, w, 7)
             for s in range(3):
@@ -935,6 +935,7 @@ def run_forms(stream):
             ctx.close()
         out["c2_lambda_path"] = {
             "lambdas": len(lams), "pulses": 4, "steps": INNER_STEPS,
+            "gram_ahead": "model (both runs)",
             "ms_per_pulse": round(res[len(lams)], 2),
             "ms_per_pulse_one_lambda": round(res[1], 2),
             "solution_pulses_per_s": round(len(lams) / (res[len(lams)] / 1e3), 1),
