@@ -89,7 +89,8 @@ def test_refusals():
     assert e.value.status == osar.OSAR_E_INVALID
     h.set_gram_ahead(0)
     for prec, extra in [("fp32", {}), ("split_bf16", {"defer_gram": 1}),
-                        ("split_bf16", {"overlap_synthesis": 0})]:
+                        ("split_bf16", {"overlap_synthesis": 0}),
+                        ("split_bf16", {"pixel_gram": 1})]:
         cfg = gpu_config(w, prec)
         cfg.gram_ahead = 1
         for k, v in extra.items():
